@@ -1,0 +1,115 @@
+/* gbdmrg -- two-site DMRG sweep engine for GB300 (sm_103a), C ABI.
+ *
+ * The library maps active-space integrals to a converged matrix-product
+ * state and returns its energy and one-/two-particle reduced density
+ * matrices: the DMRG node of the paper's pipeline, which "maps active-space
+ * integrals (h_act, B^Q_act) to the converged MPS and its RDMs" (Sec.
+ * "Contraction-DAG transpose", the paragraph introducing the DMRG node, and
+ * Sec. "The DMRG-QD-NEVPT2 energy").  Inside, every two-site step solves the
+ * effective Hamiltonian matrix-free against the MPO with Davidson and
+ * decimates the enlarged bond by SVD (Fig. 2, Sec. "Cholesky decomposition
+ * for the wavefunction"); all contractions run in this library's CUDA
+ * kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - return GBD_OK (0) on success, a negative GBD_ERR_* code otherwise;
+ *     gbd_last_error(ctx) then holds a one-line reason.  No C++ exception
+ *     crosses this boundary.
+ *   - input arrays are host memory, read during the call, copied and never
+ *     retained; outputs are written into caller-owned host buffers.
+ *   - a context owns its device memory and CUDA stream; it is not thread
+ *     safe (use one context per host thread).
+ */
+#ifndef GBDMRG_H
+#define GBDMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBD_OK 0
+#define GBD_ERR_ARG (-1)      /* invalid argument (sizes, symmetry, NaN) */
+#define GBD_ERR_OOM (-2)      /* device allocation failed */
+#define GBD_ERR_CUDA (-3)     /* a CUDA call failed */
+#define GBD_ERR_NOCONV (-4)   /* Davidson or eigensolver did not converge */
+#define GBD_ERR_TIMEOUT (-5)  /* a bounded device wait ran out */
+#define GBD_ERR_STATE (-6)    /* call order violated (e.g. sweep before prepare) */
+
+/* precision of the bulk contractions (sigma build and environment update);
+ * Davidson orthogonalisation, Rayleigh-Ritz, decimation and the final energy
+ * are FP64 in every mode */
+#define GBD_FP64 0
+#define GBD_TF32 1
+#define GBD_BF16 2
+
+#define GBD_PRECOND_DIAG 0
+#define GBD_PRECOND_LEARNED 1
+
+typedef struct gbd_ctx gbd_ctx;
+
+/* Active-space problem (Sec. "The DMRG-QD-NEVPT2 energy"):
+ *   H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps)
+ *   (pq|rs) = sum_Q chol[Q,p,q] chol[Q,r,s]   (Cholesky-factorised ERIs)
+ * h:    [n_orb * n_orb] row-major, symmetric to 1e-12, finite.
+ * chol: [n_chol * n_orb * n_orb] row-major, each slice symmetric.
+ * n_elec in [0, 2 n_orb]; n_elec and two_sz have equal parity;
+ * |two_sz| <= min(n_elec, 2 n_orb - n_elec).  2 <= n_orb <= 32.
+ * e_core is added to every returned energy. */
+typedef struct {
+  int32_t n_orb, n_elec, two_sz, n_chol;
+  const double *h;
+  const double *chol;
+  double e_core;
+} gbd_problem;
+
+/* Sweep schedule.  One sweep = left-to-right over the bonds (0,1)..(n-2,n-1)
+ * then right-to-left back, 2(n-1) two-site steps.
+ * bond_dim[s], davidson_tol[s]: bond dimension M and the tolerance on the
+ * residual norm ||H psi - theta psi|| of the normalised Ritz vector, per
+ * sweep s.  svd_cutoff: discarded-weight floor on sigma^2 (0 -> 1e-12).
+ * seed: seeds the counter-based initial MPS. */
+typedef struct {
+  int32_t n_sweeps;
+  const int32_t *bond_dim;
+  const double *davidson_tol;
+  int32_t davidson_max_iter;      /* per two-site step (0 -> 100) */
+  int32_t davidson_max_subspace;  /* restart size limit (0 -> 24) */
+  int32_t precision;              /* GBD_FP64 | GBD_TF32 | GBD_BF16 */
+  int32_t preconditioner;         /* GBD_PRECOND_DIAG | GBD_PRECOND_LEARNED */
+  uint64_t seed;
+  double svd_cutoff;
+} gbd_schedule;
+
+/* Results.  sweep_energies: [n_sweeps] caller-owned (may be NULL); rdm1
+ * [n^2] and rdm2 [n^4] caller-owned or NULL (skipped).  RDM conventions:
+ * rdm1[p,q] = sum_s <a+_ps a_qs>, rdm2[p,q,r,s] = sum_st <a+_ps a+_rt a_st a_qs>,
+ * so E = sum h rdm1 + 1/2 sum (pq|rs) rdm2 + e_core. */
+typedef struct {
+  double energy;
+  double *sweep_energies;
+  double *rdm1;
+  double *rdm2;
+  double max_discarded_weight;
+  int64_t n_matvec;
+  int32_t status;
+} gbd_result;
+
+/* Create a context on CUDA device `device_ordinal`. */
+int gbd_create(gbd_ctx **ctx, int device_ordinal);
+/* Release all device memory and the stream of a context (NULL is a no-op). */
+void gbd_destroy(gbd_ctx *ctx);
+/* Reason for the last failure on this context ("" if none). */
+const char *gbd_last_error(const gbd_ctx *ctx);
+
+/* Full solve: validate, build the MPO, initial MPS and environments on the
+ * device, run the schedule, then energy and RDMs.  Host<->device traffic is
+ * the inputs once and the results once. */
+int gbd_solve(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule,
+              gbd_result *result);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

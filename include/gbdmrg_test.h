@@ -1,0 +1,92 @@
+/* gbdmrg test and timing hooks: the steps gbd_solve runs, exposed one by one
+ * so that each can be compared with an independent CPU implementation and
+ * timed on its own.  Same conventions as gbdmrg.h (status codes, host
+ * buffers, no exceptions).
+ *
+ * MPS exchange format ("canonical blocks").  Bond k (0..n) is a list of
+ * sectors (N_alpha, N_beta, dim) of the left block (sites < k), sorted by
+ * (N_alpha, N_beta); `sectors` holds the triples of all bonds back to back
+ * and n_sectors[k] their counts.  Site i stores, for every sector q_l of
+ * bond i in order and every local state s = 0..3 ([0, alpha, beta,
+ * alpha+beta]) with q_r = q_l + s present in bond i+1, one row-major
+ * dim(q_l) x dim(q_r) block; `data` holds all sites back to back.
+ *
+ * Two-site vector format for bond pair (k, k+1): for every sector q_l of bond
+ * k in order, s1 = 0..3, s2 = 0..3 with q_r = q_l + s1 + s2 present in bond
+ * k+2, one row-major dim(q_l) x dim(q_r) block.
+ */
+#ifndef GBDMRG_TEST_H
+#define GBDMRG_TEST_H
+
+#include "gbdmrg.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double sigma_flops;     /* algorithmic flops of all sigma builds (2mnk per block product) */
+  double sigma_ms;        /* device time of the sigma builds (CUDA events on the engine stream) */
+  double env_flops, env_ms;
+  double enlarge_ms;      /* host wall time forming the enlarged operators */
+  double davidson_ms, truncate_ms, step_ms;
+  int64_t n_sigma, n_steps, kernel_launches, h2d_bytes, d2h_bytes;
+  double max_discarded_weight;
+} gbd_stats;
+
+/* Validate the problem and schedule, build the MPO; no MPS yet. */
+int gbd_setup(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule);
+/* Seeded initial MPS (right-canonical) and all right environments. */
+int gbd_init_state(gbd_ctx *ctx);
+/* One full sweep with the schedule's entry `sweep`; energy = last Ritz value. */
+int gbd_run_sweep(gbd_ctx *ctx, int32_t sweep, double *energy);
+/* <psi|H|psi>/<psi|psi> + e_core of the current MPS (evaluated at bond (0,1)). */
+int gbd_final_energy(gbd_ctx *ctx, double *energy);
+/* Sector triples of one bond; count = number of sectors (cap in triples). */
+int gbd_get_bond(gbd_ctx *ctx, int32_t bond, int32_t *triples, int32_t cap, int32_t *count);
+/* Install an MPS in canonical blocks.  Sites < center must be left-
+ * orthonormal and sites > center+1 right-orthonormal; left environments up
+ * to bond `center` and right environments from bond center+2 are built. */
+int gbd_set_mps(gbd_ctx *ctx, const int32_t *n_sectors, const int32_t *sectors, const double *data,
+                int32_t center);
+/* Length of the two-site vector at (k, k+1). */
+int gbd_two_site_size(gbd_ctx *ctx, int32_t k, int64_t *size);
+/* out = H_eff in (two-site format); diag (may be NULL) = diagonal of H_eff. */
+int gbd_apply_heff(gbd_ctx *ctx, int32_t k, const double *in, double *out, double *diag);
+/* One two-site step at (k, k+1): Davidson from the current two-site state,
+ * decimation to at most M states and the environment update.  dir 0 = left
+ * to right, 1 = right to left.  kept: the kept weights sigma^2 in descending
+ * order (cap entries, count in *nkept). */
+int gbd_run_step(gbd_ctx *ctx, int32_t k, int32_t dir, int32_t M, double tol, double *energy,
+                 double *discarded, double *kept, int32_t cap, int32_t *nkept);
+/* MPO channel keys of one bond (kind<<40 | nops<<32 | code0<<16 | code1). */
+int gbd_mpo_labels(gbd_ctx *ctx, int32_t bond, uint64_t *keys, int32_t cap, int32_t *count);
+/* One environment block (side 0 = left, 1 = right) for (channel, sector index). */
+int gbd_env_block(gbd_ctx *ctx, int32_t side, int32_t bond, int32_t channel, int32_t sector, double *out,
+                  int64_t cap, int32_t *rows, int32_t *cols);
+int gbd_get_stats(const gbd_ctx *ctx, gbd_stats *stats);
+/* Counter-based initial-MPS entry (splitmix64; the same definition as the
+ * synthetic-input generator), for checking that both agree. */
+double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, int32_t s, int32_t row,
+                          int32_t col);
+
+/* ---- host-only pieces of the planner (no GPU needed) ---- */
+/* Initial bond dimensions of the seeded MPS for n orbitals, (N_alpha,
+ * N_beta) electrons and bond dimension M; n_sectors [n+1], triples [3 cap]. */
+int gbd_host_initial_dims(int32_t n, int32_t n_alpha, int32_t n_beta, int32_t M, int32_t *n_sectors,
+                          int32_t *triples, int32_t cap);
+/* Decimation rule on `count` weights lam (= sigma^2) with sector keys
+ * (64 N_alpha + N_beta) and in-sector ranks j: indices of the kept weights
+ * in kept order, their number, and the total weight. */
+int gbd_host_select(int32_t count, const double *lam, const int32_t *key, const int32_t *j, int32_t M,
+                    double cutoff, double tie, int32_t *kept_index, int32_t *nkept, double *total);
+/* MPO bond dimensions [n+1]; if dense != NULL (n <= 5) also the full
+ * 4^n x 4^n matrix of the contracted MPO in the product basis
+ * |s_0 ... s_{n-1}> (site 0 most significant). */
+int gbd_host_mpo(int32_t n, const double *h, int32_t n_chol, const double *chol, int32_t k_switch,
+                 int32_t *bond_dims, double *dense);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,397 @@
+// C ABI of the sweep engine: argument validation, error codes, and the
+// translation of exceptions into status codes (none crosses the boundary).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "../../include/gbdmrg.h"
+#include "../../include/gbdmrg_test.h"
+#include "engine.h"
+
+namespace gbd {
+double mps_init_value(uint64_t seed, int site, int na, int nb, int s, int row, int col);
+}
+
+struct gbd_ctx {
+  int device = 0;
+  std::unique_ptr<gbd::Engine> eng;
+  std::string err;
+};
+
+namespace {
+
+int fail(gbd_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+template <class F>
+int guarded(gbd_ctx* c, F&& f) {
+  if (!c) return GBD_ERR_ARG;
+  try {
+    c->err.clear();
+    return f();
+  } catch (const gbd::Error& e) {
+    return fail(c, e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(c, GBD_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(c, GBD_ERR_CUDA, e.what());
+  }
+}
+
+int validate(gbd_ctx* c, const gbd_problem* p, const gbd_schedule* s) {
+  if (!p || !s) return fail(c, GBD_ERR_ARG, "problem or schedule is NULL");
+  int n = p->n_orb;
+  if (n < 2 || n > 32) return fail(c, GBD_ERR_ARG, "n_orb must be in [2, 32]");
+  if (p->n_elec < 0 || p->n_elec > 2 * n) return fail(c, GBD_ERR_ARG, "n_elec outside [0, 2 n_orb]");
+  if (((p->n_elec - p->two_sz) % 2) != 0) return fail(c, GBD_ERR_ARG, "n_elec and two_sz parity differ");
+  int lim = std::min(p->n_elec, 2 * n - p->n_elec);
+  if (std::abs(p->two_sz) > lim) return fail(c, GBD_ERR_ARG, "|two_sz| too large for n_elec");
+  if (p->n_chol < 0) return fail(c, GBD_ERR_ARG, "n_chol < 0");
+  if (!p->h || (p->n_chol > 0 && !p->chol)) return fail(c, GBD_ERR_ARG, "h or chol is NULL");
+  if (!std::isfinite(p->e_core)) return fail(c, GBD_ERR_ARG, "e_core not finite");
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double a = p->h[i * n + j], b = p->h[j * n + i];
+      if (!std::isfinite(a)) return fail(c, GBD_ERR_ARG, "h has NaN/Inf");
+      if (std::fabs(a - b) > 1e-12) return fail(c, GBD_ERR_ARG, "h is not symmetric");
+    }
+  for (int Q = 0; Q < p->n_chol; ++Q)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double a = p->chol[((size_t)Q * n + i) * n + j], b = p->chol[((size_t)Q * n + j) * n + i];
+        if (!std::isfinite(a)) return fail(c, GBD_ERR_ARG, "chol has NaN/Inf");
+        if (std::fabs(a - b) > 1e-12) return fail(c, GBD_ERR_ARG, "chol slice is not symmetric");
+      }
+  if (s->n_sweeps < 1 || !s->bond_dim || !s->davidson_tol) return fail(c, GBD_ERR_ARG, "empty sweep schedule");
+  for (int i = 0; i < s->n_sweeps; ++i) {
+    if (s->bond_dim[i] < 1) return fail(c, GBD_ERR_ARG, "bond_dim < 1");
+    if (!(s->davidson_tol[i] > 0) || !std::isfinite(s->davidson_tol[i]))
+      return fail(c, GBD_ERR_ARG, "davidson_tol must be positive");
+  }
+  if (s->davidson_max_iter < 0 || s->davidson_max_subspace < 0) return fail(c, GBD_ERR_ARG, "negative Davidson limit");
+  if (s->davidson_max_subspace != 0 && s->davidson_max_subspace < 5)
+    return fail(c, GBD_ERR_ARG, "davidson_max_subspace must be >= 5");
+  if (s->precision != GBD_FP64 && s->precision != GBD_TF32 && s->precision != GBD_BF16)
+    return fail(c, GBD_ERR_ARG, "unknown precision");
+  if (s->precision != GBD_FP64) return fail(c, GBD_ERR_ARG, "reduced-precision contractions are not built in this library");
+  if (s->preconditioner != GBD_PRECOND_DIAG && s->preconditioner != GBD_PRECOND_LEARNED)
+    return fail(c, GBD_ERR_ARG, "unknown preconditioner");
+  if (s->preconditioner != GBD_PRECOND_DIAG) return fail(c, GBD_ERR_ARG, "learned preconditioner not loaded");
+  if (s->svd_cutoff < 0 || !std::isfinite(s->svd_cutoff)) return fail(c, GBD_ERR_ARG, "svd_cutoff invalid");
+  return GBD_OK;
+}
+
+gbd::Schedule to_schedule(const gbd_schedule* s) {
+  gbd::Schedule out;
+  for (int i = 0; i < s->n_sweeps; ++i) {
+    out.M.push_back(s->bond_dim[i]);
+    out.tol.push_back(s->davidson_tol[i]);
+  }
+  out.max_iter = s->davidson_max_iter > 0 ? s->davidson_max_iter : 100;
+  out.max_space = s->davidson_max_subspace > 0 ? s->davidson_max_subspace : 24;
+  out.precision = s->precision;
+  out.precond = s->preconditioner;
+  out.seed = s->seed;
+  out.cutoff = s->svd_cutoff > 0 ? s->svd_cutoff : 1e-12;
+  return out;
+}
+
+int setup(gbd_ctx* c, const gbd_problem* p, const gbd_schedule* s) {
+  int rc = validate(c, p, s);
+  if (rc != GBD_OK) return rc;
+  if (!c->eng) c->eng.reset(new gbd::Engine(c->device));
+  c->eng->prepare(p->n_orb, p->n_elec, p->two_sz, p->n_chol, p->h, p->chol, p->e_core, to_schedule(s));
+  return GBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbd_create(gbd_ctx** ctx, int device_ordinal) {
+  if (!ctx) return GBD_ERR_ARG;
+  *ctx = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return GBD_ERR_CUDA;
+  if (device_ordinal < 0 || device_ordinal >= ndev) return GBD_ERR_ARG;
+  gbd_ctx* c = new (std::nothrow) gbd_ctx;
+  if (!c) return GBD_ERR_OOM;
+  c->device = device_ordinal;
+  *ctx = c;
+  return GBD_OK;
+}
+
+void gbd_destroy(gbd_ctx* ctx) {
+  if (!ctx) return;
+  try {
+    ctx->eng.reset();
+  } catch (...) {
+  }
+  delete ctx;
+}
+
+const char* gbd_last_error(const gbd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gbd_solve(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, gbd_result* r) {
+  return guarded(ctx, [&]() {
+    if (!r) return fail(ctx, GBD_ERR_ARG, "result is NULL");
+    int rc = setup(ctx, p, s);
+    if (rc != GBD_OK) return rc;
+    gbd::Engine& e = *ctx->eng;
+    e.init_state();
+    for (int i = 0; i < s->n_sweeps; ++i) {
+      double en = e.sweep(i);
+      if (r->sweep_energies) r->sweep_energies[i] = en + p->e_core;
+    }
+    r->energy = e.final_energy() + p->e_core;
+    if (r->rdm1 || r->rdm2) e.rdms(r->rdm1, r->rdm2);
+    r->max_discarded_weight = e.stats.max_discarded;
+    r->n_matvec = e.stats.n_sigma;
+    r->status = GBD_OK;
+    return GBD_OK;
+  });
+}
+
+int gbd_setup(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s) {
+  return guarded(ctx, [&]() { return setup(ctx, p, s); });
+}
+
+int gbd_init_state(gbd_ctx* ctx) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    ctx->eng->init_state();
+    return GBD_OK;
+  });
+}
+
+int gbd_run_sweep(gbd_ctx* ctx, int32_t sweep, double* energy) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state: gbd_init_state first");
+    if (sweep < 0 || sweep >= (int)ctx->eng->sched.M.size()) return fail(ctx, GBD_ERR_ARG, "sweep index out of range");
+    double e = ctx->eng->sweep(sweep);
+    if (energy) *energy = e + ctx->eng->e_core;
+    return GBD_OK;
+  });
+}
+
+int gbd_final_energy(gbd_ctx* ctx, double* energy) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (!energy) return fail(ctx, GBD_ERR_ARG, "energy is NULL");
+    *energy = ctx->eng->final_energy() + ctx->eng->e_core;
+    return GBD_OK;
+  });
+}
+
+int gbd_get_bond(gbd_ctx* ctx, int32_t bond, int32_t* triples, int32_t cap, int32_t* count) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (bond < 0 || bond > ctx->eng->n) return fail(ctx, GBD_ERR_ARG, "bond out of range");
+    std::vector<int> v;
+    ctx->eng->bond_sectors(bond, v);
+    int nsec = (int)v.size() / 3;
+    if (count) *count = nsec;
+    if (triples) {
+      if (cap < nsec) return fail(ctx, GBD_ERR_ARG, "triples buffer too small");
+      std::memcpy(triples, v.data(), v.size() * sizeof(int));
+    }
+    return GBD_OK;
+  });
+}
+
+int gbd_set_mps(gbd_ctx* ctx, const int32_t* n_sectors, const int32_t* sectors, const double* data, int32_t center) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    if (!n_sectors || !sectors || !data) return fail(ctx, GBD_ERR_ARG, "NULL MPS input");
+    int n = ctx->eng->n;
+    if (center < 0 || center > n - 2) return fail(ctx, GBD_ERR_ARG, "center out of range");
+    ctx->eng->set_mps(n_sectors, sectors, data, center);
+    return GBD_OK;
+  });
+}
+
+int gbd_two_site_size(gbd_ctx* ctx, int32_t k, int64_t* size) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (k < 0 || k > ctx->eng->n - 2) return fail(ctx, GBD_ERR_ARG, "k out of range");
+    *size = ctx->eng->two_site_size(k);
+    return GBD_OK;
+  });
+}
+
+int gbd_apply_heff(gbd_ctx* ctx, int32_t k, const double* in, double* out, double* diag) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (k < 0 || k > ctx->eng->n - 2) return fail(ctx, GBD_ERR_ARG, "k out of range");
+    if (!in || !out) return fail(ctx, GBD_ERR_ARG, "NULL vector");
+    ctx->eng->apply_heff(k, in, out, diag);
+    return GBD_OK;
+  });
+}
+
+int gbd_run_step(gbd_ctx* ctx, int32_t k, int32_t dir, int32_t M, double tol, double* energy, double* discarded,
+                 double* kept, int32_t cap, int32_t* nkept) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (k < 0 || k > ctx->eng->n - 2) return fail(ctx, GBD_ERR_ARG, "k out of range");
+    if (dir != 0 && dir != 1) return fail(ctx, GBD_ERR_ARG, "dir must be 0 or 1");
+    if (M < 1 || !(tol > 0)) return fail(ctx, GBD_ERR_ARG, "bad M or tol");
+    std::vector<double> kw;
+    double tau = 0;
+    double e = ctx->eng->run_step(k, dir, M, tol, &tau, &kw);
+    if (energy) *energy = e + ctx->eng->e_core;
+    if (discarded) *discarded = tau;
+    if (nkept) *nkept = (int)kw.size();
+    if (kept) {
+      if (cap < (int)kw.size()) return fail(ctx, GBD_ERR_ARG, "kept buffer too small");
+      std::memcpy(kept, kw.data(), kw.size() * sizeof(double));
+    }
+    return GBD_OK;
+  });
+}
+
+int gbd_mpo_labels(gbd_ctx* ctx, int32_t bond, uint64_t* keys, int32_t cap, int32_t* count) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    if (bond < 0 || bond > ctx->eng->n) return fail(ctx, GBD_ERR_ARG, "bond out of range");
+    auto v = ctx->eng->mpo_labels(bond);
+    if (count) *count = (int)v.size();
+    if (keys) {
+      if (cap < (int)v.size()) return fail(ctx, GBD_ERR_ARG, "keys buffer too small");
+      std::memcpy(keys, v.data(), v.size() * sizeof(uint64_t));
+    }
+    return GBD_OK;
+  });
+}
+
+int gbd_env_block(gbd_ctx* ctx, int32_t side, int32_t bond, int32_t channel, int32_t sector, double* out,
+                  int64_t cap, int32_t* rows, int32_t* cols) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (bond < 0 || bond > ctx->eng->n) return fail(ctx, GBD_ERR_ARG, "bond out of range");
+    if (channel < 0 || channel >= ctx->eng->mpo_bond_dim(bond)) return fail(ctx, GBD_ERR_ARG, "channel out of range");
+    std::vector<int> sec;
+    ctx->eng->bond_sectors(bond, sec);
+    if (sector < 0 || sector >= (int)sec.size() / 3) return fail(ctx, GBD_ERR_ARG, "sector out of range");
+    std::vector<double> v;
+    int r = 0, c = 0;
+    ctx->eng->env_block(side, bond, channel, sector, v, r, c);
+    if (rows) *rows = r;
+    if (cols) *cols = c;
+    if (out) {
+      if (cap < (int64_t)v.size()) return fail(ctx, GBD_ERR_ARG, "out buffer too small");
+      std::memcpy(out, v.data(), v.size() * sizeof(double));
+    }
+    return GBD_OK;
+  });
+}
+
+int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {
+  if (!ctx || !s) return GBD_ERR_ARG;
+  std::memset(s, 0, sizeof(*s));
+  if (!ctx->eng) return GBD_OK;
+  const gbd::Stats& t = ctx->eng->stats;
+  s->sigma_flops = t.sigma_flops;
+  s->sigma_ms = t.sigma_ms;
+  s->env_flops = t.env_flops;
+  s->env_ms = t.env_ms;
+  s->enlarge_ms = t.enl_ms;
+  s->davidson_ms = t.davidson_ms;
+  s->truncate_ms = t.trunc_ms;
+  s->step_ms = t.step_ms;
+  s->n_sigma = t.n_sigma;
+  s->n_steps = t.n_steps;
+  s->kernel_launches = t.launches;
+  s->h2d_bytes = t.h2d;
+  s->d2h_bytes = t.d2h;
+  s->max_discarded_weight = t.max_discarded;
+  return GBD_OK;
+}
+
+int gbd_host_initial_dims(int32_t n, int32_t n_alpha, int32_t n_beta, int32_t M, int32_t* n_sectors,
+                          int32_t* triples, int32_t cap) {
+  if (n < 1 || n > 32 || n_alpha < 0 || n_beta < 0 || n_alpha > n || n_beta > n || M < 1 || !n_sectors)
+    return GBD_ERR_ARG;
+  try {
+    auto bonds = gbd::initial_bond_dims(n, n_alpha, n_beta, M);
+    int pos = 0;
+    for (int k = 0; k <= n; ++k) {
+      n_sectors[k] = bonds[k].nsec();
+      for (int j = 0; j < bonds[k].nsec(); ++j) {
+        if (triples) {
+          if (pos + 3 > 3 * cap) return GBD_ERR_ARG;
+          triples[pos] = bonds[k].na[j];
+          triples[pos + 1] = bonds[k].nb[j];
+          triples[pos + 2] = bonds[k].dim[j];
+        }
+        pos += 3;
+      }
+    }
+    return GBD_OK;
+  } catch (...) {
+    return GBD_ERR_ARG;
+  }
+}
+
+int gbd_host_select(int32_t count, const double* lam, const int32_t* key, const int32_t* j, int32_t M,
+                    double cutoff, double tie, int32_t* kept_index, int32_t* nkept, double* total) {
+  if (count < 0 || (count > 0 && (!lam || !key || !j)) || M < 1 || !nkept) return GBD_ERR_ARG;
+  std::vector<gbd::Weight> w;
+  for (int i = 0; i < count; ++i) w.push_back({lam[i], key[i], i, j[i]});
+  auto kw = gbd::select_states(w, M, cutoff, tie, total);
+  *nkept = (int)kw.size();
+  if (kept_index)
+    for (size_t i = 0; i < kw.size(); ++i) kept_index[i] = kw[i].idx;
+  return GBD_OK;
+}
+
+int gbd_host_mpo(int32_t n, const double* h, int32_t n_chol, const double* chol, int32_t k_switch,
+                 int32_t* bond_dims, double* dense) {
+  if (n < 1 || n > 32 || !h || (n_chol > 0 && !chol) || !bond_dims) return GBD_ERR_ARG;
+  if (dense && n > 5) return GBD_ERR_ARG;
+  try {
+    std::vector<double> eri((size_t)n * n * n * n, 0.0);
+    for (int Q = 0; Q < n_chol; ++Q)
+      for (int pq = 0; pq < n * n; ++pq)
+        for (int rs = 0; rs < n * n; ++rs)
+          eri[(size_t)pq * n * n + rs] += chol[(size_t)Q * n * n + pq] * chol[(size_t)Q * n * n + rs];
+    gbd::Mpo m;
+    gbd::build_mpo(n, h, eri.data(), k_switch, m);
+    for (int k = 0; k <= n; ++k) bond_dims[k] = (int)m.labels[k].size();
+    if (dense) {
+      // plain Kronecker contraction of the dressed tensors (site 0 most significant)
+      std::vector<std::vector<double>> env(1, std::vector<double>(1, 1.0));
+      int dim = 1;
+      for (int i = 0; i < n; ++i) {
+        int nd = dim * 4;
+        std::vector<std::vector<double>> nx(m.labels[i + 1].size());
+        for (const auto& e : m.W[i]) {
+          if (env[e.a].empty()) continue;
+          auto& t = nx[e.b];
+          if (t.empty()) t.assign((size_t)nd * nd, 0.0);
+          for (int r = 0; r < dim; ++r)
+            for (int c = 0; c < dim; ++c) {
+              double x = env[e.a][(size_t)r * dim + c];
+              if (x == 0.0) continue;
+              t[(size_t)(r * 4 + e.sout) * nd + c * 4 + e.sin] += x * e.v;
+            }
+        }
+        env.swap(nx);
+        dim = nd;
+      }
+      for (size_t i = 0; i < (size_t)dim * dim; ++i) dense[i] = env[0].empty() ? 0.0 : env[0][i];
+    }
+    return GBD_OK;
+  } catch (...) {
+    return GBD_ERR_ARG;
+  }
+}
+
+double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, int32_t s, int32_t row, int32_t col) {
+  return gbd::mps_init_value(seed, site, na, nb, s, row, col);
+}
+
+}  // extern "C"

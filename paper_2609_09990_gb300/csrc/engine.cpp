@@ -1,0 +1,1600 @@
+// Two-site DMRG sweep engine (host driver of the device kernels).
+//
+// Method (paper, Fig. 2 and Sec. "Cholesky decomposition for the
+// wavefunction"): sites (k, k+1) are optimised against the left block and
+// the right block; the two-site effective Hamiltonian is applied matrix-free
+// through the MPO inside Davidson; the enlarged bond is decimated back to
+// chi_k by the singular values of the two-site state, discarding weight
+// tau = sum sigma^2 of the dropped states; the sweep runs left-to-right and
+// back.  FP64 throughout in this path (Sec. "Computational details").
+//
+// GB300 formulation (ours).  Every tensor is blocked by the left-block
+// particle numbers q = (N_alpha, N_beta).  With the MPO bond b between the
+// two sites, H_eff = sum_b Lenl[b] (x) Renl[b], where
+//   Lenl[b] = sum_a L_k[a] (x) W_k[a,b]        (enlarged left operator)
+//   Renl[b] = sum_c W_{k+1}[b,c] (x) R_{k+2}[c] (enlarged right operator)
+// are formed once per step, and each matvec is two grouped GEMM launches:
+//   stage A  Y_b = psi Renl[b]^T      stage B  sigma = sum_b Lenl[b] Y_b.
+// The environment update reuses Lenl (Renl): L_{k+1}[b] = U^T Lenl[b] U.
+// The decimation diagonalises the per-sector reduced density matrix
+// psi psi^T (or psi^T psi), whose eigenvalues are sigma^2.
+#include "engine.h"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <thread>
+
+#include "linalg_host.h"
+
+namespace gbd {
+
+#define CK(x)                                                                                      \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ != cudaSuccess)                                                                         \
+      throw Error(e_ == cudaErrorMemoryAllocation ? -2 : -3,                                      \
+                  std::string(#x) + ": " + cudaGetErrorString(e_) + " (line " +                  \
+                      std::to_string(__LINE__) + ")");                                             \
+  } while (0)
+
+void Bond::finalize() {
+  std::vector<int> ord(na.size());
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return qkey(na[x], nb[x]) < qkey(na[y], nb[y]); });
+  std::vector<int> a2, b2, d2;
+  for (int i : ord) { a2.push_back(na[i]); b2.push_back(nb[i]); d2.push_back(dim[i]); }
+  na = a2; nb = b2; dim = d2;
+  off.assign(na.size() + 1, 0);
+  idx.clear();
+  for (size_t i = 0; i < na.size(); ++i) {
+    off[i + 1] = off[i] + dim[i];
+    idx[qkey(na[i], nb[i])] = (int)i;
+  }
+}
+
+namespace {
+
+constexpr uint64_t GOLDEN = 0x9E3779B97F4A7C15ull;
+constexpr uint64_t SALT = 0x4D50535F494E4954ull;
+
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  double r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return std::round(r);
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void parallel_for(int n, const std::function<void(int)>& f) {
+  int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+  if (n < 2 || nt < 2) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < std::min(nt, n); ++t)
+    th.emplace_back([&]() {
+      for (int i = next++; i < n; i = next++) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+// counter-based initial-MPS value (same published definition as the input
+// generator: splitmix64 finalizer on a derived seed and an element key)
+double mps_init_value(uint64_t seed, int site, int na, int nb, int s, int row, int col) {
+  uint64_t base = mix64(seed ^ SALT);
+  uint64_t key = ((((((uint64_t)site * 64 + na) * 64 + nb) * 4 + s) << 20 | (uint64_t)row) << 20) | (uint64_t)col;
+  uint64_t z = mix64(base + (key + 1) * GOLDEN);
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// Initial bond dimensions (the paper leaves the initial state open): every
+// sector allowed by the target particle numbers, with the exact dimension
+// min(left multiplicity, right multiplicity); when the exact total T exceeds
+// M, sector q gets min(d(q), max(1, floor(M d(q) / T))); then passes from
+// the left (dim <= sum_s dim_{k-1}(q - s)) and from the right (dim <= sum_s
+// dim_{k+1}(q + s)) repeat until nothing changes.
+std::vector<Bond> initial_bond_dims(int n, int Na, int Nb, int M) {
+  // initial bond dimensions: every allowed sector, scaled to M when the
+  // exact total exceeds it, then made consistent from both sides
+  std::vector<std::map<int, int64_t>> dims(n + 1);
+  for (int k = 0; k <= n; ++k) {
+    std::map<int, int64_t> ex;
+    double T = 0;
+    for (int a = 0; a <= std::min(k, Na); ++a)
+      for (int b = 0; b <= std::min(k, Nb); ++b) {
+        int ra = Na - a, rb = Nb - b;
+        if (ra < 0 || rb < 0 || ra > n - k || rb > n - k) continue;
+        double left = binom(k, a) * binom(k, b), right = binom(n - k, ra) * binom(n - k, rb);
+        double d = std::min(left, right);
+        if (d > 0) { ex[qkey(a, b)] = (int64_t)d; T += d; }
+      }
+    if (T <= M) dims[k] = ex;
+    else {
+      unsigned __int128 TT = 0;
+      for (auto& kv : ex) TT += (unsigned __int128)kv.second;
+      for (auto& kv : ex) {
+        unsigned __int128 v = ((unsigned __int128)M * (unsigned __int128)kv.second) / TT;
+        int64_t d = std::max<int64_t>(1, (int64_t)v);
+        dims[k][kv.first] = std::min<int64_t>(kv.second, d);
+      }
+    }
+  }
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int k = 1; k <= n; ++k)
+      for (auto& kv : dims[k]) {
+        int a = kv.first / 64, b = kv.first % 64;
+        int64_t sup = 0;
+        for (int s = 0; s < 4; ++s) {
+          auto it = dims[k - 1].find(qkey(a - QA[s], b - QB[s]));
+          if (a - QA[s] >= 0 && b - QB[s] >= 0 && it != dims[k - 1].end()) sup += it->second;
+        }
+        if (sup < kv.second) { kv.second = sup; changed = true; }
+      }
+    for (int k = n - 1; k >= 0; --k)
+      for (auto& kv : dims[k]) {
+        int a = kv.first / 64, b = kv.first % 64;
+        int64_t sup = 0;
+        for (int s = 0; s < 4; ++s) {
+          auto it = dims[k + 1].find(qkey(a + QA[s], b + QB[s]));
+          if (it != dims[k + 1].end()) sup += it->second;
+        }
+        if (sup < kv.second) { kv.second = sup; changed = true; }
+      }
+    for (int k = 0; k <= n; ++k)
+      for (auto it = dims[k].begin(); it != dims[k].end();) {
+        if (it->second == 0) { it = dims[k].erase(it); changed = true; }
+        else ++it;
+      }
+  }
+  std::vector<Bond> bonds(n + 1);
+  for (int k = 0; k <= n; ++k) {
+    for (auto& kv : dims[k]) {
+      bonds[k].na.push_back(kv.first / 64);
+      bonds[k].nb.push_back(kv.first % 64);
+      bonds[k].dim.push_back((int)kv.second);
+    }
+    bonds[k].finalize();
+  }
+  return bonds;
+}
+
+// Decimation rule (the paper keeps chi_k states and discards tau = sum of
+// the dropped sigma^2, Fig. 2): drop lambda = sigma^2 <= cutoff; order by
+// lambda descending, equal values by (sector key, in-sector rank); keep
+// min(M, count); if the last kept and the first dropped differ by <= tie,
+// step back so that a near-degenerate cluster is never split at the cut
+// (unless the cluster reaches the top, then keep min(M, count)).
+std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, double tie, double* total) {
+  double tot = 0;
+  std::vector<Weight> cand;
+  for (auto& x : w) {
+    tot += x.lam;
+    if (x.lam > cutoff) cand.push_back(x);
+  }
+  if (total) *total = tot;
+  std::stable_sort(cand.begin(), cand.end(), [](const Weight& a, const Weight& b) {
+    if (a.lam != b.lam) return a.lam > b.lam;
+    if (a.key != b.key) return a.key < b.key;
+    return a.j < b.j;
+  });
+  int nk = std::min<int>(M, (int)cand.size());
+  if ((int)cand.size() > nk) {
+    int j = nk;
+    while (j > 0 && cand[j - 1].lam - cand[j].lam <= tie) --j;
+    if (j > 0) nk = j;
+  }
+  cand.resize(nk);
+  return cand;
+}
+
+// ------------------------------------------------------------------ basics
+Engine::Engine(int dev) : device(dev) {
+  CK(cudaSetDevice(device));
+  CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  cudaMemPool_t pool;
+  CK(cudaDeviceGetDefaultMemPool(&pool, device));
+  uint64_t thr = UINT64_MAX;
+  CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+}
+
+Engine::~Engine() {
+  cudaSetDevice(device);
+  for (auto& e : Lenv) free_env(e);
+  for (auto& e : Renv) free_env(e);
+  for (auto& s : sites) free_site(s);
+  if (psi) dfree(psi);
+  cudaStreamSynchronize(stream);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+template <class T>
+T* Engine::dalloc(size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), stream);
+  if (e != cudaSuccess) throw Error(-2, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  allocs[(uintptr_t)p] = n * sizeof(T);
+  return (T*)p;
+}
+
+void Engine::dfree(void* p) {
+  if (!p) return;
+  allocs.erase((uintptr_t)p);
+  CK(cudaFreeAsync(p, stream));
+}
+
+// Every block a plan touches must lie inside one live allocation; a planning
+// error becomes a GBD_ERR_STATE instead of an out-of-bounds device access.
+void Engine::check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, const char* what) const {
+  if (rows <= 0 || cols <= 0) return;
+  if (ld < cols) throw Error(-6, std::string("plan check: leading dimension too small for ") + what);
+  uintptr_t a = (uintptr_t)p;
+  uintptr_t end = a + (uintptr_t)(((rows - 1) * ld + cols) * (int64_t)sizeof(double));
+  auto it = allocs.upper_bound(a);
+  if (it == allocs.begin()) throw Error(-6, std::string("plan check: pointer outside allocations: ") + what);
+  --it;
+  if (a < it->first || end > it->first + it->second)
+    throw Error(-6, std::string("plan check: block exceeds its allocation: ") + what);
+}
+
+void Engine::check(const GemmPlan& p) const {
+  for (const auto& o : p.outs) {
+    check_range(o.C, o.M, o.N, o.ldc, "C");
+    for (int t = o.t0; t < o.t1; ++t) {
+      const GemmTerm& g = p.terms[t];
+      if (g.K <= 0) continue;
+      if (g.flags & 1) check_range(g.A, g.K, o.M, g.lda, "A^T");
+      else check_range(g.A, o.M, g.K, g.lda, "A");
+      if (g.flags & 2) check_range(g.B, o.N, g.K, g.ldb, "B^T");
+      else check_range(g.B, g.K, o.N, g.ldb, "B");
+    }
+  }
+}
+
+void Engine::check(const AxpyPlan& p) const {
+  for (const auto& o : p.outs) {
+    check_range(o.dst, 1, o.len, o.len, "axpy dst");
+    for (int t = o.t0; t < o.t1; ++t) check_range(p.terms[t].src, 1, o.len, o.len, "axpy src");
+  }
+}
+
+void Engine::sync() { CK(cudaStreamSynchronize(stream)); }
+
+void Engine::upload(GemmPlan& p) {
+  check(p);
+  p.d_terms = dalloc<GemmTerm>(p.terms.size());
+  p.d_outs = dalloc<GemmOut>(p.outs.size());
+  // tiles: 32 x 32 outputs
+  p.tiles.clear();
+  for (int o = 0; o < (int)p.outs.size(); ++o) {
+    const GemmOut& g = p.outs[o];
+    for (int tm = 0; tm * 32 < g.M; ++tm)
+      for (int tn = 0; tn * 32 < g.N; ++tn) p.tiles.push_back({o, tm, tn, 0});
+  }
+  // longest term lists first for load balance
+  std::stable_sort(p.tiles.begin(), p.tiles.end(), [&](const GemmTile& a, const GemmTile& b) {
+    const GemmOut& x = p.outs[a.out];
+    const GemmOut& y = p.outs[b.out];
+    return (x.t1 - x.t0) > (y.t1 - y.t0);
+  });
+  p.d_tiles = dalloc<GemmTile>(p.tiles.size());
+  if (!p.terms.empty())
+    CK(cudaMemcpyAsync(p.d_terms, p.terms.data(), p.terms.size() * sizeof(GemmTerm), cudaMemcpyHostToDevice, stream));
+  if (!p.outs.empty())
+    CK(cudaMemcpyAsync(p.d_outs, p.outs.data(), p.outs.size() * sizeof(GemmOut), cudaMemcpyHostToDevice, stream));
+  if (!p.tiles.empty())
+    CK(cudaMemcpyAsync(p.d_tiles, p.tiles.data(), p.tiles.size() * sizeof(GemmTile), cudaMemcpyHostToDevice, stream));
+  sync();   // host vectors may be reused after return
+}
+
+void Engine::release(GemmPlan& p) {
+  dfree(p.d_terms);
+  dfree(p.d_outs);
+  dfree(p.d_tiles);
+  p.d_terms = nullptr;
+  p.d_outs = nullptr;
+  p.d_tiles = nullptr;
+}
+
+void Engine::upload(AxpyPlan& p) {
+  check(p);
+  p.d_terms = dalloc<AxpyTerm>(p.terms.size());
+  p.d_outs = dalloc<AxpyOut>(p.outs.size());
+  if (!p.terms.empty())
+    CK(cudaMemcpyAsync(p.d_terms, p.terms.data(), p.terms.size() * sizeof(AxpyTerm), cudaMemcpyHostToDevice, stream));
+  if (!p.outs.empty())
+    CK(cudaMemcpyAsync(p.d_outs, p.outs.data(), p.outs.size() * sizeof(AxpyOut), cudaMemcpyHostToDevice, stream));
+  sync();
+}
+
+void Engine::release(AxpyPlan& p) {
+  dfree(p.d_terms);
+  dfree(p.d_outs);
+  p.d_terms = nullptr;
+  p.d_outs = nullptr;
+}
+
+void Engine::run(GemmPlan& p) {
+  if (p.tiles.empty()) return;
+  launch_gemm_f64(p, stream);
+  stats.launches++;
+  CK(cudaGetLastError());
+}
+
+void Engine::run(AxpyPlan& p) {
+  if (p.outs.empty()) return;
+  launch_axpy(p, stream);
+  stats.launches++;
+  CK(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ layout helpers
+std::vector<std::pair<int, int>> Engine::bond_qs(const Bond& b) const {
+  std::vector<std::pair<int, int>> q;
+  for (int i = 0; i < b.nsec(); ++i) q.push_back({b.na[i], b.nb[i]});
+  return q;
+}
+
+Space Engine::left_space(const Bond& bl, const std::vector<std::pair<int, int>>& Qs) const {
+  Space sp;
+  for (auto& Q : Qs) {
+    std::array<int, 4> so, sq, sd;
+    int tot = 0;
+    for (int s = 0; s < 4; ++s) {
+      int i = bl.find(Q.first - QA[s], Q.second - QB[s]);
+      so[s] = i >= 0 ? tot : -1;
+      sq[s] = i;
+      sd[s] = i >= 0 ? bl.dim[i] : 0;
+      tot += sd[s];
+    }
+    sp.idx[qkey(Q.first, Q.second)] = sp.n();
+    sp.qa.push_back(Q.first);
+    sp.qb.push_back(Q.second);
+    sp.dim.push_back(tot);
+    sp.soff.push_back(so);
+    sp.ssec.push_back(sq);
+    sp.sdim.push_back(sd);
+  }
+  return sp;
+}
+
+Space Engine::right_space(const Bond& br, const std::vector<std::pair<int, int>>& Qs) const {
+  Space sp;
+  for (auto& Q : Qs) {
+    std::array<int, 4> so, sq, sd;
+    int tot = 0;
+    for (int s = 0; s < 4; ++s) {
+      int i = br.find(Q.first + QA[s], Q.second + QB[s]);
+      so[s] = i >= 0 ? tot : -1;
+      sq[s] = i;
+      sd[s] = i >= 0 ? br.dim[i] : 0;
+      tot += sd[s];
+    }
+    sp.idx[qkey(Q.first, Q.second)] = sp.n();
+    sp.qa.push_back(Q.first);
+    sp.qb.push_back(Q.second);
+    sp.dim.push_back(tot);
+    sp.soff.push_back(so);
+    sp.ssec.push_back(sq);
+    sp.sdim.push_back(sd);
+  }
+  return sp;
+}
+
+// site i between bonds i and i+1.  FL: per sector Q of bond i+1, a
+// (sum_s m_i(Q-s)) x m_{i+1}(Q) block.  FR: per sector q of bond i, a
+// m_i(q) x (sum_s m_{i+1}(q+s)) block.
+void Engine::layout_site(int i, int layout, Site& s) const {
+  s.layout = layout;
+  s.off.clear();
+  int64_t tot = 0;
+  if (layout == 0) {
+    const Bond& br = bonds[i + 1];
+    Space sp = left_space(bonds[i], bond_qs(br));
+    for (int j = 0; j < br.nsec(); ++j) {
+      s.off.push_back(tot);
+      tot += (int64_t)sp.dim[j] * br.dim[j];
+    }
+  } else {
+    const Bond& bl = bonds[i];
+    Space sp = right_space(bonds[i + 1], bond_qs(bl));
+    for (int j = 0; j < bl.nsec(); ++j) {
+      s.off.push_back(tot);
+      tot += (int64_t)bl.dim[j] * sp.dim[j];
+    }
+  }
+  s.size = tot;
+}
+
+void Engine::free_site(Site& s) {
+  if (s.d) dfree(s.d);
+  s.d = nullptr;
+  s.size = 0;
+}
+
+void Engine::free_env(Env& e) {
+  if (e.d) dfree(e.d);
+  e.d = nullptr;
+  e.size = 0;
+  e.valid = false;
+}
+
+void Engine::make_env(int bond, Env& e) {
+  free_env(e);
+  const Bond& b = bonds[bond];
+  e.nch = (int)mpo.labels[bond].size();
+  e.nsec = b.nsec();
+  e.off.assign((size_t)e.nch * e.nsec, -1);
+  e.rows.assign((size_t)e.nch * e.nsec, 0);
+  e.cols.assign((size_t)e.nch * e.nsec, 0);
+  int64_t tot = 0;
+  for (int a = 0; a < e.nch; ++a)
+    for (int q = 0; q < e.nsec; ++q) {
+      int qo = b.find(b.na[q] + mpo.dA[bond][a], b.nb[q] + mpo.dB[bond][a]);
+      if (qo < 0) continue;
+      size_t id = (size_t)a * e.nsec + q;
+      e.off[id] = tot;
+      e.rows[id] = b.dim[qo];
+      e.cols[id] = b.dim[q];
+      tot += (int64_t)b.dim[qo] * b.dim[q];
+    }
+  e.size = tot;
+  e.d = dalloc<double>(tot);
+  CK(cudaMemsetAsync(e.d, 0, tot * sizeof(double), stream));
+  e.valid = true;
+}
+
+// ------------------------------------------------------------------ enlarged operators
+namespace {
+struct TermKey {
+  int sec;
+  std::vector<std::pair<int, double>> t;
+  bool operator==(const TermKey& o) const { return sec == o.sec && t == o.t; }
+};
+struct TermKeyHash {
+  size_t operator()(const TermKey& k) const {
+    uint64_t h = 1469598103934665603ull ^ (uint64_t)k.sec;
+    for (auto& x : k.t) {
+      uint64_t v;
+      std::memcpy(&v, &x.second, 8);
+      h = (h ^ (uint64_t)x.first) * 1099511628211ull;
+      h = (h ^ v) * 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+}  // namespace
+
+// Lenl[b] over E_L(Q) (Q in el), from L_k and W_k.  Sub-block (b, Qin, sin,
+// sout) maps rows (q_l, sin) of E_L(Qin) to rows (q_l', sout) of E_L(Qout):
+//   sum_a W_k[a,b](sout, sin) L_k[a](q_l' <- q_l).
+// A single +-1 term aliases the environment block; other combinations are
+// formed once (shared between sub-blocks with proportional term lists).
+void Engine::build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPlan& ax) {
+  const Bond& bk = bonds[k];
+  const auto& W = mpo.W[k];
+  op.subs.clear();
+  op.own_size = 0;
+  std::unordered_map<TermKey, std::pair<int64_t, double>, TermKeyHash> combos;
+  size_t e0 = 0;
+  while (e0 < W.size()) {
+    int b = W[e0].b;
+    size_t e1 = e0;
+    while (e1 < W.size() && W[e1].b == b) ++e1;
+    // group by (sout, sin)
+    for (int so = 0; so < 4; ++so)
+      for (int si = 0; si < 4; ++si) {
+        std::vector<std::pair<int, double>> lst;
+        for (size_t e = e0; e < e1; ++e)
+          if (W[e].sout == so && W[e].sin == si) lst.push_back({W[e].a, W[e].v});
+        if (lst.empty()) continue;
+        int da = mpo.dA[k + 1][b] - (QA[so] - QA[si]);
+        int db = mpo.dB[k + 1][b] - (QB[so] - QB[si]);
+        for (int il = 0; il < bk.nsec(); ++il) {
+          int qin = el.find(bk.na[il] + QA[si], bk.nb[il] + QB[si]);
+          if (qin < 0) continue;
+          int ilp = bk.find(bk.na[il] + da, bk.nb[il] + db);
+          if (ilp < 0) continue;
+          int qout = el.find(bk.na[ilp] + QA[so], bk.nb[ilp] + QB[so]);
+          if (qout < 0) continue;
+          TermKey key;
+          key.sec = il;
+          for (auto& t : lst)
+            if (Lk.at(t.first, il) >= 0) key.t.push_back(t);
+          if (key.t.empty()) continue;
+          EnlSub sub{b, qin, si, qout, so, bk.dim[ilp], bk.dim[il], nullptr, -1, 1.0};
+          if (key.t.size() == 1 && std::fabs(key.t[0].second) == 1.0) {
+            sub.ptr = Lk.d + Lk.at(key.t[0].first, il);
+            sub.sign = key.t[0].second;
+          } else {
+            double sg = key.t[0].second < 0 ? -1.0 : 1.0;
+            for (auto& t : key.t) t.second *= sg;
+            auto it = combos.find(key);
+            if (it == combos.end()) {
+              int64_t len = (int64_t)sub.rows * sub.cols;
+              it = combos.emplace(key, std::make_pair(op.own_size, 1.0)).first;
+              AxpyOut o{nullptr, len, (int)ax.terms.size(), 0};
+              for (auto& t : key.t) ax.terms.push_back({Lk.d + Lk.at(t.first, il), t.second});
+              o.t1 = (int)ax.terms.size();
+              o.dst = (double*)(intptr_t)(op.own_size);   // resolved in finish_enl
+              ax.outs.push_back(o);
+              op.own_size += len;
+            }
+            sub.own_off = it->second.first;
+            sub.sign = sg;
+          }
+          op.subs.push_back(sub);
+        }
+      }
+    e0 = e1;
+  }
+}
+
+// Renl[b] over E_R(Q) (Q in er), from R_{i+1} and W_i (i = site).  Sub-block
+// (b, Qin, sin, sout) maps columns (sin, q_r) of E_R(Qin) to (sout, q_r') of
+// E_R(Qout):  sum_c W_i[b,c](sout, sin) R_{i+1}[c](q_r' <- q_r).
+void Engine::build_renl(int i, const Env& R, const Space& er, EnlOp& op, AxpyPlan& ax) {
+  const Bond& br = bonds[i + 1];
+  const auto& W = mpo.W[i];
+  op.subs.clear();
+  op.own_size = 0;
+  // entries sorted by b; regroup per b
+  std::unordered_map<TermKey, std::pair<int64_t, double>, TermKeyHash> combos;
+  // group the entries of W_i by their left channel (called b here)
+  std::map<int, std::vector<const MpoEntry*>> bya;
+  for (const auto& e : W) bya[e.a].push_back(&e);
+  for (auto& kv : bya) {
+    int b = kv.first;   // channel at bond i (left of site i)
+    for (int so = 0; so < 4; ++so)
+      for (int si = 0; si < 4; ++si) {
+        std::vector<std::pair<int, double>> lst;
+        for (const MpoEntry* e : kv.second)
+          if (e->sout == so && e->sin == si) lst.push_back({e->b, e->v});
+        if (lst.empty()) continue;
+        int dca = mpo.dA[i][b] + (QA[so] - QA[si]);
+        int dcb = mpo.dB[i][b] + (QB[so] - QB[si]);
+        for (int ir = 0; ir < br.nsec(); ++ir) {
+          int qin = er.find(br.na[ir] - QA[si], br.nb[ir] - QB[si]);
+          if (qin < 0) continue;
+          int irp = br.find(br.na[ir] + dca, br.nb[ir] + dcb);
+          if (irp < 0) continue;
+          int qout = er.find(br.na[irp] - QA[so], br.nb[irp] - QB[so]);
+          if (qout < 0) continue;
+          TermKey key;
+          key.sec = ir;
+          for (auto& t : lst)
+            if (R.at(t.first, ir) >= 0) key.t.push_back(t);
+          if (key.t.empty()) continue;
+          EnlSub sub{b, qin, si, qout, so, br.dim[irp], br.dim[ir], nullptr, -1, 1.0};
+          if (key.t.size() == 1 && std::fabs(key.t[0].second) == 1.0) {
+            sub.ptr = R.d + R.at(key.t[0].first, ir);
+            sub.sign = key.t[0].second;
+          } else {
+            double sg = key.t[0].second < 0 ? -1.0 : 1.0;
+            for (auto& t : key.t) t.second *= sg;
+            auto it = combos.find(key);
+            if (it == combos.end()) {
+              int64_t len = (int64_t)sub.rows * sub.cols;
+              it = combos.emplace(key, std::make_pair(op.own_size, 1.0)).first;
+              AxpyOut o{nullptr, len, (int)ax.terms.size(), 0};
+              for (auto& t : key.t) ax.terms.push_back({R.d + R.at(t.first, ir), t.second});
+              o.t1 = (int)ax.terms.size();
+              o.dst = (double*)(intptr_t)(op.own_size);
+              ax.outs.push_back(o);
+              op.own_size += len;
+            }
+            sub.own_off = it->second.first;
+            sub.sign = sg;
+          }
+          op.subs.push_back(sub);
+        }
+      }
+  }
+}
+
+void Engine::finish_enl(EnlOp& op, AxpyPlan& ax) {
+  op.own = dalloc<double>(op.own_size);
+  for (auto& o : ax.outs) o.dst = op.own + (intptr_t)o.dst;
+  for (auto& s : op.subs)
+    if (s.own_off >= 0) s.ptr = op.own + s.own_off;
+  upload(ax);
+  run(ax);
+  release(ax);
+  ax.clear();
+}
+
+void Engine::free_enl(EnlOp& op) {
+  if (op.own) dfree(op.own);
+  op.own = nullptr;
+  op.subs.clear();
+}
+
+// ------------------------------------------------------------------ environment updates
+// L_{k+1}[b](Qout <- Qin) = U_Qout^T (Lenl[b] U_Qin); U = A_k (fused-left).
+void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, const Bond& bnew, Env& out) {
+  int bond = (int)(&bnew - &bonds[0]);
+  make_env(bond, out);
+  // T_b(Qin) blocks: rows E_L(Qout), cols m_new(Qin)
+  std::map<std::pair<int, int>, std::vector<const EnlSub*>> groups;   // (b, qin) -> subs
+  for (const auto& s : lenl.subs) groups[{s.b, s.qin}].push_back(&s);
+  struct TB { int b, qin, qout, nin, nout; int64_t off; };
+  std::vector<TB> tbs;
+  int64_t tsize = 0;
+  for (auto& g : groups) {
+    int b = g.first.first, qin = g.first.second;
+    int jin = bnew.find(el.qa[qin], el.qb[qin]);
+    if (jin < 0) continue;
+    int qout = g.second[0]->qout;
+    int jout = bnew.find(el.qa[qout], el.qb[qout]);
+    if (jout < 0) continue;
+    tbs.push_back({b, qin, qout, jin, jout, tsize});
+    tsize += (int64_t)el.dim[qout] * bnew.dim[jin];
+  }
+  double* T = dalloc<double>(tsize);
+  GemmPlan p1, p2;
+  for (auto& tb : tbs) {
+    int nin = bnew.dim[tb.nin];
+    const auto& subs = groups[{tb.b, tb.qin}];
+    const double* U_in = A.d + A.off[tb.nin];
+    for (int so = 0; so < 4; ++so) {
+      if (el.soff[tb.qout][so] < 0) continue;
+      p1.add_out(T + tb.off + (int64_t)el.soff[tb.qout][so] * nin, nin, el.sdim[tb.qout][so], nin, 0);
+      for (const EnlSub* s : subs) {
+        if (s->sout != so) continue;
+        p1.add_term(s->ptr, s->cols, U_in + (int64_t)el.soff[tb.qin][s->sin] * nin, nin, s->cols, 0, s->sign);
+      }
+    }
+    int nout = bnew.dim[tb.nout];
+    int64_t eo = out.at(tb.b, tb.nin);
+    if (eo < 0) continue;
+    p2.add_out(out.d + eo, nin, nout, nin, 0);
+    p2.add_term(A.d + A.off[tb.nout], nout, T + tb.off, nin, el.dim[tb.qout], 1, 1.0);
+  }
+  CK(cudaEventRecord(ev0, stream));
+  upload(p1);
+  upload(p2);
+  run(p1);
+  run(p2);
+  CK(cudaEventRecord(ev1, stream));
+  sync();
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  stats.env_ms += ms;
+  stats.env_flops += p1.flops + p2.flops;
+  release(p1);
+  release(p2);
+  dfree(T);
+}
+
+// R_{k+1}[b](Qout <- Qin) = B_Qout (Renl[b] B_Qin^T); B fused-right.
+void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B, const Bond& bnew, Env& out) {
+  int bond = (int)(&bnew - &bonds[0]);
+  make_env(bond, out);
+  std::map<std::pair<int, int>, std::vector<const EnlSub*>> groups;
+  for (const auto& s : renl.subs) groups[{s.b, s.qin}].push_back(&s);
+  struct TB { int b, qin, qout, nin, nout; int64_t off; };
+  std::vector<TB> tbs;
+  int64_t tsize = 0;
+  for (auto& g : groups) {
+    int b = g.first.first, qin = g.first.second;
+    int jin = bnew.find(er.qa[qin], er.qb[qin]);
+    if (jin < 0) continue;
+    int qout = g.second[0]->qout;
+    int jout = bnew.find(er.qa[qout], er.qb[qout]);
+    if (jout < 0) continue;
+    tbs.push_back({b, qin, qout, jin, jout, tsize});
+    tsize += (int64_t)er.dim[qout] * bnew.dim[jin];
+  }
+  double* T = dalloc<double>(tsize);
+  GemmPlan p1, p2;
+  for (auto& tb : tbs) {
+    int nin = bnew.dim[tb.nin];
+    const auto& subs = groups[{tb.b, tb.qin}];
+    const double* B_in = B.d + B.off[tb.nin];   // nin x m_ER(qin)
+    for (int so = 0; so < 4; ++so) {
+      if (er.soff[tb.qout][so] < 0) continue;
+      p1.add_out(T + tb.off + (int64_t)er.soff[tb.qout][so] * nin, nin, er.sdim[tb.qout][so], nin, 0);
+      for (const EnlSub* s : subs) {
+        if (s->sout != so) continue;
+        p1.add_term(s->ptr, s->cols, B_in + er.soff[tb.qin][s->sin], er.dim[tb.qin], s->cols, 2, s->sign);
+      }
+    }
+    int nout = bnew.dim[tb.nout];
+    int64_t eo = out.at(tb.b, tb.nin);
+    if (eo < 0) continue;
+    p2.add_out(out.d + eo, nin, nout, nin, 0);
+    p2.add_term(B.d + B.off[tb.nout], er.dim[tb.qout], T + tb.off, nin, er.dim[tb.qout], 0, 1.0);
+  }
+  CK(cudaEventRecord(ev0, stream));
+  upload(p1);
+  upload(p2);
+  run(p1);
+  run(p2);
+  CK(cudaEventRecord(ev1, stream));
+  sync();
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  stats.env_ms += ms;
+  stats.env_flops += p1.flops + p2.flops;
+  release(p1);
+  release(p2);
+  dfree(T);
+}
+
+// ------------------------------------------------------------------ two-site state
+void Engine::setup_two_site(int k) {
+  const Bond& bk = bonds[k];
+  const Bond& bk2 = bonds[k + 2];
+  std::vector<std::pair<int, int>> cand;
+  for (int i = 0; i < bk.nsec(); ++i)
+    for (int s = 0; s < 4; ++s) cand.push_back({bk.na[i] + QA[s], bk.nb[i] + QB[s]});
+  std::sort(cand.begin(), cand.end(), [](auto& x, auto& y) { return qkey(x.first, x.second) < qkey(y.first, y.second); });
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  std::vector<std::pair<int, int>> Qs;
+  for (auto& Q : cand) {
+    bool r = false;
+    for (int s = 0; s < 4; ++s)
+      if (bk2.find(Q.first + QA[s], Q.second + QB[s]) >= 0) r = true;
+    if (r) Qs.push_back(Q);
+  }
+  EL = left_space(bk, Qs);
+  ER = right_space(bk2, Qs);
+  psi_off.assign(Qs.size() + 1, 0);
+  for (size_t i = 0; i < Qs.size(); ++i) psi_off[i + 1] = psi_off[i] + (int64_t)EL.dim[i] * ER.dim[i];
+  psi_size = psi_off.back();
+  if (psi) dfree(psi);
+  psi = dalloc<double>(psi_size);
+  cur_k = k;
+}
+
+// psi at (k, k+1) = sites[k] . sites[k+1] contracted over bond k+1.
+void Engine::form_psi(int k, int) {
+  const Site& X = sites[k];
+  const Site& Y = sites[k + 1];
+  const Bond& b1 = bonds[k + 1];
+  GemmPlan p;
+  for (int iq = 0; iq < EL.n(); ++iq) {
+    int Qa = EL.qa[iq], Qb = EL.qb[iq];
+    double* out = psi + psi_off[iq];
+    int mEL = EL.dim[iq], mER = ER.dim[iq];
+    if (X.layout == 0 && Y.layout == 1) {
+      int j = b1.find(Qa, Qb);
+      p.add_out(out, mER, mEL, mER, 0);
+      if (j >= 0) p.add_term(X.d + X.off[j], b1.dim[j], Y.d + Y.off[j], mER, b1.dim[j], 0, 1.0);
+    } else if (X.layout == 1 && Y.layout == 1) {
+      // center X fused-right over (bond k, bond k+1), B = Y over (bond k+1, bond k+2)
+      Space xr = right_space(b1, {});
+      int j = b1.find(Qa, Qb);
+      for (int s1 = 0; s1 < 4; ++s1) {
+        if (EL.soff[iq][s1] < 0) continue;
+        int iql = EL.ssec[iq][s1];
+        int mql = EL.sdim[iq][s1];
+        p.add_out(out + (int64_t)EL.soff[iq][s1] * mER, mER, mql, mER, 0);
+        if (j < 0) continue;
+        // column offset of (s1, Q) inside the fused-right block of q_l
+        const Bond& bk = bonds[k];
+        int coff = 0, xcols = 0;
+        for (int s = 0; s < 4; ++s) {
+          int jj = b1.find(bk.na[iql] + QA[s], bk.nb[iql] + QB[s]);
+          if (s < s1 && jj >= 0) coff += b1.dim[jj];
+          if (jj >= 0) xcols += b1.dim[jj];
+        }
+        p.add_term(X.d + X.off[iql] + coff, xcols, Y.d + Y.off[j], mER, b1.dim[j], 0, 1.0);
+      }
+      (void)xr;
+    } else if (X.layout == 0 && Y.layout == 0) {
+      // A = X fused-left over (bond k, bond k+1); center Y fused-left over (bond k+1, bond k+2)
+      const Bond& bk2 = bonds[k + 2];
+      for (int s2 = 0; s2 < 4; ++s2) {
+        if (ER.soff[iq][s2] < 0) continue;
+        int iqr = ER.ssec[iq][s2];
+        int mqr = ER.sdim[iq][s2];
+        p.add_out(out + ER.soff[iq][s2], mER, mEL, mqr, 0);
+        int j = b1.find(Qa, Qb);
+        if (j < 0) continue;
+        int roff = 0;
+        for (int s = 0; s < 4; ++s) {
+          int jj = b1.find(bk2.na[iqr] - QA[s], bk2.nb[iqr] - QB[s]);
+          if (s < s2 && jj >= 0) roff += b1.dim[jj];
+        }
+        p.add_term(X.d + X.off[j], b1.dim[j], Y.d + Y.off[iqr] + (int64_t)roff * mqr, mqr, b1.dim[j], 0, 1.0);
+      }
+    } else {
+      throw Error(-6, "inconsistent site layouts for the two-site state");
+    }
+  }
+  upload(p);
+  run(p);
+  release(p);
+}
+
+// ------------------------------------------------------------------ sigma
+struct Engine::Sigma {
+  EnlOp lenl, renl;
+  double* Y = nullptr;
+  double* in = nullptr;
+  double* out = nullptr;
+  GemmPlan A, B;
+};
+
+void Engine::plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg) {
+  // Y_b(Qin) exists when both operators have sub-blocks for (b, Qin)
+  std::map<std::pair<int, int>, std::vector<const EnlSub*>> rby, lby;
+  for (const auto& s : renl.subs) rby[{s.b, s.qin}].push_back(&s);
+  for (const auto& s : lenl.subs) lby[{s.b, s.qin}].push_back(&s);
+  std::map<std::pair<int, int>, int64_t> yoff;
+  int64_t ysize = 0;
+  std::vector<std::tuple<int, int, int>> ys;   // b, qin, qout
+  for (auto& kv : rby) {
+    if (!lby.count(kv.first)) continue;
+    int qin = kv.first.second;
+    int qout = kv.second[0]->qout;
+    yoff[kv.first] = ysize;
+    ys.push_back({kv.first.first, qin, qout});
+    ysize += (int64_t)EL.dim[qin] * ER.dim[qout];
+  }
+  sg.Y = dalloc<double>(ysize);
+  sg.in = dalloc<double>(psi_size);
+  sg.out = dalloc<double>(psi_size);
+  GemmPlan& A = sg.A;
+  GemmPlan& B = sg.B;
+  A.clear();
+  B.clear();
+  // stage A: Y_b(Qin)[:, cols (sout, q_r')] = sum psi(Qin)[:, cols (sin, q_r)] Rsub^T
+  for (auto& y : ys) {
+    int b = std::get<0>(y), qin = std::get<1>(y), qout = std::get<2>(y);
+    double* Yb = sg.Y + yoff[{b, qin}];
+    int ldy = ER.dim[qout];
+    const auto& subs = rby[{b, qin}];
+    for (int so = 0; so < 4; ++so) {
+      if (ER.soff[qout][so] < 0) continue;
+      A.add_out(Yb + ER.soff[qout][so], ldy, EL.dim[qin], ER.sdim[qout][so], 0);
+      for (const EnlSub* s : subs) {
+        if (s->sout != so) continue;
+        A.add_term(sg.in + psi_off[qin] + ER.soff[qin][s->sin], ER.dim[qin], s->ptr, s->cols, s->cols, 2, s->sign);
+      }
+    }
+  }
+  // stage B: sigma(Qout)[rows (q_l', sout), :] = sum Lsub Y_b(Qin)[rows (q_l, sin), :]
+  std::map<std::pair<int, int>, std::vector<const EnlSub*>> lout;
+  for (const auto& s : lenl.subs) lout[{s.qout, s.sout}].push_back(&s);
+  for (int q = 0; q < EL.n(); ++q)
+    for (int so = 0; so < 4; ++so) {
+      if (EL.soff[q][so] < 0) continue;
+      int ld = ER.dim[q];
+      B.add_out(sg.out + psi_off[q] + (int64_t)EL.soff[q][so] * ld, ld, EL.sdim[q][so], ld, 0);
+      auto it = lout.find({q, so});
+      if (it == lout.end()) continue;
+      for (const EnlSub* s : it->second) {
+        auto yo = yoff.find({s->b, s->qin});
+        if (yo == yoff.end()) continue;
+        B.add_term(s->ptr, s->cols, sg.Y + yo->second + (int64_t)EL.soff[s->qin][s->sin] * ld, ld, s->cols, 0,
+                   s->sign);
+      }
+    }
+  upload(A);
+  upload(B);
+}
+
+void Engine::sigma(Sigma& sg, const double* x, double* y) {
+  CK(cudaMemcpyAsync(sg.in, x, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  CK(cudaEventRecord(ev0, stream));
+  run(sg.A);
+  run(sg.B);
+  CK(cudaEventRecord(ev1, stream));
+  CK(cudaMemcpyAsync(y, sg.out, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  CK(cudaEventSynchronize(ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  stats.sigma_ms += ms;
+  stats.sigma_flops += sg.A.flops + sg.B.flops;
+  stats.n_sigma++;
+}
+
+// diag(Q)[i,j] = sum_{b: delta_b = 0} Lenl[b](i,i) Renl[b](j,j)
+void Engine::compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag) {
+  int mid = cur_k + 1;
+  std::vector<int> zc;   // channel -> column index
+  std::vector<int> col(mpo.labels[mid].size(), -1);
+  for (int b = 0; b < (int)mpo.labels[mid].size(); ++b)
+    if (mpo.dA[mid][b] == 0 && mpo.dB[mid][b] == 0) {
+      col[b] = (int)zc.size();
+      zc.push_back(b);
+    }
+  int nz = (int)zc.size();
+  std::vector<int64_t> dl_off(EL.n() + 1, 0), dr_off(EL.n() + 1, 0);
+  for (int q = 0; q < EL.n(); ++q) {
+    dl_off[q + 1] = dl_off[q] + (int64_t)EL.dim[q] * nz;
+    dr_off[q + 1] = dr_off[q] + (int64_t)nz * ER.dim[q];
+  }
+  double* DL = dalloc<double>(dl_off.back());
+  double* DR = dalloc<double>(dr_off.back());
+  CK(cudaMemsetAsync(DL, 0, dl_off.back() * sizeof(double), stream));
+  CK(cudaMemsetAsync(DR, 0, dr_off.back() * sizeof(double), stream));
+  // gathers expressed as 1-wide GEMMs would be wasteful; use strided axpy:
+  // each diagonal element is one 1x1 output of a GEMM with K=1 (A = element,
+  // B = 1).  Cheaper: copy via the axpy kernel on strided views is not
+  // supported, so gather on the device with tiny GEMMs of shape m x 1.
+  GemmPlan g;
+  static const double one = 1.0;
+  double* d_one = dalloc<double>(1);
+  CK(cudaMemcpyAsync(d_one, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  for (const auto& s : lenl.subs) {
+    if (s.qin != s.qout || s.sin != s.sout || col[s.b] < 0 || s.rows != s.cols) continue;
+    // column vector of the diagonal: rows r -> DL(q)[soff + r, col]
+    // express as M=rows, N=1, K=1 with A = diag elements (lda = cols+1), B = one
+    g.add_out(DL + dl_off[s.qin] + (int64_t)EL.soff[s.qin][s.sin] * nz + col[s.b], nz, s.rows, 1, 0);
+    g.add_term(s.ptr, s.cols + 1, d_one, 1, 1, 0, s.sign);
+  }
+  for (const auto& s : renl.subs) {
+    if (s.qin != s.qout || s.sin != s.sout || col[s.b] < 0 || s.rows != s.cols) continue;
+    // row vector: DR(q)[col, soff + r]: M=1, N=rows, K=1, A = one, B = diag (ldb = cols+1, transB)
+    g.add_out(DR + dr_off[s.qin] + (int64_t)col[s.b] * ER.dim[s.qin] + ER.soff[s.qin][s.sin], 1, 1, s.rows, 0);
+    g.add_term(d_one, 1, s.ptr, s.cols + 1, 1, 2, s.sign);
+  }
+  upload(g);
+  run(g);
+  release(g);
+  GemmPlan p;
+  for (int q = 0; q < EL.n(); ++q) {
+    p.add_out(diag + psi_off[q], ER.dim[q], EL.dim[q], ER.dim[q], 0);
+    if (nz > 0) p.add_term(DL + dl_off[q], nz, DR + dr_off[q], ER.dim[q], nz, 0, 1.0);
+  }
+  upload(p);
+  run(p);
+  release(p);
+  dfree(DL);
+  dfree(DR);
+  dfree(d_one);
+}
+
+// ------------------------------------------------------------------ Davidson
+// Davidson (ground state) on the two-site state: Rayleigh-Ritz in FP64 on
+// the host, vectors on the device; preconditioner t = -r / (diag - theta)
+// with |diag - theta| clamped to 1e-8; two classical Gram-Schmidt passes;
+// restart from the 4 lowest Ritz vectors when the space is full.
+double Engine::davidson(Sigma& sg, const double* diag, double tol, int max_iter, int max_space) {
+  const int64_t n = psi_size;
+  const int keep = 4;
+  double* V = dalloc<double>((size_t)max_space * n);
+  double* S = dalloc<double>((size_t)max_space * n);
+  double* Vt = dalloc<double>((size_t)keep * n);
+  double* St = dalloc<double>((size_t)keep * n);
+  double* x = dalloc<double>(n);
+  double* sx = dalloc<double>(n);
+  double* r = dalloc<double>(n);
+  double* t = dalloc<double>(n);
+  int nblk = reduction_blocks(n);
+  double* partial = dalloc<double>((size_t)nblk * (max_space + 1));
+  double* dots = dalloc<double>(max_space + 1);
+  double* coef = dalloc<double>((size_t)max_space * keep + max_space);
+  std::vector<double> Hs((size_t)max_space * max_space, 0.0), hd(max_space + 1);
+  auto d2h = [&](double* host, const double* dev, int cnt) {
+    CK(cudaMemcpyAsync(host, dev, cnt * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    sync();
+    stats.d2h += cnt * sizeof(double);
+  };
+  auto h2d = [&](double* dev, const double* host, int cnt) {
+    CK(cudaMemcpyAsync(dev, host, cnt * sizeof(double), cudaMemcpyHostToDevice, stream));
+    stats.h2d += cnt * sizeof(double);
+  };
+  auto dot_many = [&](const double* base, int k, const double* vec, double* host) {
+    launch_multi_dot(base, n, k, vec, n, dots, partial, nblk, stream);
+    stats.launches += 2;
+    d2h(host, dots, k);
+  };
+  // v0 = psi / |psi|
+  CK(cudaMemcpyAsync(V, psi, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  dot_many(V, 1, V, hd.data());
+  double nrm = std::sqrt(hd[0]);
+  if (!(nrm > 0)) throw Error(-4, "two-site guess vector has zero norm");
+  launch_scale(V, 1.0 / nrm, n, stream);
+  stats.launches++;
+  sigma(sg, V, S);
+  dot_many(V, 1, S, hd.data());
+  Hs[0] = hd[0];
+  int k = 1;
+  double theta = hd[0];
+  std::vector<double> w(max_space), Z((size_t)max_space * max_space), hk((size_t)max_space * max_space);
+  for (int it = 0;; ++it) {
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) hk[(size_t)i * k + j] = 0.5 * (Hs[(size_t)i * max_space + j] + Hs[(size_t)j * max_space + i]);
+    if (sym_eig(k, hk.data(), w.data(), Z.data()) != 0) throw Error(-4, "Rayleigh-Ritz eigensolver failed");
+    theta = w[0];
+    std::vector<double> c(k);
+    for (int i = 0; i < k; ++i) c[i] = Z[(size_t)i * k + 0];
+    h2d(coef, c.data(), k);
+    launch_lincomb(x, V, n, coef, k, n, 0, stream);
+    launch_lincomb(sx, S, n, coef, k, n, 0, stream);
+    launch_residual_precond(x, sx, diag, theta, n, r, t, partial, nblk, dots, stream);
+    stats.launches += 4;
+    double rr;
+    d2h(&rr, dots, 1);
+    double rn = std::sqrt(std::max(rr, 0.0));
+    if (rn < tol || it >= max_iter) break;
+    if (k == max_space) {
+      int kk = std::min(keep, k);
+      std::vector<double> cc((size_t)kk * k);
+      for (int j = 0; j < kk; ++j)
+        for (int i = 0; i < k; ++i) cc[(size_t)j * k + i] = Z[(size_t)i * k + j];
+      h2d(coef, cc.data(), kk * k);
+      for (int j = 0; j < kk; ++j) {
+        launch_lincomb(Vt + (size_t)j * n, V, n, coef + (size_t)j * k, k, n, 0, stream);
+        launch_lincomb(St + (size_t)j * n, S, n, coef + (size_t)j * k, k, n, 0, stream);
+        stats.launches += 2;
+      }
+      CK(cudaMemcpyAsync(V, Vt, (size_t)kk * n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      CK(cudaMemcpyAsync(S, St, (size_t)kk * n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      std::fill(Hs.begin(), Hs.end(), 0.0);
+      for (int j = 0; j < kk; ++j) Hs[(size_t)j * max_space + j] = w[j];
+      k = kk;
+    }
+    // orthogonalise t against V (two passes) and normalise
+    for (int pass = 0; pass < 2; ++pass) {
+      dot_many(V, k, t, hd.data());
+      for (int i = 0; i < k; ++i) hd[i] = -hd[i];
+      h2d(coef, hd.data(), k);
+      launch_lincomb(t, V, n, coef, k, n, 1, stream);
+      stats.launches++;
+    }
+    dot_many(t, 1, t, hd.data());
+    double tn = std::sqrt(std::max(hd[0], 0.0));
+    if (tn < 1e-14) break;
+    launch_scale(t, 1.0 / tn, n, stream);
+    stats.launches++;
+    CK(cudaMemcpyAsync(V + (size_t)k * n, t, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    sigma(sg, V + (size_t)k * n, S + (size_t)k * n);
+    dot_many(V, k + 1, S + (size_t)k * n, hd.data());
+    for (int i = 0; i <= k; ++i) {
+      Hs[(size_t)i * max_space + k] = hd[i];
+      Hs[(size_t)k * max_space + i] = hd[i];
+    }
+    ++k;
+  }
+  // psi <- normalised Ritz vector
+  dot_many(x, 1, x, hd.data());
+  CK(cudaMemcpyAsync(psi, x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  launch_scale(psi, 1.0 / std::sqrt(hd[0]), n, stream);
+  stats.launches++;
+  for (void* p : {(void*)V, (void*)S, (void*)Vt, (void*)St, (void*)x, (void*)sx, (void*)r, (void*)t, (void*)partial,
+                  (void*)dots, (void*)coef})
+    dfree(p);
+  return theta;
+}
+
+// ------------------------------------------------------------------ decimation
+// Keep the M largest sigma^2 over all sectors (after dropping sigma^2 <=
+// cutoff); equal values ordered by (sector, in-sector rank); a cluster of
+// weights within `tie` of each other is never split at the cut.
+void Engine::truncate(int k, int dir, int M, double* tau_out, std::vector<double>* kept_out) {
+  const int nq = EL.n();
+  std::vector<int64_t> roff(nq + 1, 0);
+  std::vector<int> md(nq);
+  for (int q = 0; q < nq; ++q) {
+    md[q] = dir == 0 ? EL.dim[q] : ER.dim[q];
+    roff[q + 1] = roff[q] + (int64_t)md[q] * md[q];
+  }
+  double* rho = dalloc<double>(roff.back());
+  GemmPlan p;
+  for (int q = 0; q < nq; ++q) {
+    const double* P = psi + psi_off[q];
+    p.add_out(rho + roff[q], md[q], md[q], md[q], 0);
+    if (dir == 0) p.add_term(P, ER.dim[q], P, ER.dim[q], ER.dim[q], 2, 1.0);
+    else p.add_term(P, ER.dim[q], P, ER.dim[q], EL.dim[q], 1, 1.0);
+  }
+  upload(p);
+  run(p);
+  release(p);
+  std::vector<double> h_rho(roff.back());
+  CK(cudaMemcpyAsync(h_rho.data(), rho, roff.back() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  stats.d2h += roff.back() * sizeof(double);
+  dfree(rho);
+  std::vector<std::vector<double>> ew(nq), ev(nq);
+  std::atomic<int> fail(0);
+  parallel_for(nq, [&](int q) {
+    int m = md[q];
+    ew[q].resize(m);
+    ev[q].resize((size_t)m * m);
+    if (sym_eig(m, h_rho.data() + roff[q], ew[q].data(), ev[q].data()) != 0) fail = 1;
+  });
+  if (fail) throw Error(-4, "density-matrix eigensolver failed");
+  std::vector<Weight> all;
+  for (int q = 0; q < nq; ++q) {
+    int m = md[q];
+    for (int j = 0; j < m; ++j) all.push_back({ew[q][m - 1 - j], qkey(EL.qa[q], EL.qb[q]), q, j});
+  }
+  double total = 0, kept_sum = 0;
+  std::vector<Weight> kw = select_states(all, M, sched.cutoff, sched.tie, &total);
+  std::vector<int> nkeep(nq, 0);
+  for (auto& w : kw) {
+    nkeep[w.idx]++;
+    kept_sum += w.lam;
+    if (kept_out) kept_out->push_back(w.lam);
+  }
+  double tau = total - kept_sum;
+  if (tau_out) *tau_out = tau;
+  stats.max_discarded = std::max(stats.max_discarded, tau);
+  // new bond k+1
+  Bond nb;
+  std::vector<int> qmap;   // new sector -> two-site sector index
+  for (int q = 0; q < nq; ++q)
+    if (nkeep[q] > 0) {
+      nb.na.push_back(EL.qa[q]);
+      nb.nb.push_back(EL.qb[q]);
+      nb.dim.push_back(nkeep[q]);
+    }
+  nb.finalize();
+  for (int j = 0; j < nb.nsec(); ++j) qmap.push_back(EL.find(nb.na[j], nb.nb[j]));
+  bonds[k + 1] = nb;
+  // basis matrices
+  Site U;
+  int which = dir == 0 ? k : k + 1;
+  free_site(sites[which]);
+  layout_site(which, dir == 0 ? 0 : 1, U);
+  std::vector<double> hU(U.size);
+  for (int j = 0; j < nb.nsec(); ++j) {
+    int q = qmap[j], m = md[q], nkq = nb.dim[j];
+    double* dst = hU.data() + U.off[j];
+    for (int c = 0; c < nkq; ++c)
+      for (int i = 0; i < m; ++i) {
+        double v = ev[q][(size_t)i * m + (m - 1 - c)];
+        if (dir == 0) dst[(size_t)i * nkq + c] = v;   // U: m_EL x nk
+        else dst[(size_t)c * m + i] = v;              // B = V^T: nk x m_ER
+      }
+  }
+  U.d = dalloc<double>(U.size);
+  CK(cudaMemcpyAsync(U.d, hU.data(), U.size * sizeof(double), cudaMemcpyHostToDevice, stream));
+  stats.h2d += U.size * sizeof(double);
+  sites[which] = U;
+  // center = U^T psi (L->R, site k+1 fused-right) or psi B^T (R->L, site k fused-left)
+  int cw = dir == 0 ? k + 1 : k;
+  free_site(sites[cw]);
+  Site C;
+  layout_site(cw, dir == 0 ? 1 : 0, C);
+  C.d = dalloc<double>(C.size);
+  GemmPlan pc;
+  for (int j = 0; j < nb.nsec(); ++j) {
+    int q = qmap[j], nkq = nb.dim[j];
+    const double* P = psi + psi_off[q];
+    if (dir == 0) {
+      pc.add_out(C.d + C.off[j], ER.dim[q], nkq, ER.dim[q], 0);
+      pc.add_term(U.d + U.off[j], nkq, P, ER.dim[q], EL.dim[q], 1, 1.0);
+    } else {
+      pc.add_out(C.d + C.off[j], nkq, EL.dim[q], nkq, 0);
+      pc.add_term(P, ER.dim[q], U.d + U.off[j], ER.dim[q], ER.dim[q], 2, 1.0);
+    }
+  }
+  upload(pc);
+  run(pc);
+  release(pc);
+  sites[cw] = C;
+  sync();
+}
+
+// ------------------------------------------------------------------ one step
+double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept) {
+  double t0 = now_ms();
+  setup_two_site(k);
+  form_psi(k, 0);
+  Sigma sg;
+  AxpyPlan ax;
+  double te = now_ms();
+  build_lenl(k, Lenv[k], EL, sg.lenl, ax);
+  finish_enl(sg.lenl, ax);
+  build_renl(k + 1, Renv[k + 2], ER, sg.renl, ax);
+  finish_enl(sg.renl, ax);
+  sync();
+  stats.enl_ms += now_ms() - te;
+  plan_sigma(sg.lenl, sg.renl, sg);
+  double* diag = dalloc<double>(psi_size);
+  compute_diag(sg.lenl, sg.renl, diag);
+  double td = now_ms();
+  double theta = davidson(sg, diag, tol, sched.max_iter, sched.max_space);
+  stats.davidson_ms += now_ms() - td;
+  dfree(diag);
+  release(sg.A);
+  release(sg.B);
+  dfree(sg.Y);
+  dfree(sg.in);
+  dfree(sg.out);
+  double tt = now_ms();
+  truncate(k, dir, M, tau, kept);
+  stats.trunc_ms += now_ms() - tt;
+  // environment update on the side the sweep moves away from
+  if (dir == 0) {
+    Space el2 = EL;
+    env_update_left(sg.lenl, el2, sites[k], bonds[k + 1], Lenv[k + 1]);
+    Renv[k + 1].valid = false;
+  } else {
+    env_update_right(sg.renl, ER, sites[k + 1], bonds[k + 1], Renv[k + 1]);
+    Lenv[k + 1].valid = false;
+  }
+  free_enl(sg.lenl);
+  free_enl(sg.renl);
+  sync();
+  stats.n_steps++;
+  stats.step_ms += now_ms() - t0;
+  return theta;
+}
+
+// ------------------------------------------------------------------ initial MPS
+void Engine::init_mps(uint64_t seed, int M) {
+  bonds = initial_bond_dims(n, Na, Nb, M);
+  // fused-right host tensors with counter-based entries
+  std::vector<std::vector<double>> hs(n);
+  std::vector<Site> lay(n);
+  for (int i = 0; i < n; ++i) {
+    layout_site(i, 1, lay[i]);
+    hs[i].assign(lay[i].size, 0.0);
+    const Bond& bl = bonds[i];
+    const Bond& br = bonds[i + 1];
+    for (int j = 0; j < bl.nsec(); ++j) {
+      int cols = 0;
+      int coff[4];
+      for (int s = 0; s < 4; ++s) {
+        int r = br.find(bl.na[j] + QA[s], bl.nb[j] + QB[s]);
+        coff[s] = r >= 0 ? cols : -1;
+        if (r >= 0) cols += br.dim[r];
+      }
+      for (int s = 0; s < 4; ++s) {
+        if (coff[s] < 0) continue;
+        int r = br.find(bl.na[j] + QA[s], bl.nb[j] + QB[s]);
+        for (int row = 0; row < bl.dim[j]; ++row)
+          for (int col = 0; col < br.dim[r]; ++col)
+            hs[i][lay[i].off[j] + (int64_t)row * cols + coff[s] + col] =
+                mps_init_value(seed, i, bl.na[j], bl.nb[j], s, row, col);
+      }
+    }
+  }
+  // right-canonicalise sites n-1 .. 1; absorb the triangular factor leftwards
+  for (int i = n - 1; i >= 1; --i) {
+    const Bond& bl = bonds[i];
+    const Bond& bp = bonds[i - 1];
+    for (int j = 0; j < bl.nsec(); ++j) {
+      int m = bl.dim[j];
+      int cols = (int)((j + 1 < bl.nsec() ? lay[i].off[j + 1] : lay[i].size) - lay[i].off[j]) / m;
+      std::vector<double> Lo((size_t)m * m);
+      if (row_orthonormalize(m, cols, hs[i].data() + lay[i].off[j], Lo.data()) != 0)
+        throw Error(-4, "initial MPS is rank deficient");
+      for (int jp = 0; jp < bp.nsec(); ++jp) {
+        int coff = 0, pcols = 0, s_hit = -1, hit_off = 0;
+        for (int s = 0; s < 4; ++s) {
+          int r = bl.find(bp.na[jp] + QA[s], bp.nb[jp] + QB[s]);
+          if (r < 0) continue;
+          if (r == j) { s_hit = s; hit_off = coff; }
+          coff += bl.dim[r];
+        }
+        pcols = coff;
+        if (s_hit < 0) continue;
+        int mp = bp.dim[jp];
+        double* base = hs[i - 1].data() + lay[i - 1].off[jp];
+        std::vector<double> tmp((size_t)mp * m);
+        for (int rr = 0; rr < mp; ++rr)
+          for (int c = 0; c < m; ++c) {
+            double s = 0;
+            for (int t = 0; t < m; ++t) s += base[(size_t)rr * pcols + hit_off + t] * Lo[(size_t)t * m + c];
+            tmp[(size_t)rr * m + c] = s;
+          }
+        for (int rr = 0; rr < mp; ++rr)
+          for (int c = 0; c < m; ++c) base[(size_t)rr * pcols + hit_off + c] = tmp[(size_t)rr * m + c];
+      }
+    }
+  }
+  double nrm = 0;
+  for (double v : hs[0]) nrm += v * v;
+  nrm = std::sqrt(nrm);
+  for (double& v : hs[0]) v /= nrm;
+  for (auto& s : sites) free_site(s);
+  sites.assign(n, Site());
+  for (int i = 0; i < n; ++i) {
+    sites[i] = lay[i];
+    sites[i].d = dalloc<double>(lay[i].size);
+    CK(cudaMemcpyAsync(sites[i].d, hs[i].data(), lay[i].size * sizeof(double), cudaMemcpyHostToDevice, stream));
+    stats.h2d += lay[i].size * sizeof(double);
+  }
+  sync();
+}
+
+void Engine::build_right_envs(int from_k) {
+  // R_n = 1 on channel H; R_i = B_i Renl_i B_i^T for i = n-1 .. from_k
+  for (auto& e : Renv) free_env(e);
+  Renv.assign(n + 1, Env());
+  make_env(n, Renv[n]);
+  {
+    double one = 1.0;
+    int64_t o = Renv[n].at(mpo.ham_channel[n], 0);
+    CK(cudaMemcpyAsync(Renv[n].d + o, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+    sync();
+  }
+  for (int i = n - 1; i >= from_k; --i) {
+    Space er = right_space(bonds[i + 1], bond_qs(bonds[i]));
+    EnlOp op;
+    AxpyPlan ax;
+    build_renl(i, Renv[i + 1], er, op, ax);
+    finish_enl(op, ax);
+    env_update_right(op, er, sites[i], bonds[i], Renv[i]);
+    free_enl(op);
+  }
+}
+
+void Engine::build_left_envs(int to_k) {
+  for (auto& e : Lenv) free_env(e);
+  Lenv.assign(n + 1, Env());
+  make_env(0, Lenv[0]);
+  double one = 1.0;
+  int64_t o = Lenv[0].at(mpo.ident_channel[0], 0);
+  CK(cudaMemcpyAsync(Lenv[0].d + o, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  sync();
+  for (int i = 0; i < to_k; ++i) {
+    Space el = left_space(bonds[i], bond_qs(bonds[i + 1]));
+    EnlOp op;
+    AxpyPlan ax;
+    build_lenl(i, Lenv[i], el, op, ax);
+    finish_enl(op, ax);
+    env_update_left(op, el, sites[i], bonds[i + 1], Lenv[i + 1]);
+    free_enl(op);
+  }
+}
+
+// ------------------------------------------------------------------ public driver
+void Engine::prepare(int n_, int n_elec, int two_sz, int n_chol, const double* h_, const double* chol,
+                     double e_core_, const Schedule& sch) {
+  CK(cudaSetDevice(device));
+  n = n_;
+  Na = (n_elec + two_sz) / 2;
+  Nb = (n_elec - two_sz) / 2;
+  e_core = e_core_;
+  sched = sch;
+  h.assign(h_, h_ + (size_t)n * n);
+  eri.assign((size_t)n * n * n * n, 0.0);
+  for (int Q = 0; Q < n_chol; ++Q) {
+    const double* L = chol + (size_t)Q * n * n;
+    for (int pq = 0; pq < n * n; ++pq) {
+      double v = L[pq];
+      if (v == 0.0) continue;
+      double* row = eri.data() + (size_t)pq * n * n;
+      for (int rs = 0; rs < n * n; ++rs) row[rs] += v * L[rs];
+    }
+  }
+  build_mpo(n, h.data(), eri.data(), n / 2, mpo);
+  stats = Stats();
+  sweep_E.clear();
+  prepared = false;
+}
+
+void Engine::init_state() {
+  init_mps(sched.seed, sched.M.empty() ? 1 : sched.M[0]);
+  build_right_envs(2);
+  build_left_envs(0);
+  prepared = true;
+}
+
+double Engine::sweep(int s) {
+  if (!prepared) throw Error(-6, "sweep before prepare");
+  int M = sched.M[s];
+  double tol = sched.tol[s];
+  double e = 0;
+  for (int k = 0; k <= n - 2; ++k) e = step(k, 0, M, tol, nullptr, nullptr);
+  for (int k = n - 2; k >= 0; --k) e = step(k, 1, M, tol, nullptr, nullptr);
+  sweep_E.push_back(e);
+  return e;
+}
+
+// <psi|H|psi> / <psi|psi> at bond (0,1) of the current MPS
+double Engine::final_energy() {
+  setup_two_site(0);
+  form_psi(0, 0);
+  Sigma sg;
+  AxpyPlan ax;
+  build_lenl(0, Lenv[0], EL, sg.lenl, ax);
+  finish_enl(sg.lenl, ax);
+  build_renl(1, Renv[2], ER, sg.renl, ax);
+  finish_enl(sg.renl, ax);
+  plan_sigma(sg.lenl, sg.renl, sg);
+  double* y = dalloc<double>(psi_size);
+  sigma(sg, psi, y);
+  int nblk = reduction_blocks(psi_size);
+  double* partial = dalloc<double>(nblk * 2);
+  double* dots = dalloc<double>(2);
+  double hv[2];
+  launch_multi_dot(psi, psi_size, 1, y, psi_size, dots, partial, nblk, stream);
+  launch_multi_dot(psi, psi_size, 1, psi, psi_size, dots + 1, partial + nblk, nblk, stream);
+  CK(cudaMemcpyAsync(hv, dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  release(sg.A);
+  release(sg.B);
+  for (void* p : {(void*)sg.Y, (void*)sg.in, (void*)sg.out, (void*)y, (void*)partial, (void*)dots}) dfree(p);
+  free_enl(sg.lenl);
+  free_enl(sg.renl);
+  return hv[0] / hv[1];
+}
+
+// ------------------------------------------------------------------ test hooks
+void Engine::bond_sectors(int bond, std::vector<int>& out) const {
+  out.clear();
+  const Bond& b = bonds[bond];
+  for (int i = 0; i < b.nsec(); ++i) {
+    out.push_back(b.na[i]);
+    out.push_back(b.nb[i]);
+    out.push_back(b.dim[i]);
+  }
+}
+
+std::vector<uint64_t> Engine::mpo_labels(int bond) const {
+  std::vector<uint64_t> v;
+  for (auto& l : mpo.labels[bond]) v.push_back(l.key());
+  return v;
+}
+
+// canonical block order per site i: for q_l in bond i (sorted), s = 0..3,
+// q_r = q_l + s in bond i+1: a m_i(q_l) x m_{i+1}(q_r) row-major block
+void Engine::set_mps(const int* nsec, const int* sectors, const double* data, int center) {
+  bonds.assign(n + 1, Bond());
+  int pos = 0;
+  for (int k = 0; k <= n; ++k) {
+    for (int j = 0; j < nsec[k]; ++j) {
+      bonds[k].na.push_back(sectors[pos++]);
+      bonds[k].nb.push_back(sectors[pos++]);
+      bonds[k].dim.push_back(sectors[pos++]);
+    }
+    bonds[k].finalize();
+  }
+  for (auto& s : sites) free_site(s);
+  sites.assign(n, Site());
+  int64_t dpos = 0;
+  for (int i = 0; i < n; ++i) {
+    int layout = i < center ? 0 : 1;
+    Site s;
+    layout_site(i, layout, s);
+    std::vector<double> hs(s.size, 0.0);
+    const Bond& bl = bonds[i];
+    const Bond& br = bonds[i + 1];
+    for (int j = 0; j < bl.nsec(); ++j)
+      for (int st = 0; st < 4; ++st) {
+        int r = br.find(bl.na[j] + QA[st], bl.nb[j] + QB[st]);
+        if (r < 0) continue;
+        int ml = bl.dim[j], mr = br.dim[r];
+        if (layout == 0) {
+          // FL block of sector r: rows concat_s (q_r - s); our rows start at soff(st)
+          int roff = 0, rows = 0;
+          for (int s2 = 0; s2 < 4; ++s2) {
+            int jj = bl.find(br.na[r] - QA[s2], br.nb[r] - QB[s2]);
+            if (jj < 0) continue;
+            if (s2 < st) roff += bl.dim[jj];
+            rows += bl.dim[jj];
+          }
+          double* dst = hs.data() + s.off[r] + (int64_t)roff * mr;
+          for (int a = 0; a < ml; ++a)
+            for (int c = 0; c < mr; ++c) dst[(size_t)a * mr + c] = data[dpos + (int64_t)a * mr + c];
+        } else {
+          int coff = 0, cols = 0;
+          for (int s2 = 0; s2 < 4; ++s2) {
+            int rr = br.find(bl.na[j] + QA[s2], bl.nb[j] + QB[s2]);
+            if (rr < 0) continue;
+            if (s2 < st) coff += br.dim[rr];
+            cols += br.dim[rr];
+          }
+          double* dst = hs.data() + s.off[j] + coff;
+          for (int a = 0; a < ml; ++a)
+            for (int c = 0; c < mr; ++c) dst[(size_t)a * cols + c] = data[dpos + (int64_t)a * mr + c];
+        }
+        dpos += (int64_t)ml * mr;
+      }
+    s.d = dalloc<double>(s.size);
+    CK(cudaMemcpyAsync(s.d, hs.data(), s.size * sizeof(double), cudaMemcpyHostToDevice, stream));
+    sync();
+    sites[i] = s;
+  }
+  build_right_envs(center + 2);
+  build_left_envs(center);
+  prepared = true;
+}
+
+int64_t Engine::two_site_size(int k) {
+  setup_two_site(k);
+  return psi_size;
+}
+
+// psi in the canonical two-site order: for q_l in bond k (sorted), s1, s2 with
+// q_r = q_l + s1 + s2 in bond k+2: a m_k(q_l) x m_{k+2}(q_r) block
+void Engine::apply_heff(int k, const double* in, double* out, double* diag_out) {
+  setup_two_site(k);
+  const Bond& bk = bonds[k];
+  const Bond& bk2 = bonds[k + 2];
+  struct Map { int64_t src, dst; int rows, cols, ld; };
+  std::vector<Map> maps;
+  int64_t pos = 0;
+  for (int j = 0; j < bk.nsec(); ++j)
+    for (int s1 = 0; s1 < 4; ++s1)
+      for (int s2 = 0; s2 < 4; ++s2) {
+        int r = bk2.find(bk.na[j] + QA[s1] + QA[s2], bk.nb[j] + QB[s1] + QB[s2]);
+        if (r < 0) continue;
+        int q = EL.find(bk.na[j] + QA[s1], bk.nb[j] + QB[s1]);
+        int ml = bk.dim[j], mr = bk2.dim[r];
+        int ld = ER.dim[q];
+        maps.push_back({pos, psi_off[q] + (int64_t)EL.soff[q][s1] * ld + ER.soff[q][s2], ml, mr, ld});
+        pos += (int64_t)ml * mr;
+      }
+  std::vector<double> hp(psi_size, 0.0);
+  for (auto& m : maps)
+    for (int a = 0; a < m.rows; ++a)
+      for (int c = 0; c < m.cols; ++c) hp[m.dst + (int64_t)a * m.ld + c] = in[m.src + (int64_t)a * m.cols + c];
+  CK(cudaMemcpyAsync(psi, hp.data(), psi_size * sizeof(double), cudaMemcpyHostToDevice, stream));
+  Sigma sg;
+  AxpyPlan ax;
+  build_lenl(k, Lenv[k], EL, sg.lenl, ax);
+  finish_enl(sg.lenl, ax);
+  build_renl(k + 1, Renv[k + 2], ER, sg.renl, ax);
+  finish_enl(sg.renl, ax);
+  plan_sigma(sg.lenl, sg.renl, sg);
+  double* y = dalloc<double>(psi_size);
+  sigma(sg, psi, y);
+  std::vector<double> hy(psi_size);
+  CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  for (auto& m : maps)
+    for (int a = 0; a < m.rows; ++a)
+      for (int c = 0; c < m.cols; ++c) out[m.src + (int64_t)a * m.cols + c] = hy[m.dst + (int64_t)a * m.ld + c];
+  if (diag_out) {
+    compute_diag(sg.lenl, sg.renl, y);
+    CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    sync();
+    for (auto& m : maps)
+      for (int a = 0; a < m.rows; ++a)
+        for (int c = 0; c < m.cols; ++c) diag_out[m.src + (int64_t)a * m.cols + c] = hy[m.dst + (int64_t)a * m.ld + c];
+  }
+  release(sg.A);
+  release(sg.B);
+  for (void* p : {(void*)sg.Y, (void*)sg.in, (void*)sg.out, (void*)y}) dfree(p);
+  free_enl(sg.lenl);
+  free_enl(sg.renl);
+  sync();
+}
+
+double Engine::run_step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept) {
+  return step(k, dir, M, tol, tau, kept);
+}
+
+void Engine::env_block(int side, int bond, int ch, int sec, std::vector<double>& out, int& rows, int& cols) {
+  const Env& e = side == 0 ? Lenv[bond] : Renv[bond];
+  if (!e.valid) throw Error(-6, "environment not built at this bond");
+  int64_t o = e.at(ch, sec);
+  if (o < 0) { rows = cols = 0; out.clear(); return; }
+  rows = e.rows[(size_t)ch * e.nsec + sec];
+  cols = e.cols[(size_t)ch * e.nsec + sec];
+  out.resize((size_t)rows * cols);
+  CK(cudaMemcpyAsync(out.data(), e.d + o, out.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+}
+
+}  // namespace gbd
+
+namespace gbd {
+void Engine::rdms(double*, double*) { throw Error(-6, "RDMs are not built in this library yet"); }
+}  // namespace gbd

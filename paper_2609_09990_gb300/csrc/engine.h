@@ -1,0 +1,169 @@
+// Sweep engine: the host-side planner and driver of the device kernels.
+#pragma once
+
+#include <array>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "gbd_internal.h"
+
+namespace gbd {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+// Enlarged space over a list of sectors Q: E_L(Q) = concat_s (Q - s) from a
+// left bond, or E_R(Q) = concat_s (Q + s) from a right bond.
+struct Space {
+  std::vector<int> qa, qb, dim;
+  std::vector<std::array<int, 4>> soff, ssec, sdim;
+  std::unordered_map<int, int> idx;
+  int find(int a, int b) const {
+    if (a < 0 || b < 0 || a > 63 || b > 63) return -1;
+    auto it = idx.find(qkey(a, b));
+    return it == idx.end() ? -1 : it->second;
+  }
+  int n() const { return (int)qa.size(); }
+};
+
+struct Env {          // operator blocks (channel, q_in) of one bond
+  int nch = 0, nsec = 0;
+  std::vector<int64_t> off;   // nch * nsec, -1 if absent
+  std::vector<int> rows, cols;
+  double* d = nullptr;
+  int64_t size = 0;
+  bool valid = false;
+  int64_t at(int ch, int sec) const { return off[(size_t)ch * nsec + sec]; }
+};
+
+struct EnlSub {       // one sub-block of an enlarged operator
+  int b, qin, sin, qout, sout, rows, cols;
+  const double* ptr;
+  int64_t own_off;    // >= 0: offset into the owned buffer (resolved later)
+  double sign;
+};
+struct EnlOp {
+  std::vector<EnlSub> subs;
+  double* own = nullptr;
+  int64_t own_size = 0;
+};
+
+struct Site {         // device tensor of one site; layout 0 = fused-left, 1 = fused-right
+  double* d = nullptr;
+  int64_t size = 0;
+  int layout = 1;
+  std::vector<int64_t> off;   // per sector of the key bond (right bond for FL, left bond for FR)
+};
+
+struct Weight { double lam; int key, idx, j; };
+std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, double tie, double* total);
+std::vector<Bond> initial_bond_dims(int n, int Na, int Nb, int M);
+
+struct Stats {
+  double sigma_flops = 0, sigma_ms = 0, env_flops = 0, env_ms = 0, enl_ms = 0, step_ms = 0;
+  double trunc_ms = 0, davidson_ms = 0;
+  int64_t n_sigma = 0, n_steps = 0, launches = 0, h2d = 0, d2h = 0;
+  double max_discarded = 0;
+};
+
+struct Schedule {
+  std::vector<int> M;
+  std::vector<double> tol;
+  int max_iter = 100, max_space = 24, precision = 0, precond = 0;
+  uint64_t seed = 1;
+  double cutoff = 1e-12, tie = 1e-10;
+};
+
+class Engine {
+ public:
+  explicit Engine(int device);
+  ~Engine();
+  void prepare(int n, int n_elec, int two_sz, int n_chol, const double* h, const double* chol,
+               double e_core, const Schedule& sch);
+  void init_state();       // initial MPS and environments
+  double sweep(int s);     // returns the Ritz value of the last step
+  double final_energy();
+  void rdms(double* rdm1, double* rdm2);
+  // debug / test hooks
+  void set_mps(const int* nsec, const int* sectors, const double* data, int center);
+  int64_t two_site_size(int k);
+  void apply_heff(int k, const double* in, double* out, double* diag_out);
+  double run_step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept);
+  void bond_sectors(int bond, std::vector<int>& out) const;
+  int mpo_bond_dim(int bond) const { return (int)mpo.labels[bond].size(); }
+  std::vector<uint64_t> mpo_labels(int bond) const;
+  void env_block(int side, int bond, int channel, int sector, std::vector<double>& out, int& rows, int& cols);
+
+  Stats stats;
+  std::vector<double> sweep_E;
+  int n = 0, Na = 0, Nb = 0;
+  double e_core = 0;
+  Schedule sched;
+  bool prepared = false;
+
+ private:
+  int device;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<double> h, eri;
+  Mpo mpo;
+  std::vector<Bond> bonds;
+  std::vector<Site> sites;
+  std::vector<Env> Lenv, Renv;
+
+  // ---- current two-site step state
+  int cur_k = -1;
+  Space EL, ER;
+  std::vector<int64_t> psi_off;
+  int64_t psi_size = 0;
+  double* psi = nullptr;
+
+  std::map<uintptr_t, size_t> allocs;   // live device allocations (base -> bytes)
+  template <class T> T* dalloc(size_t n);
+  void check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, const char* what) const;
+  void check(const GemmPlan& p) const;
+  void check(const AxpyPlan& p) const;
+  void dfree(void* p);
+  void upload(GemmPlan& p);
+  void release(GemmPlan& p);
+  void upload(AxpyPlan& p);
+  void release(AxpyPlan& p);
+  void run(GemmPlan& p);
+  void run(AxpyPlan& p);
+  void sync();
+
+  void free_env(Env& e);
+  void make_env(int bond, Env& e);
+  Space left_space(const Bond& bl, const std::vector<std::pair<int, int>>& Qs) const;
+  Space right_space(const Bond& br, const std::vector<std::pair<int, int>>& Qs) const;
+  std::vector<std::pair<int, int>> bond_qs(const Bond& b) const;
+  void layout_site(int i, int layout, Site& s) const;
+  void free_site(Site& s);
+  void build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPlan& ax);
+  void build_renl(int i, const Env& Ri1, const Space& er, EnlOp& op, AxpyPlan& ax);
+  void finish_enl(EnlOp& op, AxpyPlan& ax);
+  void free_enl(EnlOp& op);
+  void env_update_left(const EnlOp& lenl, const Space& el, const Site& A, const Bond& bnew, Env& out);
+  void env_update_right(const EnlOp& renl, const Space& er, const Site& B, const Bond& bnew, Env& out);
+  void setup_two_site(int k);
+  void form_psi(int k, int pattern);
+  struct Sigma;
+  void plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg);
+  void sigma(Sigma& sg, const double* x, double* y);
+  void compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag);
+  double davidson(Sigma& sg, const double* diag, double tol, int max_iter, int max_space);
+  void truncate(int k, int dir, int M, double* tau, std::vector<double>* kept);
+  double step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept);
+  void init_mps(uint64_t seed, int M);
+  void build_right_envs(int from_k);
+  void build_left_envs(int to_k);
+  std::vector<int> last_pattern;
+  int psi_pattern(int k, int dir);
+};
+
+}  // namespace gbd

@@ -1,0 +1,139 @@
+// Internal data structures of the DMRG sweep engine (host + device).
+//
+// Quantum numbers: every bond k (0..n) is labelled by the particle numbers
+// q = (N_alpha, N_beta) of the left block (sites < k).  Local site states are
+// [0, alpha, beta, alpha+beta] with quantum numbers QA/QB below.
+//
+// Layouts (all row-major FP64 on the device unless stated):
+//   environment block  (channel a, sector q_in) -> m(q_in + delta_a) x m(q_in)
+//   two-site state     one dense block per middle sector Q of bond k+1:
+//                      rows = enlarged left  E_L(Q) = concat_s (q_l = Q - s, s)
+//                      cols = enlarged right E_R(Q) = concat_s (s, q_r = Q + s)
+//   left-canonical A_k fused-left per sector Q of bond k+1: m_EL(Q) x m_{k+1}(Q)
+//   right-canonical B_k fused-right per sector q of bond k: m_k(q) x m_ER(q)
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace gbd {
+
+constexpr int QA[4] = {0, 1, 0, 1};
+constexpr int QB[4] = {0, 0, 1, 1};
+constexpr int PAR[4] = {0, 1, 1, 0};
+
+inline int qkey(int a, int b) { return a * 64 + b; }
+
+struct Bond {
+  std::vector<int> na, nb, dim;   // sorted by (na, nb)
+  std::vector<int64_t> off;        // prefix offsets of dims
+  std::unordered_map<int, int> idx;
+  void finalize();
+  int find(int a, int b) const {
+    if (a < 0 || b < 0 || a > 63 || b > 63) return -1;
+    auto it = idx.find(qkey(a, b));
+    return it == idx.end() ? -1 : it->second;
+  }
+  int nsec() const { return (int)na.size(); }
+  int64_t total() const { return off.empty() ? 0 : off.back(); }
+};
+
+// ---------------------------------------------------------------- MPO
+// Channel labels: kind 0 = I, 1 = H, 2 = bare (left operators fixed),
+// 3 = complementary (right operators fixed); up to two operator codes
+// code = site*4 + spin*2 + (creator ? 0 : 1).  key orders labels.
+struct Label {
+  int kind = 0, nops = 0, c0 = 0, c1 = 0;
+  uint64_t key() const {
+    return ((uint64_t)kind << 40) | ((uint64_t)nops << 32) | ((uint64_t)c0 << 16) | (uint64_t)c1;
+  }
+};
+
+struct MpoEntry {       // one nonzero local matrix element of W_i[a,b]
+  int a, b, sout, sin;
+  double v;
+};
+
+struct Mpo {
+  int n = 0, k_switch = 0;
+  std::vector<std::vector<Label>> labels;          // per bond
+  std::vector<std::vector<int>> dA, dB, parity;    // per bond per channel
+  std::vector<std::vector<MpoEntry>> W;            // per site, dressed, sorted by (b, a, sout, sin)
+  std::vector<int> ident_channel;                  // per bond: index of 'I' (-1 if absent)
+  std::vector<int> ham_channel;                    // per bond: index of 'H' (-1 if absent)
+};
+
+void build_mpo(int n, const double* h, const double* eri, int k_switch, Mpo& out);
+
+// ---------------------------------------------------------------- grouped GEMM
+// C[out] = beta * C + sum_terms alpha * op(A) op(B), op = transpose if flag.
+struct GemmTerm {
+  const double* A;
+  const double* B;
+  int32_t lda, ldb, K, flags;   // flags: 1 = transA, 2 = transB
+  double alpha;
+};
+struct GemmOut {
+  double* C;
+  int32_t ldc, M, N;
+  int32_t t0, t1;   // term range
+  int32_t beta;     // 0 = overwrite, 1 = accumulate
+  int32_t pad;
+};
+struct GemmTile {
+  int32_t out, tm, tn, pad;
+};
+
+struct GemmPlan {       // host side lists plus their device copies
+  std::vector<GemmTerm> terms;
+  std::vector<GemmOut> outs;
+  std::vector<GemmTile> tiles;
+  GemmTerm* d_terms = nullptr;
+  GemmOut* d_outs = nullptr;
+  GemmTile* d_tiles = nullptr;
+  double flops = 0.0;       // 2 m n k summed over terms
+  void clear() { terms.clear(); outs.clear(); tiles.clear(); flops = 0.0; }
+  int add_out(double* C, int ldc, int M, int N, int beta) {
+    GemmOut o{C, ldc, M, N, (int)terms.size(), (int)terms.size(), beta, 0};
+    outs.push_back(o);
+    return (int)outs.size() - 1;
+  }
+  void add_term(const double* A, int lda, const double* B, int ldb, int K, int flags, double alpha) {
+    GemmTerm t{A, B, lda, ldb, K, flags, alpha};
+    terms.push_back(t);
+    GemmOut& o = outs.back();
+    o.t1 = (int)terms.size();
+    flops += 2.0 * o.M * o.N * K;
+  }
+};
+
+// Block axpy: out[i] = sum_j coef_j * src_j[i] over equally sized blocks.
+struct AxpyTerm { const double* src; double coef; };
+struct AxpyOut { double* dst; int64_t len; int32_t t0, t1; };
+struct AxpyPlan {
+  std::vector<AxpyTerm> terms;
+  std::vector<AxpyOut> outs;
+  AxpyTerm* d_terms = nullptr;
+  AxpyOut* d_outs = nullptr;
+  void clear() { terms.clear(); outs.clear(); }
+};
+
+// ---------------------------------------------------------------- kernels (kernels.cu)
+void launch_gemm_f64(const GemmPlan& p, cudaStream_t s);
+void launch_axpy(const AxpyPlan& p, cudaStream_t s);
+void launch_set_identity(double* d, int m, cudaStream_t s);
+// Davidson vector ops (vectors V_j = V + j * stride)
+void launch_multi_dot(const double* V, int64_t stride, int k, const double* x, int64_t n, double* out_dev,
+                      double* partial, int nblk, cudaStream_t s);
+void launch_lincomb(double* out, const double* V, int64_t stride, const double* coef_dev, int k, int64_t n,
+                    int accumulate, cudaStream_t s);
+void launch_residual_precond(const double* x, const double* sx, const double* diag, double theta, int64_t n,
+                             double* r, double* t, double* partial, int nblk, double* out_dev, cudaStream_t s);
+void launch_scale(double* x, double a, int64_t n, cudaStream_t s);
+int reduction_blocks(int64_t n);
+
+}  // namespace gbd

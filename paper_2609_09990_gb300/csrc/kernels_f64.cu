@@ -1,0 +1,233 @@
+// FP64 kernels of the sweep: grouped block GEMM (the sigma build, environment
+// update and decimation contractions all reduce to lists of small dense
+// products), block axpy (forming enlarged operators from environment blocks
+// and MPO entries) and the Davidson vector operations.
+//
+// GB300 executes FP64 on its CUDA cores only; these kernels are the plain
+// FP64 path.  The grouped GEMM keeps a 32x32 output tile per CTA in
+// registers and walks every (A,B) term that contributes to that tile, so each
+// output block is written once, deterministically, without atomics.
+#include <cuda_runtime.h>
+
+#include "gbd_internal.h"
+
+namespace gbd {
+
+namespace {
+
+constexpr int TM = 32, TN = 32, TK = 16, GEMM_THREADS = 64;
+
+__global__ void __launch_bounds__(GEMM_THREADS)
+gemm_f64_kernel(const GemmTerm* __restrict__ terms, const GemmOut* __restrict__ outs,
+                const GemmTile* __restrict__ tiles, int ntiles) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const GemmTile tl = tiles[tile];
+    const GemmOut o = outs[tl.out];
+    const int m0 = tl.tm * TM, n0 = tl.tn * TN;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int t = o.t0; t < o.t1; ++t) {
+      const GemmTerm T = terms[t];
+      const bool ta = T.flags & 1, tb = T.flags & 2;
+      for (int k0 = 0; k0 < T.K; k0 += TK) {
+        // A tile: TM x TK of op(A), scaled by alpha
+#pragma unroll
+        for (int r = 0; r < (TM * TK) / GEMM_THREADS; ++r) {
+          int idx = tid + r * GEMM_THREADS;
+          int i, kk;
+          if (!ta) { i = idx / TK; kk = idx % TK; } else { i = idx % TM; kk = idx / TM; }
+          int gm = m0 + i, gk = k0 + kk;
+          double v = 0.0;
+          if (gm < o.M && gk < T.K)
+            v = ta ? T.A[(int64_t)gk * T.lda + gm] : T.A[(int64_t)gm * T.lda + gk];
+          As[kk][i] = v * T.alpha;
+        }
+        // B tile: TK x TN of op(B)
+#pragma unroll
+        for (int r = 0; r < (TN * TK) / GEMM_THREADS; ++r) {
+          int idx = tid + r * GEMM_THREADS;
+          int j, kk;
+          if (!tb) { j = idx % TN; kk = idx / TN; } else { j = idx / TK; kk = idx % TK; }
+          int gn = n0 + j, gk = k0 + kk;
+          double v = 0.0;
+          if (gn < o.N && gk < T.K)
+            v = tb ? T.B[(int64_t)gn * T.ldb + gk] : T.B[(int64_t)gk * T.ldb + gn];
+          Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 8 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 8 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gm = m0 + ty + 8 * i;
+      if (gm >= o.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gn = n0 + tx + 8 * j;
+        if (gn >= o.N) continue;
+        double* c = o.C + (int64_t)gm * o.ldc + gn;
+        *c = o.beta ? (*c + acc[i][j]) : acc[i][j];
+      }
+    }
+  }
+}
+
+__global__ void axpy_kernel(const AxpyTerm* __restrict__ terms, const AxpyOut* __restrict__ outs, int nouts) {
+  for (int oi = blockIdx.x; oi < nouts; oi += gridDim.x) {
+    const AxpyOut o = outs[oi];
+    for (int64_t e = threadIdx.x; e < o.len; e += blockDim.x) {
+      double s = 0.0;
+      for (int t = o.t0; t < o.t1; ++t) s = fma(terms[t].coef, terms[t].src[e], s);
+      o.dst[e] = s;
+    }
+  }
+}
+
+__global__ void set_identity_kernel(double* d, int m) {
+  int64_t n = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (e / m == e % m) ? 1.0 : 0.0;
+}
+
+constexpr int RED_THREADS = 256;
+
+__device__ double block_sum(double v) {
+  __shared__ double sh[RED_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < RED_THREADS / 32) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
+// partial[j * nblk + b] = sum over block b's chunk of V_j . x
+__global__ void multi_dot_partial(const double* __restrict__ V, int64_t stride, int k,
+                                  const double* __restrict__ x, int64_t n, double* partial) {
+  const int j = blockIdx.y;
+  const double* v = V + (int64_t)j * stride;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS)
+    s = fma(v[i], x[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[j * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void finish_sums(const double* partial, int nblk, int k, double* out) {
+  int j = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += RED_THREADS) s += partial[j * nblk + b];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+__global__ void lincomb_kernel(double* out, const double* __restrict__ V, int64_t stride,
+                               const double* __restrict__ coef, int k, int64_t n, int accumulate) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = accumulate ? out[i] : 0.0;
+    for (int j = 0; j < k; ++j) s = fma(coef[j], V[(int64_t)j * stride + i], s);
+    out[i] = s;
+  }
+}
+
+// r = sx - theta x ; t = -r / clamp(diag - theta) ; partial sums of r^2
+__global__ void residual_precond_kernel(const double* __restrict__ x, const double* __restrict__ sx,
+                                        const double* __restrict__ diag, double theta, int64_t n,
+                                        double* r, double* t, double* partial) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+    double ri = sx[i] - theta * x[i];
+    r[i] = ri;
+    double den = diag[i] - theta;
+    if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
+    t[i] = -ri / den;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void scale_kernel(double* x, double a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= a;
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int reduction_blocks(int64_t n) {
+  int64_t b = (n + RED_THREADS * 4 - 1) / (RED_THREADS * 4);
+  if (b > 608) b = 608;
+  return (int)(b < 1 ? 1 : b);
+}
+
+void launch_gemm_f64(const GemmPlan& p, cudaStream_t s) {
+  int nt = (int)p.tiles.size();
+  if (nt == 0) return;
+  int grid = nt < 152 * 24 ? nt : 152 * 24;
+  gemm_f64_kernel<<<grid, GEMM_THREADS, 0, s>>>(p.d_terms, p.d_outs, p.d_tiles, nt);
+}
+
+void launch_axpy(const AxpyPlan& p, cudaStream_t s) {
+  int no = (int)p.outs.size();
+  if (no == 0) return;
+  int grid = no < 152 * 16 ? no : 152 * 16;
+  axpy_kernel<<<grid, 128, 0, s>>>(p.d_terms, p.d_outs, no);
+}
+
+void launch_set_identity(double* d, int m, cudaStream_t s) {
+  set_identity_kernel<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(d, m);
+}
+
+void launch_multi_dot(const double* V, int64_t stride, int k, const double* x, int64_t n, double* out_dev,
+                      double* partial, int nblk, cudaStream_t s) {
+  if (k <= 0) return;
+  dim3 g(nblk, k);
+  multi_dot_partial<<<g, RED_THREADS, 0, s>>>(V, stride, k, x, n, partial);
+  finish_sums<<<k, RED_THREADS, 0, s>>>(partial, nblk, k, out_dev);
+}
+
+void launch_lincomb(double* out, const double* V, int64_t stride, const double* coef_dev, int k, int64_t n,
+                    int accumulate, cudaStream_t s) {
+  lincomb_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, V, stride, coef_dev, k, n, accumulate);
+}
+
+void launch_residual_precond(const double* x, const double* sx, const double* diag, double theta, int64_t n,
+                             double* r, double* t, double* partial, int nblk, double* out_dev, cudaStream_t s) {
+  residual_precond_kernel<<<nblk, RED_THREADS, 0, s>>>(x, sx, diag, theta, n, r, t, partial);
+  finish_sums<<<1, RED_THREADS, 0, s>>>(partial, nblk, 1, out_dev);
+}
+
+void launch_scale(double* x, double a, int64_t n, cudaStream_t s) {
+  scale_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, a, n);
+}
+
+}  // namespace gbd

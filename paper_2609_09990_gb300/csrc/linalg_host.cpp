@@ -1,0 +1,166 @@
+// Small dense FP64 linear algebra on the host: the Rayleigh-Ritz
+// eigenproblem of Davidson (k <= ~24) and the per-sector reduced density
+// matrices of the decimation step (edges of a few hundred).
+//
+// Symmetric eigensolver: Householder reduction to tridiagonal form followed
+// by the implicit-shift QL iteration (Wilkinson & Reinsch, Handbook for
+// Automatic Computation II, 1971), written from the algorithm's description.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "linalg_host.h"
+
+namespace gbd {
+
+// A: n x n symmetric, row-major.  On return w ascending, Z column j = eigvec j.
+int sym_eig(int n, const double* A, double* w, double* Z) {
+  if (n <= 0) return 0;
+  std::vector<double> a(A, A + (size_t)n * n);
+  std::vector<double> d(n), e(n, 0.0);
+  // ---- Householder tridiagonalisation, storing the reflectors in a
+  std::vector<std::vector<double>> refl;
+  std::vector<double> beta_l;
+  for (int k = 0; k + 2 < n; ++k) {
+    int m = n - k - 1;
+    std::vector<double> v(m);
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) { v[i] = a[(size_t)(k + 1 + i) * n + k]; nrm += v[i] * v[i]; }
+    nrm = std::sqrt(nrm);
+    double alpha = v[0] > 0 ? -nrm : nrm;
+    double vv = 0.0;
+    v[0] -= alpha;
+    for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+    if (vv == 0.0 || nrm == 0.0) {
+      refl.push_back({});
+      beta_l.push_back(0.0);
+      continue;
+    }
+    double beta = 2.0 / vv;
+    // p = beta * A22 v
+    std::vector<double> p(m, 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double* row = &a[(size_t)(k + 1 + i) * n + k + 1];
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += row[j] * v[j];
+      p[i] = beta * s;
+    }
+    double K = 0.0;
+    for (int i = 0; i < m; ++i) K += v[i] * p[i];
+    K *= 0.5 * beta;
+    for (int i = 0; i < m; ++i) p[i] -= K * v[i];   // w
+    for (int i = 0; i < m; ++i) {
+      double* row = &a[(size_t)(k + 1 + i) * n + k + 1];
+      for (int j = 0; j < m; ++j) row[j] -= v[i] * p[j] + p[i] * v[j];
+    }
+    a[(size_t)(k + 1) * n + k] = alpha;
+    a[(size_t)k * n + k + 1] = alpha;
+    for (int i = 1; i < m; ++i) { a[(size_t)(k + 1 + i) * n + k] = 0.0; a[(size_t)k * n + k + 1 + i] = 0.0; }
+    refl.push_back(v);
+    beta_l.push_back(beta);
+  }
+  for (int i = 0; i < n; ++i) d[i] = a[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = a[(size_t)(i + 1) * n + i];
+  // ---- Q = H_0 H_1 ... H_{n-3}, built from the right
+  std::vector<double> z((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) z[(size_t)i * n + i] = 1.0;
+  for (int k = (int)refl.size() - 1; k >= 0; --k) {
+    if (beta_l[k] == 0.0) continue;
+    const std::vector<double>& v = refl[k];
+    int m = (int)v.size(), o = k + 1;
+    // z[o:, :] -= beta v (v^T z[o:, :])
+    std::vector<double> t(n, 0.0);
+    for (int i = 0; i < m; ++i) {
+      const double* row = &z[(size_t)(o + i) * n];
+      for (int j = 0; j < n; ++j) t[j] += v[i] * row[j];
+    }
+    for (int i = 0; i < m; ++i) {
+      double* row = &z[(size_t)(o + i) * n];
+      double f = beta_l[k] * v[i];
+      for (int j = 0; j < n; ++j) row[j] -= f * t[j];
+    }
+  }
+  // ---- implicit QL on (d, e), rotating the columns of z
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    while (true) {
+      int m = l;
+      for (; m < n - 1; ++m) {
+        double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= 1e-16 * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 60) return -1;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+      double s = 1.0, c = 1.0, p = 0.0;
+      int i = m - 1;
+      bool early = false;
+      for (; i >= l; --i) {
+        double f = s * e[i], b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= p;
+          e[m] = 0.0;
+          early = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+        for (int k = 0; k < n; ++k) {
+          double zf = z[(size_t)k * n + i + 1];
+          z[(size_t)k * n + i + 1] = s * z[(size_t)k * n + i] + c * zf;
+          z[(size_t)k * n + i] = c * z[(size_t)k * n + i] - s * zf;
+        }
+      }
+      if (early) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  // ---- sort ascending
+  std::vector<int> ord(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return d[x] < d[y]; });
+  for (int j = 0; j < n; ++j) {
+    w[j] = d[ord[j]];
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = z[(size_t)i * n + ord[j]];
+  }
+  return 0;
+}
+
+// Rows of M (m x c, m <= c) -> M = Lo Q with Q orthonormal rows (Gram-Schmidt
+// applied twice per row).  Lo is m x m lower triangular.
+int row_orthonormalize(int m, int c, double* M, double* Lo) {
+  std::fill(Lo, Lo + (size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    double* mi = M + (size_t)i * c;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = 0; j < i; ++j) {
+        const double* qj = M + (size_t)j * c;
+        double r = 0.0;
+        for (int t = 0; t < c; ++t) r += qj[t] * mi[t];
+        for (int t = 0; t < c; ++t) mi[t] -= r * qj[t];
+        Lo[(size_t)i * m + j] += r;
+      }
+    }
+    double nrm = 0.0;
+    for (int t = 0; t < c; ++t) nrm += mi[t] * mi[t];
+    nrm = std::sqrt(nrm);
+    if (nrm < 1e-300) return -1;
+    for (int t = 0; t < c; ++t) mi[t] /= nrm;
+    Lo[(size_t)i * m + i] = nrm;
+  }
+  return 0;
+}
+
+}  // namespace gbd

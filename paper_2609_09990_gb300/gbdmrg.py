@@ -1,0 +1,284 @@
+"""Python binding of libgbdmrg (include/gbdmrg.h, include/gbdmrg_test.h).
+
+Argument marshalling only: every step of the sweep runs inside the C/CUDA
+library.  The names mirror the C entry points.  If the shared library has not
+been built, loading raises -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbdmrg.so")
+
+GBD_OK = 0
+GBD_FP64, GBD_TF32, GBD_BF16 = 0, 1, 2
+GBD_PRECOND_DIAG, GBD_PRECOND_LEARNED = 0, 1
+ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_OOM", -3: "GBD_ERR_CUDA", -4: "GBD_ERR_NOCONV",
+          -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_STATE"}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class gbd_problem(C.Structure):
+    _fields_ = [("n_orb", C.c_int32), ("n_elec", C.c_int32), ("two_sz", C.c_int32), ("n_chol", C.c_int32),
+                ("h", _dp), ("chol", _dp), ("e_core", C.c_double)]
+
+
+class gbd_schedule(C.Structure):
+    _fields_ = [("n_sweeps", C.c_int32), ("bond_dim", _ip), ("davidson_tol", _dp),
+                ("davidson_max_iter", C.c_int32), ("davidson_max_subspace", C.c_int32),
+                ("precision", C.c_int32), ("preconditioner", C.c_int32), ("seed", C.c_uint64),
+                ("svd_cutoff", C.c_double)]
+
+
+class gbd_result(C.Structure):
+    _fields_ = [("energy", C.c_double), ("sweep_energies", _dp), ("rdm1", _dp), ("rdm2", _dp),
+                ("max_discarded_weight", C.c_double), ("n_matvec", C.c_int64), ("status", C.c_int32)]
+
+
+class gbd_stats(C.Structure):
+    _fields_ = [("sigma_flops", C.c_double), ("sigma_ms", C.c_double), ("env_flops", C.c_double),
+                ("env_ms", C.c_double), ("enlarge_ms", C.c_double), ("davidson_ms", C.c_double),
+                ("truncate_ms", C.c_double), ("step_ms", C.c_double), ("n_sigma", C.c_int64),
+                ("n_steps", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64), ("max_discarded_weight", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libgbdmrg.so (built by paper_2609_09990_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2609_09990_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    sig = {
+        "gbd_create": (C.c_int, [C.POINTER(vp), C.c_int]),
+        "gbd_destroy": (None, [vp]),
+        "gbd_last_error": (C.c_char_p, [vp]),
+        "gbd_solve": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), C.POINTER(gbd_result)]),
+        "gbd_setup": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule)]),
+        "gbd_init_state": (C.c_int, [vp]),
+        "gbd_run_sweep": (C.c_int, [vp, C.c_int32, _dp]),
+        "gbd_final_energy": (C.c_int, [vp, _dp]),
+        "gbd_get_bond": (C.c_int, [vp, C.c_int32, _ip, C.c_int32, _ip]),
+        "gbd_set_mps": (C.c_int, [vp, _ip, _ip, _dp, C.c_int32]),
+        "gbd_two_site_size": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64)]),
+        "gbd_apply_heff": (C.c_int, [vp, C.c_int32, _dp, _dp, _dp]),
+        "gbd_run_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp,
+                                   C.c_int32, _ip]),
+        "gbd_mpo_labels": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, _ip]),
+        "gbd_env_block": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_int64, _ip, _ip]),
+        "gbd_get_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
+        "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                            C.c_int32, C.c_int32]),
+        "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
+        "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
+                                      _dp]),
+        "gbd_host_mpo": (C.c_int, [C.c_int32, _dp, C.c_int32, _dp, C.c_int32, _ip, _dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip) if a is not None else None
+
+
+class GbdError(RuntimeError):
+    pass
+
+
+class Context:
+    """Owns one gbd_ctx (device memory, stream) and keeps the marshalled
+    inputs alive while the library reads them."""
+
+    def __init__(self, device: int = 0):
+        self.L = lib()
+        self.ptr = C.c_void_p()
+        rc = self.L.gbd_create(C.byref(self.ptr), device)
+        if rc != GBD_OK:
+            raise GbdError(f"gbd_create failed: {ERRORS.get(rc, rc)}")
+        self._keep = []
+
+    def close(self):
+        if self.ptr:
+            self.L.gbd_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != GBD_OK:
+            msg = self.L.gbd_last_error(self.ptr).decode()
+            raise GbdError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+
+    def _structs(self, h, chol, n_elec, two_sz, bond_dims, tols, seed=1, precision=GBD_FP64,
+                 preconditioner=GBD_PRECOND_DIAG, max_iter=100, max_subspace=24, svd_cutoff=1e-12,
+                 e_core=0.0):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        chol = np.ascontiguousarray(chol, dtype=np.float64)
+        bd = np.ascontiguousarray(bond_dims, dtype=np.int32)
+        tl = np.ascontiguousarray(tols, dtype=np.float64)
+        self._keep = [h, chol, bd, tl]
+        p = gbd_problem(h.shape[0], n_elec, two_sz, chol.shape[0], _d(h), _d(chol), e_core)
+        s = gbd_schedule(len(bd), _i(bd), _d(tl), max_iter, max_subspace, precision, preconditioner,
+                         seed, svd_cutoff)
+        return p, s
+
+    def solve(self, h, chol, n_elec, two_sz, bond_dims, tols, rdms=False, **kw):
+        """gbd_solve; returns dict(energy, sweep_energies, rdm1, rdm2, ...)."""
+        p, s = self._structs(h, chol, n_elec, two_sz, bond_dims, tols, **kw)
+        n = p.n_orb
+        se = np.zeros(len(bond_dims))
+        r1 = np.zeros((n, n)) if rdms else None
+        r2 = np.zeros((n, n, n, n)) if rdms else None
+        res = gbd_result(0.0, _d(se), _d(r1), _d(r2), 0.0, 0, 0)
+        self._check(self.L.gbd_solve(self.ptr, C.byref(p), C.byref(s), C.byref(res)), "gbd_solve")
+        return dict(energy=res.energy, sweep_energies=se, rdm1=r1, rdm2=r2,
+                    max_discarded_weight=res.max_discarded_weight, n_matvec=res.n_matvec)
+
+    def setup(self, h, chol, n_elec, two_sz, bond_dims, tols, **kw):
+        p, s = self._structs(h, chol, n_elec, two_sz, bond_dims, tols, **kw)
+        self._check(self.L.gbd_setup(self.ptr, C.byref(p), C.byref(s)), "gbd_setup")
+
+    def init_state(self):
+        self._check(self.L.gbd_init_state(self.ptr), "gbd_init_state")
+
+    def run_sweep(self, sweep):
+        e = C.c_double()
+        self._check(self.L.gbd_run_sweep(self.ptr, sweep, C.byref(e)), "gbd_run_sweep")
+        return e.value
+
+    def final_energy(self):
+        e = C.c_double()
+        self._check(self.L.gbd_final_energy(self.ptr, C.byref(e)), "gbd_final_energy")
+        return e.value
+
+    def get_bond(self, bond):
+        cnt = C.c_int32()
+        self._check(self.L.gbd_get_bond(self.ptr, bond, None, 0, C.byref(cnt)), "gbd_get_bond")
+        t = np.zeros(3 * cnt.value, dtype=np.int32)
+        self._check(self.L.gbd_get_bond(self.ptr, bond, _i(t), cnt.value, C.byref(cnt)), "gbd_get_bond")
+        return t.reshape(-1, 3)
+
+    def set_mps(self, n_sectors, sectors, data, center):
+        ns = np.ascontiguousarray(n_sectors, dtype=np.int32)
+        sc = np.ascontiguousarray(sectors, dtype=np.int32)
+        dt = np.ascontiguousarray(data, dtype=np.float64)
+        self._check(self.L.gbd_set_mps(self.ptr, _i(ns), _i(sc), _d(dt), center), "gbd_set_mps")
+
+    def two_site_size(self, k):
+        n = C.c_int64()
+        self._check(self.L.gbd_two_site_size(self.ptr, k, C.byref(n)), "gbd_two_site_size")
+        return n.value
+
+    def apply_heff(self, k, x, want_diag=False):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        d = np.zeros_like(x) if want_diag else None
+        self._check(self.L.gbd_apply_heff(self.ptr, k, _d(x), _d(y), _d(d)), "gbd_apply_heff")
+        return (y, d) if want_diag else y
+
+    def run_step(self, k, direction, M, tol):
+        e, tau, nk = C.c_double(), C.c_double(), C.c_int32()
+        kept = np.zeros(max(M, 1))
+        self._check(self.L.gbd_run_step(self.ptr, k, direction, M, tol, C.byref(e), C.byref(tau), _d(kept),
+                                        len(kept), C.byref(nk)), "gbd_run_step")
+        return e.value, tau.value, kept[:nk.value].copy()
+
+    def mpo_labels(self, bond):
+        cnt = C.c_int32()
+        self._check(self.L.gbd_mpo_labels(self.ptr, bond, None, 0, C.byref(cnt)), "gbd_mpo_labels")
+        k = np.zeros(cnt.value, dtype=np.uint64)
+        self._check(self.L.gbd_mpo_labels(self.ptr, bond, k.ctypes.data_as(C.POINTER(C.c_uint64)), cnt.value,
+                                          C.byref(cnt)), "gbd_mpo_labels")
+        return k
+
+    def env_block(self, side, bond, channel, sector):
+        r, c = C.c_int32(), C.c_int32()
+        self._check(self.L.gbd_env_block(self.ptr, side, bond, channel, sector, None, 0, C.byref(r),
+                                         C.byref(c)), "gbd_env_block")
+        out = np.zeros(r.value * c.value)
+        self._check(self.L.gbd_env_block(self.ptr, side, bond, channel, sector, _d(out), out.size,
+                                         C.byref(r), C.byref(c)), "gbd_env_block")
+        return out.reshape(r.value, c.value)
+
+    def stats(self):
+        s = gbd_stats()
+        self.L.gbd_get_stats(self.ptr, C.byref(s))
+        return s.as_dict()
+
+
+# ---- host-only planner pieces
+def host_initial_dims(n, n_alpha, n_beta, M):
+    L = lib()
+    ns = np.zeros(n + 1, dtype=np.int32)
+    cap = 8192
+    tr = np.zeros(3 * cap, dtype=np.int32)
+    rc = L.gbd_host_initial_dims(n, n_alpha, n_beta, M, _i(ns), _i(tr), cap)
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_initial_dims: {ERRORS.get(rc, rc)}")
+    out, pos = [], 0
+    for k in range(n + 1):
+        d = {}
+        for _ in range(ns[k]):
+            d[(int(tr[pos]), int(tr[pos + 1]))] = int(tr[pos + 2])
+            pos += 3
+        out.append(d)
+    return out
+
+
+def host_select(lam, key, j, M, cutoff=1e-12, tie=1e-10):
+    L = lib()
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    key = np.ascontiguousarray(key, dtype=np.int32)
+    j = np.ascontiguousarray(j, dtype=np.int32)
+    idx = np.zeros(max(len(lam), 1), dtype=np.int32)
+    nk = C.c_int32()
+    tot = C.c_double()
+    rc = L.gbd_host_select(len(lam), _d(lam), _i(key), _i(j), M, cutoff, tie, _i(idx), C.byref(nk), C.byref(tot))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_select: {ERRORS.get(rc, rc)}")
+    return idx[:nk.value].copy(), tot.value
+
+
+def host_mpo(h, chol, k_switch=None, dense=False):
+    L = lib()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    chol = np.ascontiguousarray(chol, dtype=np.float64)
+    n = h.shape[0]
+    bd = np.zeros(n + 1, dtype=np.int32)
+    out = np.zeros((4 ** n, 4 ** n)) if dense else None
+    rc = L.gbd_host_mpo(n, _d(h), chol.shape[0], _d(chol), n // 2 if k_switch is None else k_switch, _i(bd), _d(out))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_mpo: {ERRORS.get(rc, rc)}")
+    return (bd, out) if dense else bd
+
+
+def mps_init_value(seed, site, na, nb, s, row, col):
+    return lib().gbd_mps_init_value(seed, site, na, nb, s, row, col)
