@@ -252,7 +252,7 @@ void Engine::dfree(void* p) {
 // error becomes a GBD_ERR_STATE instead of an out-of-bounds device access.
 void Engine::check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, const char* what) const {
   if (rows <= 0 || cols <= 0) return;
-  if (ld < cols) throw Error(-6, std::string("plan check: leading dimension too small for ") + what);
+  if (rows > 1 && ld < cols) throw Error(-6, std::string("plan check: leading dimension too small for ") + what);
   uintptr_t a = (uintptr_t)p;
   uintptr_t end = a + (uintptr_t)(((rows - 1) * ld + cols) * (int64_t)sizeof(double));
   auto it = allocs.upper_bound(a);

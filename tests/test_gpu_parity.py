@@ -51,11 +51,12 @@ def test_heff_and_envs_match_oracle(G, n, ne, nq, seed, M, k):
             for si, q in enumerate(secs):
                 got = ctx.env_block(side, bond, a, si)
                 ref = env[a].get(q) if a < len(env) else None
-                if ref is None:
-                    ref = np.zeros_like(got)
-                if got.size == 0:
+                if got.size == 0:   # structurally absent block: the oracle has none either
                     assert ref is None or np.abs(ref).max() == 0
                     continue
+                if ref is None:
+                    ref = np.zeros_like(got)
+                assert got.shape == ref.shape
                 assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
     # H_eff on random vectors and its diagonal
     keys2 = dmrg.psi_keys(d.dims[k], d.dims[k + 2])
