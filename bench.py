@@ -1,0 +1,300 @@
+"""Benchmark of the DMRG sweep engine on one GB300 (or N replicas).
+
+Workload: CAS(16e,16o), S_z = 0, synthetic integrals (gbd_synth, seed 3,
+48 Cholesky vectors), bond dimension M = 512.  One "step" is one full
+two-site sweep (left-to-right and back, 30 two-site steps: H_eff diagonal,
+Davidson with sigma builds, decimation, environment updates), with the state
+resident on the device when the timed region starts.
+
+value  = algorithmic sigma-build flops of the timed sweeps / wall time of
+         the timed sweeps (TFLOP/s, whole job: everything in the sweep counts
+         in the denominator).
+e2e    = the same metric through gbd_solve (host integrals in, energies out;
+         initial state, sweeps and final energy inside the timed call).
+roofline = the grouped block-GEMM of the sigma build: algorithmic flops over
+         its CUDA-event device time.
+cpu_baseline = the CPU oracle on a bounded sample: one sigma build at the
+         central bond pair (7,8) of the same problem (initial MPS at M=512).
+
+Multi-GPU: independent replicas (one problem per rank, seed 3 + rank), no
+collective on the data path; value sums the ranks' flops over the max time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from gbd_synth import WORKLOADS, make_integrals  # noqa: E402
+
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def schedule(nsweeps, tol):
+    return [tol] * nsweeps
+
+
+def run_ours(args, rank, world):
+    from paper_2609_09990_gb300 import gbdmrg as G
+
+    wl = WORKLOADS[args.workload]
+    n, ne, nq, M = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"]
+    seed = wl["seed"] + rank
+    h, chol = make_integrals(n, nq, seed)
+    prec = PREC[args.precision]
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    import torch
+    torch.cuda.set_device(dev)
+    ctx = G.Context(dev)
+    nsw = args.warmup + args.steps
+    ctx.setup(h, chol, ne, 0, [M] * nsw, schedule(nsw, args.tol), seed=seed, precision=prec)
+    ctx.init_state()
+    for s in range(args.warmup):
+        ctx.run_sweep(s)
+    st0 = ctx.stats()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev)
+    clk.start()
+    t0 = time.perf_counter()
+    energies = []
+    for s in range(args.warmup, nsw):
+        energies.append(ctx.run_sweep(s))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    dist_barrier(world)
+    clocks = clk.stop()
+    st1 = ctx.stats()
+    dt = t1 - t0
+    flops = st1["sigma_flops"] - st0["sigma_flops"]
+    sig_ms = st1["sigma_ms"] - st0["sigma_ms"]
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+    ctx.close()
+    # end to end through gbd_solve: host integrals in, energies out
+    e2e = None
+    if not args.no_e2e:
+        ctx = G.Context(dev)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        r = ctx.solve(h, chol, ne, 0, [M] * args.steps, schedule(args.steps, args.tol), seed=seed,
+                      precision=prec)
+        t3 = time.perf_counter()
+        se = ctx.stats()
+        ctx.close()
+        e2e = dict(flops=se["sigma_flops"], time=t3 - t2, h2d=int(h.nbytes + chol.nbytes),
+                   d2h=int(8 * (1 + args.steps)), energy=r["energy"])
+    return dict(time=dt, flops=flops, sigma_ms=sig_ms, launches=launches, clocks=clocks,
+                energies=energies, e2e=e2e, n=n, M=M, st=st1)
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_sample(n_sigma=1, want_flops=True, warmup=0):
+    """CPU oracle: sigma builds at the central bond pair (7,8) of CAS(16,16)
+    on the seeded initial MPS (M = 512).  Environments are built by the
+    oracle with its MPO switch at bond 3 (untimed); the timed part is the
+    sigma builds.  Flops per build: the GPU engine's algorithmic count for
+    the same sigma on the same state (the oracle's MPS is installed in the
+    library and one H_eff application is made), which also checks parity."""
+    from oracle import dmrg
+    wl = WORKLOADS["cas16_m512"]
+    n, ne, nq, M, seed = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"]
+    h, chol = make_integrals(n, nq, seed)
+    k = n // 2 - 1
+    ts = time.perf_counter()
+    d = dmrg.DMRG(h, chol, ne, 0, M, seed=seed, k_switch=3, renv_down_to=k + 2)
+    d.move_center(k)
+    setup_s = time.perf_counter() - ts
+    psi = dmrg.two_site_psi(d.sites[k], d.sites[k + 1], d.dims[k + 1])
+    L, W1, W2, R = d.heff_parts(k)
+    for _ in range(warmup):
+        dmrg.apply_heff(L, W1, W2, R, psi, d.mpo, k)
+    times = []
+    sig = None
+    for _ in range(n_sigma):
+        t = time.perf_counter()
+        sig = dmrg.apply_heff(L, W1, W2, R, psi, d.mpo, k)
+        times.append(time.perf_counter() - t)
+    keys = dmrg.psi_keys(d.dims[k], d.dims[k + 2])
+    x = dmrg.flatten(psi, keys, d.dims[k], d.dims[k + 2])
+    y_ref = dmrg.flatten(sig, keys, d.dims[k], d.dims[k + 2])
+    flops, rel = None, None
+    if want_flops:
+        from paper_2609_09990_gb300 import gbdmrg as G
+        ctx = G.Context(int(os.environ.get("LOCAL_RANK", "0")))
+        ctx.setup(h, chol, ne, 0, [M], [1e-8], seed=seed)
+        ns, tr, data = dmrg.canonical_blocks(d)
+        ctx.set_mps(ns, tr, data, k)
+        f0 = ctx.stats()["sigma_flops"]
+        y = ctx.apply_heff(k, x)
+        flops = ctx.stats()["sigma_flops"] - f0
+        rel = float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
+        ctx.close()
+    return dict(times=times, setup_s=setup_s, flops=flops, parity_rel=rel, psi_len=len(x))
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--workload", default="cas16_m512")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    config = {"workload": f"{args.workload}: CAS({wl['n_elec']}e,{wl['n_orb']}o) S_z=0, {wl['n_chol']} Cholesky "
+                          f"vectors, M={wl['M']}, one step = one full sweep",
+              "n_orb": wl["n_orb"], "bond_dim": wl["M"], "davidson_tol": args.tol,
+              "l2": "inputs larger than L2 (environments of all bonds, > 1 GB)",
+              "parallelism": f"replicas x{world}"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        s = oracle_sample(n_sigma=args.steps, want_flops=True, warmup=args.warmup)
+        ms = 1000 * float(np.mean(s["times"]))
+        val = s["flops"] / (ms / 1000) / 1e12
+        line = {"impl": "reference", "metric": "sigma-build TFLOP/s", "value": val, "unit": "TFLOP/s",
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
+                                 "sample": "one oracle sigma build per step at bond pair (7,8) of "
+                                           "CAS(16,16) on the seeded initial MPS (M=512)"},
+                "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "oracle_setup_s": s["setup_s"], "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+        return
+    res = run_ours(args, rank, world)
+    tmax, flops = res["time"], res["flops"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([tmax], device="cuda")
+        f = torch.tensor([flops], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        tmax, flops = float(t.item()), float(f.item())
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    kern_tflops = res["flops"] / (res["sigma_ms"] / 1000) / 1e12 if res["sigma_ms"] > 0 else 0.0
+    if args.precision == "fp64":
+        # FP64 runs on the CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+        peak, bound, punit, kind = 152 * 2 * 2 * 2.07e9 / 1e12, "alu", "TFLOP/s", "derived (FP64 unit count x max clock)"
+    else:
+        peak, bound, punit, kind = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s", pk_kind
+    roof = {"bound": bound, "achieved": kern_tflops, "peak": peak, "unit": punit, "frac": kern_tflops / peak,
+            "traffic": None, "kernel": "gemm_f64_kernel (sigma stages A+B)", "peak_kind": kind}
+    line = {"metric": "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512", "value": flops / tmax / 1e12,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic", "config": config,
+            "sweep_time_s": tmax / args.steps, "sweep_energies": res["energies"],
+            "sigma_kernel_tflops": kern_tflops, "roofline": roof, "clocks": res["clocks"],
+            "gpu_launches": int(res["launches"])}
+    if res["e2e"]:
+        e = res["e2e"]
+        line["e2e"] = {"value": e["flops"] / e["time"] / 1e12, "unit": "TFLOP/s",
+                       "h2d_bytes_per_step": e["h2d"] // args.steps, "d2h_bytes_per_step": e["d2h"] // args.steps,
+                       "solve_s": e["time"]}
+    if world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(n_sigma=1, want_flops=True)
+        v = s["flops"] / s["times"][0] / 1e12
+        line["cpu_baseline"] = {"value": v, "unit": "TFLOP/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"one oracle sigma build at bond pair (7,8) of the same problem on the "
+                                          f"seeded initial MPS (M=512, psi length {s['psi_len']}); "
+                                          f"{s['times'][0]:.1f} s; oracle setup {s['setup_s']:.0f} s untimed",
+                                "gpu_vs_oracle_sigma_rel_err": s["parity_rel"]}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,10 @@ int gbd_get_stats(const gbd_ctx *ctx, gbd_stats *stats);
 double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, int32_t s, int32_t row,
                           int32_t col);
 
+/* FP64 and FP32 CUDA-core FMA throughput of `device` (TFLOP/s), measured
+ * with independent FMA chains on every SM; the peak of the FP64 path. */
+int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);
+
 /* ---- host-only pieces of the planner (no GPU needed) ---- */
 /* Initial bond dimensions of the seeded MPS for n orbitals, (N_alpha,
  * N_beta) electrons and bond dimension M; n_sectors [n+1], triples [3 cap]. */

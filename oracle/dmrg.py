@@ -416,7 +416,7 @@ def truncate(psi, dims_k, dims_k2, M, direction, cutoff=1e-12, tie=1e-10):
 class DMRG:
     """Two-site DMRG state: MPS, MPO and environments."""
 
-    def __init__(self, h, chol, n_elec, two_sz, M_init, seed, k_switch=None, mps=None):
+    def __init__(self, h, chol, n_elec, two_sz, M_init, seed, k_switch=None, mps=None, renv_down_to=2):
         self.h = np.asarray(h, dtype=np.float64)
         self.chol = np.asarray(chol, dtype=np.float64)
         self.eri = np.einsum("Qpq,Qrs->pqrs", self.chol, self.chol)
@@ -435,7 +435,7 @@ class DMRG:
         self.Renv = [None] * (n + 1)
         self.Lenv[0] = left_boundary()
         self.Renv[n] = right_boundary(self.Na, self.Nb)
-        for k in range(n - 1, 1, -1):
+        for k in range(n - 1, max(renv_down_to, 2) - 1, -1):
             self.Renv[k] = right_env_update(self.Renv[k + 1], self.sites[k], self.mpo.W[k],
                                             self.mpo.delta[k + 1], len(self.mpo.labels[k]))
         self.n_matvec = 0
@@ -483,6 +483,28 @@ class DMRG:
         for k in range(n - 2, -1, -1):
             log.append(("R", k) + self.step(k, M, tol, "R", **kw)[:2])
         return log
+
+    def move_center(self, k):
+        """Left-orthonormalise sites 0..k-1 of a state whose centre is site 0
+        (QR per sector of bond i+1, the triangular factor moves right) and
+        build the left environments up to bond k.  The state is unchanged."""
+        for i in range(k):
+            Qs = sorted({qadd(ql, QN[s]) for (ql, s) in self.sites[i]})
+            for Q in Qs:
+                rows = [(qsub(Q, QN[s]), s) for s in range(4) if (qsub(Q, QN[s]), s) in self.sites[i]]
+                mat = np.vstack([self.sites[i][r] for r in rows])
+                Qm, Rm = np.linalg.qr(mat)
+                off = 0
+                for r in rows:
+                    m = self.sites[i][r].shape[0]
+                    self.sites[i][r] = Qm[off:off + m, :].copy()
+                    off += m
+                assert Qm.shape[1] == self.dims[i + 1][Q]
+                for s in range(4):
+                    if (Q, s) in self.sites[i + 1]:
+                        self.sites[i + 1][(Q, s)] = Rm @ self.sites[i + 1][(Q, s)]
+            self.Lenv[i + 1] = left_env_update(self.Lenv[i], self.sites[i], self.mpo.W[i], self.mpo.delta[i],
+                                               len(self.mpo.labels[i + 1]))
 
     def energy(self):
         """<psi|H_eff|psi> / <psi|psi> at bond (0,1) of the current MPS."""
@@ -541,3 +563,27 @@ def run(h, chol, n_elec, two_sz, M_schedule, tol_schedule, seed, k_switch=None,
         log = d.sweep(M, tol, max_iter=max_iter, max_space=max_space, cutoff=cutoff, tie=tie)
         sweep_E.append(log[-1][2])
     return d, sweep_E
+
+
+def canonical_blocks(d):
+    """(n_sectors, triples, data) of a DMRG state in the canonical block
+    exchange format of the CUDA library's test interface: per bond the sorted
+    sector triples (N_alpha, N_beta, dim); per site, for each sector q_l and
+    local state s with q_r = q_l + s present, one row-major block."""
+    ns, tr, data = [], [], []
+    for k in range(d.n + 1):
+        secs = sorted(d.dims[k])
+        ns.append(len(secs))
+        for q in secs:
+            tr += [q[0], q[1], d.dims[k][q]]
+    for i in range(d.n):
+        for ql in sorted(d.dims[i]):
+            for s in range(4):
+                qr = qadd(ql, QN[s])
+                if qr not in d.dims[i + 1]:
+                    continue
+                b = d.sites[i].get((ql, s))
+                if b is None:
+                    b = np.zeros((d.dims[i][ql], d.dims[i + 1][qr]))
+                data.append(b.reshape(-1))
+    return np.array(ns), np.array(tr), np.concatenate(data)

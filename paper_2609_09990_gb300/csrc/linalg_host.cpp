@@ -81,17 +81,23 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
       for (int j = 0; j < n; ++j) row[j] -= f * t[j];
     }
   }
-  // ---- implicit QL on (d, e), rotating the columns of z
+  // ---- implicit QL on (d, e), rotating the columns of z.  An off-diagonal
+  // element is negligible when it is below eps relative to its neighbours or
+  // below eps * ||T|| (backward-stable absolute deflation; density matrices
+  // have many eigenvalues near zero where a purely relative test stalls).
+  const double eps = 2.220446049250313e-16;
+  double anorm = 0.0;
+  for (int i = 0; i < n; ++i) anorm = std::max(anorm, std::fabs(d[i]) + std::fabs(e[i]) + (i ? std::fabs(e[i - 1]) : 0.0));
   for (int l = 0; l < n; ++l) {
     int iter = 0;
     while (true) {
       int m = l;
       for (; m < n - 1; ++m) {
         double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) <= 1e-16 * dd) break;
+        if (std::fabs(e[m]) <= eps * dd || std::fabs(e[m]) <= eps * anorm) break;
       }
       if (m == l) break;
-      if (++iter > 60) return -1;
+      if (++iter > 200) return -1;
       double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
       double r = std::hypot(g, 1.0);
       g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));

@@ -84,6 +84,7 @@ def lib():
         "gbd_get_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
         "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32]),
+        "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
         "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
                                       _dp]),
@@ -278,6 +279,15 @@ def host_mpo(h, chol, k_switch=None, dense=False):
     if rc != GBD_OK:
         raise GbdError(f"gbd_host_mpo: {ERRORS.get(rc, rc)}")
     return (bd, out) if dense else bd
+
+
+def probe_peaks(device=0):
+    """Measured FP64 / FP32 FMA throughput (TFLOP/s) of the device."""
+    a, b = C.c_double(), C.c_double()
+    rc = lib().gbd_probe_peaks(device, C.byref(a), C.byref(b))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_probe_peaks: {ERRORS.get(rc, rc)}")
+    return a.value, b.value
 
 
 def mps_init_value(seed, site, na, nb, s, row, col):

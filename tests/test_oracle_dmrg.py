@@ -195,3 +195,30 @@ def test_select_states_tie_rule():
     assert [k[1] for k in kept] == [(1, 0), (0, 1), (1, 0)]
     kept, _ = dmrg.select_states([(0.3, (0, 0), 0), (1e-13, (0, 1), 0)], 5)
     assert len(kept) == 1
+
+
+def test_move_center_keeps_state_and_gauge():
+    # left-orthonormal sites after the move, unchanged expansion coefficients
+    h, chol = make_integrals(6, 8, 3)
+    d = dmrg.DMRG(h, chol, 6, 0, 12, seed=2)
+    C0 = d.to_ci()
+    d.move_center(3)
+    for i in range(3):
+        for Q in d.dims[i + 1]:
+            rows = [d.sites[i][(dmrg.qsub(Q, mpo.QN[s]), s)] for s in range(4)
+                    if (dmrg.qsub(Q, mpo.QN[s]), s) in d.sites[i]]
+            A = np.vstack(rows)
+            assert np.abs(A.T @ A - np.eye(A.shape[1])).max() < 1e-12
+    assert np.abs(d.to_ci() - C0).max() < 1e-12
+    # H_eff at the new centre is the projected Hamiltonian: its expectation
+    # value in the two-site state equals the energy of the full state
+    eri = fock.eri_from_chol(chol)
+    f = fci.FCI(h, eri, 3, 3)
+    c = C0.reshape(-1)
+    E = c @ f.sigma(c).ravel() / (c @ c)
+    k = 3
+    psi = dmrg.two_site_psi(d.sites[k], d.sites[k + 1], d.dims[k + 1])
+    keys = dmrg.psi_keys(d.dims[k], d.dims[k + 2])
+    x = dmrg.flatten(psi, keys, d.dims[k], d.dims[k + 2])
+    s = dmrg.flatten(dmrg.apply_heff(*d.heff_parts(k), psi, d.mpo, k), keys, d.dims[k], d.dims[k + 2])
+    assert abs(x @ s / (x @ x) - E) < 1e-11
