@@ -70,6 +70,12 @@ int gbd_get_stats(const gbd_ctx *ctx, gbd_stats *stats);
 double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, int32_t s, int32_t row,
                           int32_t col);
 
+/* Davidson overlap reduction out[j] = V_j . x for j < k, V_j = V + j*stride.
+ * V and x are device pointers (n doubles each, stride >= n); out is a host
+ * array of k doubles.  Partial sums go to scratch memory allocated on the
+ * context's stream; 1 <= k <= 32. */
+int gbd_multi_dot(gbd_ctx *ctx, const double *V, int64_t stride, int32_t k, const double *x, int64_t n,
+                  double *out);
 /* FP64 and FP32 CUDA-core FMA throughput of `device` (TFLOP/s), measured
  * with independent FMA chains on every SM; the peak of the FP64 path. */
 int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);

@@ -289,6 +289,16 @@ int gbd_env_block(gbd_ctx* ctx, int32_t side, int32_t bond, int32_t channel, int
   });
 }
 
+int gbd_multi_dot(gbd_ctx* ctx, const double* V, int64_t stride, int32_t k, const double* x, int64_t n, double* out) {
+  return guarded(ctx, [&]() {
+    if (!V || !x || !out) return fail(ctx, GBD_ERR_ARG, "NULL pointer");
+    if (k < 1 || k > 32 || n < 0 || stride < n) return fail(ctx, GBD_ERR_ARG, "bad k, n or stride");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->multi_dot(V, stride, k, x, n, out);
+    return GBD_OK;
+  });
+}
+
 int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {
   if (!ctx || !s) return GBD_ERR_ARG;
   std::memset(s, 0, sizeof(*s));

@@ -1577,6 +1577,19 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out) 
   sync();
 }
 
+void Engine::multi_dot(const double* V, int64_t stride, int k, const double* x, int64_t n, double* out_host) {
+  int nblk = reduction_blocks(n);
+  double* partial = dalloc<double>((size_t)nblk * k);
+  double* dots = dalloc<double>(k);
+  launch_multi_dot(V, stride, k, x, n, dots, partial, nblk, stream);
+  stats.launches += 2;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out_host, dots, k * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  dfree(partial);
+  dfree(dots);
+}
+
 double Engine::run_step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept) {
   return step(k, dir, M, tol, tau, kept);
 }

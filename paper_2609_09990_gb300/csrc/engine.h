@@ -98,6 +98,7 @@ class Engine {
   int mpo_bond_dim(int bond) const { return (int)mpo.labels[bond].size(); }
   std::vector<uint64_t> mpo_labels(int bond) const;
   void env_block(int side, int bond, int channel, int sector, std::vector<double>& out, int& rows, int& cols);
+  void multi_dot(const double* V, int64_t stride, int k, const double* x, int64_t n, double* out_host);
 
   Stats stats;
   std::vector<double> sweep_E;

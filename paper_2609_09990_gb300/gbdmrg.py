@@ -85,6 +85,7 @@ def lib():
         "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32]),
         "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
+        "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
         "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
                                       _dp]),
@@ -228,6 +229,12 @@ class Context:
         self._check(self.L.gbd_env_block(self.ptr, side, bond, channel, sector, _d(out), out.size,
                                          C.byref(r), C.byref(c)), "gbd_env_block")
         return out.reshape(r.value, c.value)
+
+    def multi_dot(self, V_ptr, stride, k, x_ptr, n):
+        """out[j] = V_j . x over device pointers (e.g. torch tensor data_ptr())."""
+        out = np.zeros(k)
+        self._check(self.L.gbd_multi_dot(self.ptr, V_ptr, stride, k, x_ptr, n, _d(out)), "gbd_multi_dot")
+        return out
 
     def stats(self):
         s = gbd_stats()
