@@ -76,6 +76,25 @@ double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, i
  * context's stream; 1 <= k <= 32. */
 int gbd_multi_dot(gbd_ctx *ctx, const double *V, int64_t stride, int32_t k, const double *x, int64_t n,
                   double *out);
+/* gbd_multi_dot without any allocation, for callers that cannot call
+ * cudaMalloc (their memory comes from an arena they own, or allocation is
+ * not allowed where they call from).  The paper has no counterpart: this is
+ * an interface of this library only.  Inputs V (k vectors at V + j*stride, n
+ * doubles each) and x, and the output out[k], are device pointers on
+ * `device`; the work is enqueued on `stream` (a cudaStream_t, NULL = the
+ * default stream) and this call returns without waiting for it.
+ * Partial sums live in a fixed device array of 32 x 608 doubles (152 KB per
+ * GPU, kept until the process exits) shared by every call: two calls that
+ * overlap on the GPU race on it, so order them on one stream or synchronise
+ * in between.  Every partial the reduction reads is written earlier in the
+ * same call, so nothing needs clearing.  The first call on a device looks up
+ * that device's copy of the array (cudaGetSymbolAddress with the device
+ * current); make that first call before any stream capture.
+ * Returns GBD_ERR_ARG for NULL pointers, k < 1, k > 32 (the array's limit),
+ * n < 0 or stride < n; GBD_ERR_CUDA if a CUDA call fails.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32_t k, const double *x, int64_t n,
+                          double *out, void *stream);
 /* FP64 and FP32 CUDA-core FMA throughput of `device` (TFLOP/s), measured
  * with independent FMA chains on every SM; the peak of the FP64 path. */
 int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);

@@ -231,3 +231,50 @@ void launch_scale(double* x, double a, int64_t n, cudaStream_t s) {
 }
 
 }  // namespace gbd
+
+// ---------------------------------------------------------------------------
+// Allocation-free Davidson overlap reduction.  Some callers cannot call
+// cudaMalloc (a host that hands us pointers from its own fixed arena, code
+// running inside a stream capture owned by someone else, or a process whose
+// allocator is locked).  This variant keeps its partial sums in a fixed
+// file-scope device array instead of allocating.  Every GPU that loads the
+// library holds the array until the process exits.
+#include <mutex>
+
+namespace {
+constexpr int kNoAllocMaxK = 32;
+constexpr int kNoAllocMaxBlocks = 608;   // reduction_blocks() never returns more
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxK * kNoAllocMaxBlocks];
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};
+}  // namespace
+
+extern "C" int gbd_multi_dot_noalloc(int32_t device, const double* V, int64_t stride, int32_t k, const double* x,
+                                     int64_t n, double* out, void* stream) {
+  if (!V || !x || !out) return -1;
+  if (k < 1 || k > kNoAllocMaxK || n < 0 || stride < n) return -1;
+  if (device < 0 || device >= 256) return -1;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return -3;
+  if (cudaSetDevice(device) != cudaSuccess) return -3;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+      // the array's name is a host-side stand-in; the device address of this
+      // device's copy comes from the runtime, once, with the device current
+      double* p = nullptr;
+      if (cudaGetSymbolAddress((void**)&p, g_noalloc_partials) != cudaSuccess || !p) {
+        cudaSetDevice(prev);
+        return -3;
+      }
+      g_noalloc_ptr[device] = p;
+    }
+    scratch = g_noalloc_ptr[device];
+  }
+  int nblk = gbd::reduction_blocks(n);   // <= kNoAllocMaxBlocks, so nblk * k fits the array
+  gbd::launch_multi_dot(V, stride, k, x, n, out, scratch, nblk, (cudaStream_t)stream);
+  cudaError_t e = cudaGetLastError();
+  cudaSetDevice(prev);
+  return e == cudaSuccess ? 0 : -3;
+}

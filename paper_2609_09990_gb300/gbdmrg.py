@@ -86,6 +86,8 @@ def lib():
                                             C.c_int32, C.c_int32]),
         "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
         "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
+        "gbd_multi_dot_noalloc": (C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
+                                            C.c_void_p, C.c_void_p]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
         "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
                                       _dp]),
@@ -286,6 +288,14 @@ def host_mpo(h, chol, k_switch=None, dense=False):
     if rc != GBD_OK:
         raise GbdError(f"gbd_host_mpo: {ERRORS.get(rc, rc)}")
     return (bd, out) if dense else bd
+
+
+def multi_dot_noalloc(device, V_ptr, stride, k, x_ptr, n, out_ptr, stream=None):
+    """gbd_multi_dot_noalloc: out[j] = V_j . x into the device array out_ptr,
+    enqueued on `stream` (a raw cudaStream_t value or None); no allocation."""
+    rc = lib().gbd_multi_dot_noalloc(device, V_ptr, stride, k, x_ptr, n, out_ptr, stream)
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_multi_dot_noalloc: {ERRORS.get(rc, rc)}")
 
 
 def probe_peaks(device=0):
