@@ -59,6 +59,9 @@ int gbd_apply_heff(gbd_ctx *ctx, int32_t k, const double *in, double *out, doubl
  * order (cap entries, count in *nkept). */
 int gbd_run_step(gbd_ctx *ctx, int32_t k, int32_t dir, int32_t M, double tol, double *energy,
                  double *discarded, double *kept, int32_t cap, int32_t *nkept);
+/* One- and two-particle RDMs of the current MPS (conventions of
+ * gbd_result); rdm1 [n^2], rdm2 [n^4] or NULL. */
+int gbd_rdms(gbd_ctx *ctx, double *rdm1, double *rdm2);
 /* MPO channel keys of one bond (kind<<40 | nops<<32 | code0<<16 | code1). */
 int gbd_mpo_labels(gbd_ctx *ctx, int32_t bond, uint64_t *keys, int32_t cap, int32_t *count);
 /* One environment block (side 0 = left, 1 = right) for (channel, sector index). */

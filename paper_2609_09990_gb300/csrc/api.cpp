@@ -253,6 +253,14 @@ int gbd_run_step(gbd_ctx* ctx, int32_t k, int32_t dir, int32_t M, double tol, do
   });
 }
 
+int gbd_rdms(gbd_ctx* ctx, double* rdm1, double* rdm2) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    ctx->eng->rdms(rdm1, rdm2);
+    return GBD_OK;
+  });
+}
+
 int gbd_mpo_labels(gbd_ctx* ctx, int32_t bond, uint64_t* keys, int32_t cap, int32_t* count) {
   return guarded(ctx, [&]() {
     if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");

@@ -34,15 +34,6 @@
 
 namespace gbd {
 
-#define CK(x)                                                                                      \
-  do {                                                                                             \
-    cudaError_t e_ = (x);                                                                          \
-    if (e_ != cudaSuccess)                                                                         \
-      throw Error(e_ == cudaErrorMemoryAllocation ? -2 : -3,                                      \
-                  std::string(#x) + ": " + cudaGetErrorString(e_) + " (line " +                  \
-                      std::to_string(__LINE__) + ")");                                             \
-  } while (0)
-
 void Bond::finalize() {
   std::vector<int> ord(na.size());
   std::iota(ord.begin(), ord.end(), 0);
@@ -1609,5 +1600,7 @@ void Engine::env_block(int side, int bond, int ch, int sec, std::vector<double>&
 }  // namespace gbd
 
 namespace gbd {
-void Engine::rdms(double*, double*) { throw Error(-6, "RDMs are not built in this library yet"); }
+template double* Engine::dalloc<double>(size_t);
+template int* Engine::dalloc<int>(size_t);
+template signed char* Engine::dalloc<signed char>(size_t);
 }  // namespace gbd

@@ -17,6 +17,16 @@ struct Error : std::runtime_error {
   Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
+#define CK(x)                                                                                      \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ != cudaSuccess)                                                                         \
+      throw Error(e_ == cudaErrorMemoryAllocation ? -2 : -3,                                      \
+                  std::string(#x) + ": " + cudaGetErrorString(e_) + " (line " +                  \
+                      std::to_string(__LINE__) + ")");                                             \
+  } while (0)
+
+
 // Enlarged space over a list of sectors Q: E_L(Q) = concat_s (Q - s) from a
 // left bond, or E_R(Q) = concat_s (Q + s) from a right bond.
 struct Space {

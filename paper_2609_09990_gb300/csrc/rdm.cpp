@@ -1,0 +1,349 @@
+// One- and two-particle RDMs of the current MPS (paper: device k-RDMs of the
+// converged MPS, Sec. "The DMRG-QD-NEVPT2 energy" and Sec. "Computational
+// details"):
+//   gamma_pq = sum_s <a+_ps a_qs>,  Gamma_pqrs = sum_st <a+_ps a+_rt a_st a_qs>
+//            = <E_pq E_rs> - delta_qr gamma_ps.
+// The MPS is expanded into the determinant basis |I_a, I_b> (alpha creators,
+// then beta creators, strings in colex order addr = sum_i C(o_i, i+1)):
+// prefix vectors (sites < h) and suffix vectors (sites >= h) are built by
+// grouped GEMMs and multiplied at the middle bond h, then scattered with the
+// sign that reorders site-major creators into alpha-first order.  With
+// D[pq] = E_pq C (formed in chunks of alpha strings), gamma_pq = C . D[pq]
+// and <E_pq E_rs> = D[qp] . D[rs] is one split-K Gram GEMM.  FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "engine.h"
+
+namespace gbd {
+
+void launch_scatter_ci(const double* A, int npref, int nsuf, const int* aP, const int* bP, const signed char* sP,
+                       const int* aS, const int* bS, const signed char* sS, double sector_sign, int64_t Nb,
+                       double* C, cudaStream_t s);
+void launch_apply_e_chunk(const double* C, int64_t Nb, const int* excA, const int* excB, int n2, int ja0, int cs,
+                          double* D, cudaStream_t s);
+
+namespace {
+
+double binom_i(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  double r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return std::round(r);
+}
+
+int colex(uint32_t bits, int n) {
+  int addr = 0, pos = 0;
+  for (int o = 0; o < n; ++o)
+    if (bits >> o & 1u) addr += (int)binom_i(o, ++pos);
+  return addr;
+}
+
+// all k-subsets of n orbitals indexed by colex address
+std::vector<uint32_t> strings(int n, int k) {
+  std::vector<uint32_t> out((size_t)binom_i(n, k));
+  std::vector<int> c(k);
+  for (int i = 0; i < k; ++i) c[i] = i;
+  while (true) {
+    uint32_t b = 0;
+    for (int x : c) b |= 1u << x;
+    out[colex(b, n)] = b;
+    int i = k - 1;
+    while (i >= 0 && c[i] == n - k + i) --i;
+    if (i < 0) break;
+    ++c[i];
+    for (int j = i + 1; j < k; ++j) c[j] = c[j - 1] + 1;
+  }
+  return out;
+}
+
+// exc[J * n^2 + p*n + q] = (I + 1) * sign with E_pq |I> = sign |J>, else 0
+std::vector<int> excitations(int n, int k) {
+  auto str = strings(n, k);
+  int n2 = n * n;
+  std::vector<int> exc(str.size() * n2, 0);
+  for (size_t I = 0; I < str.size(); ++I) {
+    uint32_t b = str[I];
+    for (int q = 0; q < n; ++q) {
+      if (!(b >> q & 1u)) continue;
+      int sq = __builtin_popcount(b & ((1u << q) - 1u)) & 1;
+      uint32_t rest = b & ~(1u << q);
+      for (int p = 0; p < n; ++p) {
+        if (rest >> p & 1u) continue;
+        int sp = __builtin_popcount(rest & ((1u << p) - 1u)) & 1;
+        uint32_t jb = rest | (1u << p);
+        int J = colex(jb, n);
+        exc[(size_t)J * n2 + p * n + q] = ((sq ^ sp) ? -1 : 1) * ((int)I + 1);
+      }
+    }
+  }
+  return exc;
+}
+
+}  // namespace
+
+void Engine::rdms(double* rdm1, double* rdm2) {
+  const int h = n / 2;
+  const int64_t Na_str = (int64_t)binom_i(n, Na), Nb_str = (int64_t)binom_i(n, Nb);
+  const int64_t ndet = Na_str * Nb_str;
+  if (ndet > (int64_t)400000000) throw Error(-1, "RDMs need the determinant expansion; too many determinants");
+  // site block X_i(q, s): m_i(q) x m_{i+1}(q+s) with its leading dimension
+  auto block = [&](int i, int qi, int s, int& ld) -> const double* {
+    const Bond& bl = bonds[i];
+    const Bond& br = bonds[i + 1];
+    const Site& S = sites[i];
+    int r = br.find(bl.na[qi] + QA[s], bl.nb[qi] + QB[s]);
+    if (r < 0) return nullptr;
+    if (S.layout == 1) {
+      int coff = 0, cols = 0;
+      for (int t = 0; t < 4; ++t) {
+        int rr = br.find(bl.na[qi] + QA[t], bl.nb[qi] + QB[t]);
+        if (rr < 0) continue;
+        if (t < s) coff += br.dim[rr];
+        cols += br.dim[rr];
+      }
+      ld = cols;
+      return S.d + S.off[qi] + coff;
+    }
+    int roff = 0;
+    for (int t = 0; t < s; ++t) {
+      int jj = bl.find(br.na[r] - QA[t], br.nb[r] - QB[t]);
+      if (jj >= 0) roff += bl.dim[jj];
+    }
+    ld = br.dim[r];
+    return S.d + S.off[r] + (int64_t)roff * br.dim[r];
+  };
+  // ---- prefixes (sites < h), rows of P_i(q)
+  struct Fix { std::vector<uint32_t> a, b; double* d = nullptr; };
+  std::vector<Fix> pre(1);
+  pre[0].a = {0};
+  pre[0].b = {0};
+  pre[0].d = dalloc<double>(1);
+  {
+    double one = 1.0;
+    CK(cudaMemcpyAsync(pre[0].d, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  }
+  for (int i = 0; i < h; ++i) {
+    const Bond& bl = bonds[i];
+    const Bond& br = bonds[i + 1];
+    std::vector<Fix> nx(br.nsec());
+    GemmPlan p;
+    for (int j = 0; j < br.nsec(); ++j) {
+      Fix& f = nx[j];
+      std::vector<std::pair<int, int>> parts;   // (parent sector, s)
+      for (int s = 0; s < 4; ++s) {
+        int qi = bl.find(br.na[j] - QA[s], br.nb[j] - QB[s]);
+        if (qi < 0 || pre[qi].a.empty()) continue;
+        parts.push_back({qi, s});
+        for (size_t t = 0; t < pre[qi].a.size(); ++t) {
+          f.a.push_back(pre[qi].a[t] | ((uint32_t)QA[s] << i));
+          f.b.push_back(pre[qi].b[t] | ((uint32_t)QB[s] << i));
+        }
+      }
+      if (f.a.empty()) continue;
+      int mr = br.dim[j];
+      f.d = dalloc<double>(f.a.size() * (size_t)mr);
+      int64_t row = 0;
+      for (auto& pr : parts) {
+        int qi = pr.first, s = pr.second;
+        int np = (int)pre[qi].a.size();
+        int ld = 0;
+        const double* X = block(i, qi, s, ld);
+        p.add_out(f.d + row * mr, mr, np, mr, 0);
+        p.add_term(pre[qi].d, bl.dim[qi], X, ld, bl.dim[qi], 0, 1.0);
+        row += np;
+      }
+    }
+    upload(p);
+    run(p);
+    release(p);
+    for (auto& f : pre) if (f.d) dfree(f.d);
+    pre.swap(nx);
+  }
+  // ---- suffixes (sites >= h), columns of R_i(q)
+  std::vector<Fix> suf(bonds[n].nsec());
+  {
+    int qi = 0;
+    suf[qi].a = {0};
+    suf[qi].b = {0};
+    suf[qi].d = dalloc<double>(1);
+    double one = 1.0;
+    CK(cudaMemcpyAsync(suf[qi].d, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  }
+  for (int i = n - 1; i >= h; --i) {
+    const Bond& bl = bonds[i];
+    const Bond& br = bonds[i + 1];
+    std::vector<Fix> nx(bl.nsec());
+    GemmPlan p;
+    for (int j = 0; j < bl.nsec(); ++j) {
+      Fix& f = nx[j];
+      std::vector<std::pair<int, int>> parts;   // (child sector, s)
+      for (int s = 0; s < 4; ++s) {
+        int r = br.find(bl.na[j] + QA[s], bl.nb[j] + QB[s]);
+        if (r < 0 || suf[r].a.empty()) continue;
+        parts.push_back({r, s});
+        for (size_t t = 0; t < suf[r].a.size(); ++t) {
+          f.a.push_back(suf[r].a[t] | ((uint32_t)QA[s] << i));
+          f.b.push_back(suf[r].b[t] | ((uint32_t)QB[s] << i));
+        }
+      }
+      if (f.a.empty()) continue;
+      int ncols = (int)f.a.size();
+      f.d = dalloc<double>((size_t)bl.dim[j] * ncols);
+      int64_t col = 0;
+      for (auto& pr : parts) {
+        int r = pr.first, s = pr.second;
+        int ns = (int)suf[r].a.size();
+        int ld = 0;
+        const double* X = block(i, j, s, ld);
+        p.add_out(f.d + col, ncols, bl.dim[j], ns, 0);
+        p.add_term(X, ld, suf[r].d, ns, br.dim[r], 0, 1.0);
+        col += ns;
+      }
+    }
+    upload(p);
+    run(p);
+    release(p);
+    for (auto& f : suf) if (f.d) dfree(f.d);
+    suf.swap(nx);
+  }
+  // ---- amplitudes at the middle bond, scattered into C[Ia, Ib]
+  double* C = dalloc<double>(ndet);
+  CK(cudaMemsetAsync(C, 0, ndet * sizeof(double), stream));
+  const Bond& bh = bonds[h];
+  for (int j = 0; j < bh.nsec(); ++j) {
+    if (pre[j].a.empty() || suf[j].a.empty()) continue;
+    int a = bh.na[j], b = bh.nb[j];
+    int np = (int)pre[j].a.size(), ns = (int)suf[j].a.size(), m = bh.dim[j];
+    double* A = dalloc<double>((size_t)np * ns);
+    GemmPlan p;
+    p.add_out(A, ns, np, ns, 0);
+    p.add_term(pre[j].d, m, suf[j].d, ns, m, 0, 1.0);
+    upload(p);
+    run(p);
+    release(p);
+    std::vector<int> aP(np), bP(np), aS(ns), bS(ns);
+    std::vector<signed char> sP(np), sS(ns);
+    auto addr_from = [&](uint32_t bits, int pos0) {
+      int ad = 0, pos = pos0;
+      for (int o = 0; o < n; ++o)
+        if (bits >> o & 1u) ad += (int)binom_i(o, ++pos);
+      return ad;
+    };
+    auto sign_of = [&](uint32_t ab, uint32_t bb) {
+      int ex = 0;
+      for (int jj = 0; jj < n; ++jj)
+        if (bb >> jj & 1u) ex += __builtin_popcount(ab >> (jj + 1));
+      return (signed char)((ex & 1) ? -1 : 1);
+    };
+    for (int t = 0; t < np; ++t) {
+      aP[t] = addr_from(pre[j].a[t], 0);
+      bP[t] = addr_from(pre[j].b[t], 0);
+      sP[t] = sign_of(pre[j].a[t], pre[j].b[t]);
+    }
+    for (int t = 0; t < ns; ++t) {
+      aS[t] = addr_from(suf[j].a[t], a);
+      bS[t] = addr_from(suf[j].b[t], b);
+      sS[t] = sign_of(suf[j].a[t], suf[j].b[t]);
+    }
+    double ssec = ((b * (Na - a)) & 1) ? -1.0 : 1.0;
+    int* d_i = dalloc<int>(2 * (size_t)np + 2 * (size_t)ns);
+    signed char* d_s = dalloc<signed char>((size_t)np + ns);
+    CK(cudaMemcpyAsync(d_i, aP.data(), np * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_i + np, bP.data(), np * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_i + 2 * np, aS.data(), ns * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_i + 2 * np + ns, bS.data(), ns * sizeof(int), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_s, sP.data(), np, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_s + np, sS.data(), ns, cudaMemcpyHostToDevice, stream));
+    launch_scatter_ci(A, np, ns, d_i, d_i + np, d_s, d_i + 2 * np, d_i + 2 * np + ns, d_s + np, ssec, Nb_str, C,
+                      stream);
+    stats.launches++;
+    CK(cudaGetLastError());
+    sync();
+    dfree(A);
+    dfree(d_i);
+    dfree(d_s);
+  }
+  for (auto& f : pre) if (f.d) dfree(f.d);
+  for (auto& f : suf) if (f.d) dfree(f.d);
+  // ---- D[pq] = E_pq C in chunks of alpha strings; gamma and <E E> by GEMM
+  const int n2 = n * n;
+  auto excA = excitations(n, Na), excB = excitations(n, Nb);
+  int* d_excA = dalloc<int>(excA.size());
+  int* d_excB = dalloc<int>(excB.size());
+  CK(cudaMemcpyAsync(d_excA, excA.data(), excA.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(d_excB, excB.data(), excB.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  int64_t budget = (int64_t)1 << 27;   // doubles per D chunk (1 GiB)
+  int cs = (int)std::max<int64_t>(1, std::min<int64_t>(Na_str, budget / ((int64_t)n2 * Nb_str)));
+  double* D = dalloc<double>((size_t)n2 * cs * Nb_str);
+  const int SPLIT = 32;
+  double* Mp = dalloc<double>((size_t)SPLIT * n2 * n2);
+  double* gp = dalloc<double>((size_t)SPLIT * n2);
+  bool first = true;
+  for (int ja0 = 0; ja0 < Na_str; ja0 += cs) {
+    int c = (int)std::min<int64_t>(cs, Na_str - ja0);
+    launch_apply_e_chunk(C, Nb_str, d_excA, d_excB, n2, ja0, c, D, stream);
+    stats.launches++;
+    CK(cudaGetLastError());
+    int64_t K = (int64_t)c * Nb_str;
+    int parts = (int)std::min<int64_t>(SPLIT, std::max<int64_t>(1, K / 4096));
+    int64_t step = (K + parts - 1) / parts;
+    GemmPlan p;
+    const double* Cchunk = C + (int64_t)ja0 * Nb_str;
+    for (int s = 0; s < SPLIT; ++s) {
+      int64_t k0 = (int64_t)s * step, k1 = std::min<int64_t>(K, k0 + step);
+      p.add_out(Mp + (size_t)s * n2 * n2, n2, n2, n2, first ? 0 : 1);
+      if (s < parts && k1 > k0) p.add_term(D + k0, (int)K, D + k0, (int)K, (int)(k1 - k0), 2, 1.0);
+      p.add_out(gp + (size_t)s * n2, 1, n2, 1, first ? 0 : 1);
+      if (s < parts && k1 > k0) p.add_term(D + k0, (int)K, Cchunk + k0, 1, (int)(k1 - k0), 0, 1.0);
+    }
+    upload(p);
+    run(p);
+    release(p);
+    first = false;
+  }
+  // sum the split-K partials and read back
+  double* Msum = dalloc<double>((size_t)n2 * n2 + n2);
+  AxpyPlan ax;
+  ax.outs.push_back({Msum, (int64_t)n2 * n2, 0, 0});
+  for (int s = 0; s < SPLIT; ++s) ax.terms.push_back({Mp + (size_t)s * n2 * n2, 1.0});
+  ax.outs.back().t1 = (int)ax.terms.size();
+  ax.outs.push_back({Msum + (size_t)n2 * n2, (int64_t)n2, (int)ax.terms.size(), 0});
+  for (int s = 0; s < SPLIT; ++s) ax.terms.push_back({gp + (size_t)s * n2, 1.0});
+  ax.outs.back().t1 = (int)ax.terms.size();
+  upload(ax);
+  run(ax);
+  release(ax);
+  int nblk = reduction_blocks(ndet);
+  double* partial = dalloc<double>(nblk);
+  double* nrm_d = dalloc<double>(1);
+  launch_multi_dot(C, ndet, 1, C, ndet, nrm_d, partial, nblk, stream);
+  stats.launches += 2;
+  std::vector<double> Mh((size_t)n2 * n2 + n2);
+  double nrm2 = 0;
+  CK(cudaMemcpyAsync(Mh.data(), Msum, Mh.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(&nrm2, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  stats.d2h += (Mh.size() + 1) * sizeof(double);
+  for (void* q : {(void*)C, (void*)d_excA, (void*)d_excB, (void*)D, (void*)Mp, (void*)gp, (void*)Msum,
+                  (void*)partial, (void*)nrm_d})
+    dfree(q);
+  if (!(nrm2 > 0)) throw Error(-4, "MPS has zero norm in the determinant expansion");
+  const double* M = Mh.data();
+  const double* g = Mh.data() + (size_t)n2 * n2;
+  std::vector<double> g1(n2);
+  for (int i = 0; i < n2; ++i) g1[i] = g[i] / nrm2;
+  if (rdm1) std::memcpy(rdm1, g1.data(), n2 * sizeof(double));
+  if (rdm2)
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q)
+        for (int r = 0; r < n; ++r)
+          for (int s = 0; s < n; ++s) {
+            double v = M[(size_t)(q * n + p) * n2 + r * n + s] / nrm2;
+            if (q == r) v -= g1[p * n + s];
+            rdm2[(((size_t)p * n + q) * n + r) * n + s] = v;
+          }
+}
+
+}  // namespace gbd

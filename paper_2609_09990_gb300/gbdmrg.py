@@ -79,6 +79,7 @@ def lib():
         "gbd_apply_heff": (C.c_int, [vp, C.c_int32, _dp, _dp, _dp]),
         "gbd_run_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp,
                                    C.c_int32, _ip]),
+        "gbd_rdms": (C.c_int, [vp, _dp, _dp]),
         "gbd_mpo_labels": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, _ip]),
         "gbd_env_block": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_int64, _ip, _ip]),
         "gbd_get_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
@@ -214,6 +215,12 @@ class Context:
         self._check(self.L.gbd_run_step(self.ptr, k, direction, M, tol, C.byref(e), C.byref(tau), _d(kept),
                                         len(kept), C.byref(nk)), "gbd_run_step")
         return e.value, tau.value, kept[:nk.value].copy()
+
+    def rdms(self, n):
+        r1 = np.zeros((n, n))
+        r2 = np.zeros((n, n, n, n))
+        self._check(self.L.gbd_rdms(self.ptr, _d(r1), _d(r2)), "gbd_rdms")
+        return r1, r2
 
     def mpo_labels(self, bond):
         cnt = C.c_int32()
