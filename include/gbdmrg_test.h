@@ -98,6 +98,13 @@ int gbd_multi_dot(gbd_ctx *ctx, const double *V, int64_t stride, int32_t k, cons
  * cudaFree or allocating library routine is called. */
 int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32_t k, const double *x, int64_t n,
                           double *out, void *stream);
+/* Self-test of the tensor-core grouped GEMM (tcgen05 + TMA): nterms random
+ * products of M x K by K x N in precision prec (0 BF16, 1 TF32, 2 TF32x3)
+ * accumulated in TMEM, against an FP64 host product of the operands as
+ * stored (BF16/TF32) or of the FP64 originals (TF32x3).  Returns the largest
+ * absolute error and the largest |reference| element. */
+int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t nterms, uint64_t seed,
+                    double *max_err, double *max_ref);
 /* FP64 and FP32 CUDA-core FMA throughput of `device` (TFLOP/s), measured
  * with independent FMA chains on every SM; the peak of the FP64 path. */
 int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);

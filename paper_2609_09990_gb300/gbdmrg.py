@@ -86,6 +86,8 @@ def lib():
         "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32]),
         "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
+        "gbd_tc_selftest": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                      _dp, _dp]),
         "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
         "gbd_multi_dot_noalloc": (C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                             C.c_void_p, C.c_void_p]),
@@ -303,6 +305,15 @@ def multi_dot_noalloc(device, V_ptr, stride, k, x_ptr, n, out_ptr, stream=None):
     rc = lib().gbd_multi_dot_noalloc(device, V_ptr, stride, k, x_ptr, n, out_ptr, stream)
     if rc != GBD_OK:
         raise GbdError(f"gbd_multi_dot_noalloc: {ERRORS.get(rc, rc)}")
+
+
+def tc_selftest(prec, M, N, K, nterms, seed=1, device=0):
+    """(max |error|, max |reference|) of the tensor-core grouped GEMM self-test."""
+    e, r = C.c_double(), C.c_double()
+    rc = lib().gbd_tc_selftest(device, prec, M, N, K, nterms, seed, C.byref(e), C.byref(r))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_tc_selftest: {ERRORS.get(rc, rc)}")
+    return e.value, r.value
 
 
 def probe_peaks(device=0):
