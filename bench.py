@@ -112,7 +112,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     ctx = G.Context(dev)
     nsw = args.warmup + args.steps
-    ctx.setup(h, chol, ne, 0, [M] * nsw, schedule(nsw, args.tol), seed=seed, precision=prec)
+    ctx.setup(h, chol, ne, 0, [M] * (nsw + 1), schedule(nsw + 1, args.tol), seed=seed, precision=prec,
+              fp64_refine=args.refine)
     ctx.init_state()
     for s in range(args.warmup):
         ctx.run_sweep(s)
@@ -131,9 +132,25 @@ def run_ours(args, rank, world):
     clocks = clk.stop()
     st1 = ctx.stats()
     dt = t1 - t0
+    keys = ["sigma_ms", "tc_ms", "env_ms", "enlarge_ms", "davidson_ms", "truncate_ms", "step_ms"]
+    breakdown = {k: (st1[k] - st0[k]) / args.steps for k in keys}
+    breakdown["sigma_builds"] = (st1["n_sigma"] - st0["n_sigma"]) / args.steps
+    breakdown["tc_sigma_builds"] = (st1["n_sigma_tc"] - st0["n_sigma_tc"]) / args.steps
     flops = st1["sigma_flops"] - st0["sigma_flops"]
     sig_ms = st1["sigma_ms"] - st0["sigma_ms"]
+    tc_ms = st1["tc_ms"] - st0["tc_ms"]
+    tc_flops = st1["tc_flops"] - st0["tc_flops"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
+    e_final = ctx.final_energy()
+    fp64 = None
+    if prec != 0 and args.compare_fp64:
+        # one sweep of the plain FP64 path from the same warmed state
+        ctx.set_precision(0, 0)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        e64 = ctx.run_sweep(nsw)
+        torch.cuda.synchronize()
+        fp64 = dict(sweep_s=time.perf_counter() - t4, sweep_energy=e64, final_energy=ctx.final_energy())
     ctx.close()
     # end to end through gbd_solve: host integrals in, energies out
     e2e = None
@@ -142,14 +159,15 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         r = ctx.solve(h, chol, ne, 0, [M] * args.steps, schedule(args.steps, args.tol), seed=seed,
-                      precision=prec)
+                      precision=prec, fp64_refine=args.refine)
         t3 = time.perf_counter()
         se = ctx.stats()
         ctx.close()
         e2e = dict(flops=se["sigma_flops"], time=t3 - t2, h2d=int(h.nbytes + chol.nbytes),
                    d2h=int(8 * (1 + args.steps)), energy=r["energy"])
     return dict(time=dt, flops=flops, sigma_ms=sig_ms, launches=launches, clocks=clocks,
-                energies=energies, e2e=e2e, n=n, M=M, st=st1)
+                energies=energies, e2e=e2e, n=n, M=M, st=st1, tc_ms=tc_ms, tc_flops=tc_flops,
+                e_final=e_final, fp64=fp64, breakdown=breakdown)
 
 
 def dist_barrier(world):
@@ -220,6 +238,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--refine", type=int, default=2, help="FP64 Davidson iterations after the tensor-core tiers")
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,17 +289,30 @@ def main():
     if args.precision == "fp64":
         # FP64 runs on the CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
         peak, bound, punit, kind = 152 * 2 * 2 * 2.07e9 / 1e12, "alu", "TFLOP/s", "derived (FP64 unit count x max clock)"
+        kname, achieved = "gemm_f64_kernel (sigma stages A+B)", kern_tflops
     else:
-        peak, bound, punit, kind = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s", pk_kind
-    roof = {"bound": bound, "achieved": kern_tflops, "peak": peak, "unit": punit, "frac": kern_tflops / peak,
-            "traffic": None, "kernel": "gemm_f64_kernel (sigma stages A+B)", "peak_kind": kind}
+        # tensor-core sigma builds of every tier (BF16/TF32 single pass and
+        # TF32x3), algorithmic flops over their device time, against the
+        # measured sustained BF16 peak
+        peak, bound, punit, kind = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s", pk_kind + " (bf16 sustained)"
+        kname = "tc_gemm_kernel (tcgen05; sigma stages A+B, all tiers)"
+        achieved = res["tc_flops"] / (res["tc_ms"] / 1000) / 1e12 if res["tc_ms"] > 0 else 0.0
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak,
+            "traffic": None, "kernel": kname, "peak_kind": kind}
     line = {"metric": "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512", "value": flops / tmax / 1e12,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic", "config": config,
             "sweep_time_s": tmax / args.steps, "sweep_energies": res["energies"],
-            "sigma_kernel_tflops": kern_tflops, "roofline": roof, "clocks": res["clocks"],
+            "sigma_kernel_tflops": kern_tflops, "final_energy": res["e_final"],
+            "per_sweep": res["breakdown"], "roofline": roof,
+            "clocks": res["clocks"],
             "gpu_launches": int(res["launches"])}
+    if res["fp64"]:
+        line["fp64_gpu_sweep_s"] = res["fp64"]["sweep_s"]
+        line["speedup_vs_fp64_sweep"] = res["fp64"]["sweep_s"] / (tmax / args.steps)
+        line["fp64_sweep_final_energy"] = res["fp64"]["final_energy"]
+        line["energy_change_after_fp64_sweep"] = res["fp64"]["final_energy"] - res["e_final"]
     if res["e2e"]:
         e = res["e2e"]
         line["e2e"] = {"value": e["flops"] / e["time"] / 1e12, "unit": "TFLOP/s",

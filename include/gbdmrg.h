@@ -37,9 +37,11 @@ extern "C" {
 #define GBD_ERR_TIMEOUT (-5)  /* a bounded device wait ran out */
 #define GBD_ERR_STATE (-6)    /* call order violated (e.g. sweep before prepare) */
 
-/* precision of the bulk contractions (sigma build and environment update);
- * Davidson orthogonalisation, Rayleigh-Ritz, decimation and the final energy
- * are FP64 in every mode */
+/* precision of the Davidson matvecs (sigma build).  GBD_TF32 / GBD_BF16:
+ * tensor-core tiers -- the named precision while ||r|| is large, then TF32x3
+ * (split TF32 hi/lo, FP32 accumulation) -- then optional FP64 refinement.
+ * Environments, H_eff diagonal, Davidson orthogonalisation, Rayleigh-Ritz,
+ * decimation and the final energy are FP64 in every mode. */
 #define GBD_FP64 0
 #define GBD_TF32 1
 #define GBD_BF16 2
@@ -80,6 +82,9 @@ typedef struct {
   int32_t preconditioner;         /* GBD_PRECOND_DIAG | GBD_PRECOND_LEARNED */
   uint64_t seed;
   double svd_cutoff;
+  int32_t fp64_refine;            /* GBD_TF32/GBD_BF16: at most this many FP64
+                                     Davidson iterations after the tensor-core
+                                     tiers when ||r|| is still above tol (0 = none) */
 } gbd_schedule;
 
 /* Results.  sweep_energies: [n_sweeps] caller-owned (may be NULL); rdm1

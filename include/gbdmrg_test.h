@@ -32,10 +32,16 @@ typedef struct {
   double davidson_ms, truncate_ms, step_ms;
   int64_t n_sigma, n_steps, kernel_launches, h2d_bytes, d2h_bytes;
   double max_discarded_weight;
+  double sigma_flops_exec;   /* flops executed by the tensor-core tiles (with padding) */
+  double tc_ms, tc_flops;    /* tensor-core sigma builds only: device time, algorithmic flops */
+  int64_t n_sigma_tc;
 } gbd_stats;
 
 /* Validate the problem and schedule, build the MPO; no MPS yet. */
 int gbd_setup(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule);
+/* Change the matvec precision (and FP64 refinement limit) of the current
+ * state for the following sweeps. */
+int gbd_set_precision(gbd_ctx *ctx, int32_t precision, int32_t fp64_refine);
 /* Seeded initial MPS (right-canonical) and all right environments. */
 int gbd_init_state(gbd_ctx *ctx);
 /* One full sweep with the schedule's entry `sweep`; energy = last Ritz value. */
@@ -53,6 +59,9 @@ int gbd_set_mps(gbd_ctx *ctx, const int32_t *n_sectors, const int32_t *sectors, 
 int gbd_two_site_size(gbd_ctx *ctx, int32_t k, int64_t *size);
 /* out = H_eff in (two-site format); diag (may be NULL) = diagonal of H_eff. */
 int gbd_apply_heff(gbd_ctx *ctx, int32_t k, const double *in, double *out, double *diag);
+/* out = H_eff in through the tensor-core sigma: prec 1 TF32, 2 BF16,
+ * 3 TF32x3 (0 = the FP64 path, same as gbd_apply_heff). */
+int gbd_apply_heff_prec(gbd_ctx *ctx, int32_t k, int32_t prec, const double *in, double *out);
 /* One two-site step at (k, k+1): Davidson from the current two-site state,
  * decimation to at most M states and the environment update.  dir 0 = left
  * to right, 1 = right to left.  kept: the kept weights sigma^2 in descending

@@ -76,7 +76,7 @@ int validate(gbd_ctx* c, const gbd_problem* p, const gbd_schedule* s) {
     return fail(c, GBD_ERR_ARG, "davidson_max_subspace must be >= 5");
   if (s->precision != GBD_FP64 && s->precision != GBD_TF32 && s->precision != GBD_BF16)
     return fail(c, GBD_ERR_ARG, "unknown precision");
-  if (s->precision != GBD_FP64) return fail(c, GBD_ERR_ARG, "reduced-precision contractions are not built in this library");
+  if (s->fp64_refine < 0) return fail(c, GBD_ERR_ARG, "fp64_refine < 0");
   if (s->preconditioner != GBD_PRECOND_DIAG && s->preconditioner != GBD_PRECOND_LEARNED)
     return fail(c, GBD_ERR_ARG, "unknown preconditioner");
   if (s->preconditioner != GBD_PRECOND_DIAG) return fail(c, GBD_ERR_ARG, "learned preconditioner not loaded");
@@ -96,6 +96,7 @@ gbd::Schedule to_schedule(const gbd_schedule* s) {
   out.precond = s->preconditioner;
   out.seed = s->seed;
   out.cutoff = s->svd_cutoff > 0 ? s->svd_cutoff : 1e-12;
+  out.refine = s->fp64_refine;
   return out;
 }
 
@@ -157,6 +158,16 @@ int gbd_solve(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, gbd_res
 
 int gbd_setup(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s) {
   return guarded(ctx, [&]() { return setup(ctx, p, s); });
+}
+
+int gbd_set_precision(gbd_ctx* ctx, int32_t precision, int32_t fp64_refine) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    if (precision < 0 || precision > 2 || fp64_refine < 0) return fail(ctx, GBD_ERR_ARG, "bad precision");
+    ctx->eng->sched.precision = precision;
+    ctx->eng->sched.refine = fp64_refine;
+    return GBD_OK;
+  });
 }
 
 int gbd_init_state(gbd_ctx* ctx) {
@@ -228,6 +239,17 @@ int gbd_apply_heff(gbd_ctx* ctx, int32_t k, const double* in, double* out, doubl
     if (k < 0 || k > ctx->eng->n - 2) return fail(ctx, GBD_ERR_ARG, "k out of range");
     if (!in || !out) return fail(ctx, GBD_ERR_ARG, "NULL vector");
     ctx->eng->apply_heff(k, in, out, diag);
+    return GBD_OK;
+  });
+}
+
+int gbd_apply_heff_prec(gbd_ctx* ctx, int32_t k, int32_t prec, const double* in, double* out) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    if (k < 0 || k > ctx->eng->n - 2) return fail(ctx, GBD_ERR_ARG, "k out of range");
+    if (prec < 0 || prec > 3) return fail(ctx, GBD_ERR_ARG, "prec must be 0..3");
+    if (!in || !out) return fail(ctx, GBD_ERR_ARG, "NULL vector");
+    ctx->eng->apply_heff(k, in, out, nullptr, prec);
     return GBD_OK;
   });
 }
@@ -326,6 +348,10 @@ int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {
   s->h2d_bytes = t.h2d;
   s->d2h_bytes = t.d2h;
   s->max_discarded_weight = t.max_discarded;
+  s->sigma_flops_exec = t.sigma_flops_exec;
+  s->tc_ms = t.tc_ms;
+  s->tc_flops = t.tc_flops;
+  s->n_sigma_tc = t.n_sigma_tc;
   return GBD_OK;
 }
 

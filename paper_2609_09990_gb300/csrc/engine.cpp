@@ -31,6 +31,7 @@
 #include <thread>
 
 #include "linalg_host.h"
+#include "tc_gemm.h"
 
 namespace gbd {
 
@@ -202,6 +203,7 @@ std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, d
 // ------------------------------------------------------------------ basics
 Engine::Engine(int dev) : device(dev) {
   CK(cudaSetDevice(device));
+  CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
   CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
@@ -221,16 +223,6 @@ Engine::~Engine() {
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (stream) cudaStreamDestroy(stream);
-}
-
-template <class T>
-T* Engine::dalloc(size_t n) {
-  void* p = nullptr;
-  if (n == 0) n = 1;
-  cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), stream);
-  if (e != cudaSuccess) throw Error(-2, std::string("device allocation failed: ") + cudaGetErrorString(e));
-  allocs[(uintptr_t)p] = n * sizeof(T);
-  return (T*)p;
 }
 
 void Engine::dfree(void* p) {
@@ -969,7 +961,8 @@ void Engine::compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag) {
 // the host, vectors on the device; preconditioner t = -r / (diag - theta)
 // with |diag - theta| clamped to 1e-8; two classical Gram-Schmidt passes;
 // restart from the 4 lowest Ritz vectors when the space is full.
-double Engine::davidson(Sigma& sg, const double* diag, double tol, int max_iter, int max_space) {
+double Engine::davidson(const std::function<void(const double*, double*)>& op, const double* diag, double tol,
+                        int max_iter, int max_space, bool stop_on_stagnation) {
   const int64_t n = psi_size;
   const int keep = 4;
   double* V = dalloc<double>((size_t)max_space * n);
@@ -1006,9 +999,10 @@ double Engine::davidson(Sigma& sg, const double* diag, double tol, int max_iter,
   if (!(nrm > 0)) throw Error(-4, "two-site guess vector has zero norm");
   launch_scale(V, 1.0 / nrm, n, stream);
   stats.launches++;
-  sigma(sg, V, S);
+  op(V, S);
   dot_many(V, 1, S, hd.data());
   Hs[0] = hd[0];
+  std::vector<double> rhist;
   int k = 1;
   double theta = hd[0];
   std::vector<double> w(max_space), Z((size_t)max_space * max_space), hk((size_t)max_space * max_space);
@@ -1027,7 +1021,12 @@ double Engine::davidson(Sigma& sg, const double* diag, double tol, int max_iter,
     double rr;
     d2h(&rr, dots, 1);
     double rn = std::sqrt(std::max(rr, 0.0));
+    stats.last_residual = rn;
     if (rn < tol || it >= max_iter) break;
+    // reduced-precision operators have a residual floor near u ||H||: stop
+    // when six iterations have not reduced ||r|| by 30 %
+    rhist.push_back(rn);
+    if (stop_on_stagnation && rhist.size() > 6 && rn > 0.7 * rhist[rhist.size() - 7]) break;
     if (k == max_space) {
       int kk = std::min(keep, k);
       std::vector<double> cc((size_t)kk * k);
@@ -1059,7 +1058,7 @@ double Engine::davidson(Sigma& sg, const double* diag, double tol, int max_iter,
     launch_scale(t, 1.0 / tn, n, stream);
     stats.launches++;
     CK(cudaMemcpyAsync(V + (size_t)k * n, t, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-    sigma(sg, V + (size_t)k * n, S + (size_t)k * n);
+    op(V + (size_t)k * n, S + (size_t)k * n);
     dot_many(V, k + 1, S + (size_t)k * n, hd.data());
     for (int i = 0; i <= k; ++i) {
       Hs[(size_t)i * max_space + k] = hd[i];
@@ -1202,18 +1201,47 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
   finish_enl(sg.renl, ax);
   sync();
   stats.enl_ms += now_ms() - te;
-  plan_sigma(sg.lenl, sg.renl, sg);
   double* diag = dalloc<double>(psi_size);
   compute_diag(sg.lenl, sg.renl, diag);
   double td = now_ms();
-  double theta = davidson(sg, diag, tol, sched.max_iter, sched.max_space);
+  double theta = 0;
+  bool planned = false;
+  auto fp64op = [&](const double* x, double* y) {
+    if (!planned) {
+      plan_sigma(sg.lenl, sg.renl, sg);
+      planned = true;
+    }
+    sigma(sg, x, y);
+  };
+  if (sched.precision == 0) {
+    theta = davidson(fp64op, diag, tol, sched.max_iter, sched.max_space, false);
+  } else {
+    // tier 1: BF16 or TF32 single pass while the residual is large; tier 2:
+    // TF32x3 to its floor; then at most `refine` FP64 iterations
+    const int p1 = sched.precision == 2 ? kBF16 : kTF32;
+    const double floor1 = p1 == kBF16 ? 5e-2 : 1e-2;
+    TcPlan* P = tc_build(sg.lenl, sg.renl, p1);
+    theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, std::max(tol, floor1),
+                     sched.max_iter, sched.max_space, true);
+    tc_free(P);
+    if (stats.last_residual >= tol) {
+      P = tc_build(sg.lenl, sg.renl, kTF32x3);
+      theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, tol, sched.max_iter,
+                       sched.max_space, true);
+      tc_free(P);
+    }
+    if (sched.refine > 0 && stats.last_residual >= tol)
+      theta = davidson(fp64op, diag, tol, sched.refine, sched.max_space, false);
+  }
   stats.davidson_ms += now_ms() - td;
   dfree(diag);
-  release(sg.A);
-  release(sg.B);
-  dfree(sg.Y);
-  dfree(sg.in);
-  dfree(sg.out);
+  if (planned) {
+    release(sg.A);
+    release(sg.B);
+    dfree(sg.Y);
+    dfree(sg.in);
+    dfree(sg.out);
+  }
   double tt = now_ms();
   truncate(k, dir, M, tau, kept);
   stats.trunc_ms += now_ms() - tt;
@@ -1514,7 +1542,7 @@ int64_t Engine::two_site_size(int k) {
 
 // psi in the canonical two-site order: for q_l in bond k (sorted), s1, s2 with
 // q_r = q_l + s1 + s2 in bond k+2: a m_k(q_l) x m_{k+2}(q_r) block
-void Engine::apply_heff(int k, const double* in, double* out, double* diag_out) {
+void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, int prec) {
   setup_two_site(k);
   const Bond& bk = bonds[k];
   const Bond& bk2 = bonds[k + 2];
@@ -1543,9 +1571,15 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out) 
   finish_enl(sg.lenl, ax);
   build_renl(k + 1, Renv[k + 2], ER, sg.renl, ax);
   finish_enl(sg.renl, ax);
-  plan_sigma(sg.lenl, sg.renl, sg);
   double* y = dalloc<double>(psi_size);
-  sigma(sg, psi, y);
+  if (prec == 0) {
+    plan_sigma(sg.lenl, sg.renl, sg);
+    sigma(sg, psi, y);
+  } else {
+    TcPlan* P = tc_build(sg.lenl, sg.renl, prec == 1 ? kTF32 : prec == 2 ? kBF16 : kTF32x3);
+    tc_apply(P, psi, y);
+    tc_free(P);
+  }
   std::vector<double> hy(psi_size);
   CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
   sync();
@@ -1560,9 +1594,12 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out) 
       for (int a = 0; a < m.rows; ++a)
         for (int c = 0; c < m.cols; ++c) diag_out[m.src + (int64_t)a * m.cols + c] = hy[m.dst + (int64_t)a * m.ld + c];
   }
-  release(sg.A);
-  release(sg.B);
-  for (void* p : {(void*)sg.Y, (void*)sg.in, (void*)sg.out, (void*)y}) dfree(p);
+  if (prec == 0) {
+    release(sg.A);
+    release(sg.B);
+    for (void* p : {(void*)sg.Y, (void*)sg.in, (void*)sg.out}) dfree(p);
+  }
+  dfree(y);
   free_enl(sg.lenl);
   free_enl(sg.renl);
   sync();
@@ -1597,10 +1634,4 @@ void Engine::env_block(int side, int bond, int ch, int sec, std::vector<double>&
   sync();
 }
 
-}  // namespace gbd
-
-namespace gbd {
-template double* Engine::dalloc<double>(size_t);
-template int* Engine::dalloc<int>(size_t);
-template signed char* Engine::dalloc<signed char>(size_t);
 }  // namespace gbd

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <array>
+#include <functional>
 #include <map>
 #include <memory>
 #include <stdexcept>
@@ -77,6 +78,8 @@ std::vector<Bond> initial_bond_dims(int n, int Na, int Nb, int M);
 struct Stats {
   double sigma_flops = 0, sigma_ms = 0, env_flops = 0, env_ms = 0, enl_ms = 0, step_ms = 0;
   double trunc_ms = 0, davidson_ms = 0;
+  double sigma_flops_exec = 0, tc_ms = 0, tc_flops = 0, last_residual = 0;
+  int64_t n_sigma_tc = 0;
   int64_t n_sigma = 0, n_steps = 0, launches = 0, h2d = 0, d2h = 0;
   double max_discarded = 0;
 };
@@ -84,10 +87,12 @@ struct Stats {
 struct Schedule {
   std::vector<int> M;
   std::vector<double> tol;
-  int max_iter = 100, max_space = 24, precision = 0, precond = 0;
+  int max_iter = 100, max_space = 24, precision = 0, precond = 0, refine = 0;
   uint64_t seed = 1;
   double cutoff = 1e-12, tie = 1e-10;
 };
+
+struct TcPlan;
 
 class Engine {
  public:
@@ -102,7 +107,7 @@ class Engine {
   // debug / test hooks
   void set_mps(const int* nsec, const int* sectors, const double* data, int center);
   int64_t two_site_size(int k);
-  void apply_heff(int k, const double* in, double* out, double* diag_out);
+  void apply_heff(int k, const double* in, double* out, double* diag_out, int prec = 0);
   double run_step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept);
   void bond_sectors(int bond, std::vector<int>& out) const;
   int mpo_bond_dim(int bond) const { return (int)mpo.labels[bond].size(); }
@@ -135,7 +140,16 @@ class Engine {
   double* psi = nullptr;
 
   std::map<uintptr_t, size_t> allocs;   // live device allocations (base -> bytes)
-  template <class T> T* dalloc(size_t n);
+  int num_sms = 152;
+  template <class T>
+  T* dalloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMallocAsync(&p, n * sizeof(T), stream);
+    if (e != cudaSuccess) throw Error(-2, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    allocs[(uintptr_t)p] = n * sizeof(T);
+    return (T*)p;
+  }
   void check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, const char* what) const;
   void check(const GemmPlan& p) const;
   void check(const AxpyPlan& p) const;
@@ -167,7 +181,11 @@ class Engine {
   void plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg);
   void sigma(Sigma& sg, const double* x, double* y);
   void compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag);
-  double davidson(Sigma& sg, const double* diag, double tol, int max_iter, int max_space);
+  double davidson(const std::function<void(const double*, double*)>& op, const double* diag, double tol,
+                  int max_iter, int max_space, bool stop_on_stagnation);
+  TcPlan* tc_build(const EnlOp& lenl, const EnlOp& renl, int prec);
+  void tc_apply(TcPlan* p, const double* x, double* y);
+  void tc_free(TcPlan* p);
   void truncate(int k, int dir, int M, double* tau, std::vector<double>* kept);
   double step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept);
   void init_mps(uint64_t seed, int M);

@@ -33,7 +33,7 @@ class gbd_schedule(C.Structure):
     _fields_ = [("n_sweeps", C.c_int32), ("bond_dim", _ip), ("davidson_tol", _dp),
                 ("davidson_max_iter", C.c_int32), ("davidson_max_subspace", C.c_int32),
                 ("precision", C.c_int32), ("preconditioner", C.c_int32), ("seed", C.c_uint64),
-                ("svd_cutoff", C.c_double)]
+                ("svd_cutoff", C.c_double), ("fp64_refine", C.c_int32)]
 
 
 class gbd_result(C.Structure):
@@ -46,7 +46,9 @@ class gbd_stats(C.Structure):
                 ("env_ms", C.c_double), ("enlarge_ms", C.c_double), ("davidson_ms", C.c_double),
                 ("truncate_ms", C.c_double), ("step_ms", C.c_double), ("n_sigma", C.c_int64),
                 ("n_steps", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("max_discarded_weight", C.c_double)]
+                ("d2h_bytes", C.c_int64), ("max_discarded_weight", C.c_double),
+                ("sigma_flops_exec", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
+                ("n_sigma_tc", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -71,12 +73,14 @@ def lib():
         "gbd_solve": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), C.POINTER(gbd_result)]),
         "gbd_setup": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule)]),
         "gbd_init_state": (C.c_int, [vp]),
+        "gbd_set_precision": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "gbd_run_sweep": (C.c_int, [vp, C.c_int32, _dp]),
         "gbd_final_energy": (C.c_int, [vp, _dp]),
         "gbd_get_bond": (C.c_int, [vp, C.c_int32, _ip, C.c_int32, _ip]),
         "gbd_set_mps": (C.c_int, [vp, _ip, _ip, _dp, C.c_int32]),
         "gbd_two_site_size": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_int64)]),
         "gbd_apply_heff": (C.c_int, [vp, C.c_int32, _dp, _dp, _dp]),
+        "gbd_apply_heff_prec": (C.c_int, [vp, C.c_int32, C.c_int32, _dp, _dp]),
         "gbd_run_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp,
                                    C.c_int32, _ip]),
         "gbd_rdms": (C.c_int, [vp, _dp, _dp]),
@@ -146,7 +150,7 @@ class Context:
 
     def _structs(self, h, chol, n_elec, two_sz, bond_dims, tols, seed=1, precision=GBD_FP64,
                  preconditioner=GBD_PRECOND_DIAG, max_iter=100, max_subspace=24, svd_cutoff=1e-12,
-                 e_core=0.0):
+                 e_core=0.0, fp64_refine=2):
         h = np.ascontiguousarray(h, dtype=np.float64)
         chol = np.ascontiguousarray(chol, dtype=np.float64)
         bd = np.ascontiguousarray(bond_dims, dtype=np.int32)
@@ -154,7 +158,7 @@ class Context:
         self._keep = [h, chol, bd, tl]
         p = gbd_problem(h.shape[0], n_elec, two_sz, chol.shape[0], _d(h), _d(chol), e_core)
         s = gbd_schedule(len(bd), _i(bd), _d(tl), max_iter, max_subspace, precision, preconditioner,
-                         seed, svd_cutoff)
+                         seed, svd_cutoff, fp64_refine)
         return p, s
 
     def solve(self, h, chol, n_elec, two_sz, bond_dims, tols, rdms=False, **kw):
@@ -172,6 +176,9 @@ class Context:
     def setup(self, h, chol, n_elec, two_sz, bond_dims, tols, **kw):
         p, s = self._structs(h, chol, n_elec, two_sz, bond_dims, tols, **kw)
         self._check(self.L.gbd_setup(self.ptr, C.byref(p), C.byref(s)), "gbd_setup")
+
+    def set_precision(self, precision, fp64_refine=2):
+        self._check(self.L.gbd_set_precision(self.ptr, precision, fp64_refine), "gbd_set_precision")
 
     def init_state(self):
         self._check(self.L.gbd_init_state(self.ptr), "gbd_init_state")
@@ -210,6 +217,13 @@ class Context:
         d = np.zeros_like(x) if want_diag else None
         self._check(self.L.gbd_apply_heff(self.ptr, k, _d(x), _d(y), _d(d)), "gbd_apply_heff")
         return (y, d) if want_diag else y
+
+    def apply_heff_prec(self, k, x, prec):
+        """H_eff x through the tensor-core sigma (prec 1 TF32, 2 BF16, 3 TF32x3)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        self._check(self.L.gbd_apply_heff_prec(self.ptr, k, prec, _d(x), _d(y)), "gbd_apply_heff_prec")
+        return y
 
     def run_step(self, k, direction, M, tol):
         e, tau, nk = C.c_double(), C.c_double(), C.c_int32()

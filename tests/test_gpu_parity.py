@@ -145,7 +145,7 @@ def test_invalid_inputs_are_rejected(G):
     bad_h = h.copy()
     bad_h[0, 1] += 1e-6
     for kw, args in [({}, (bad_h, chol, 4, 0)), ({}, (h, chol, 9, 0)), ({}, (h, chol, 4, 1)),
-                     ({}, (h, chol, 3, 5)), ({"precision": 7}, (h, chol, 4, 0))]:
+                     ({}, (h, chol, 3, 5)), ({"precision": 7}, (h, chol, 4, 0)), ({"fp64_refine": -1}, (h, chol, 4, 0))]:
         with pytest.raises(G.GbdError, match="GBD_ERR_ARG"):
             ctx.solve(*args, [4], [1e-8], **kw)
     nan_h = h.copy()
