@@ -114,6 +114,26 @@ const char *gbd_last_error(const gbd_ctx *ctx);
 int gbd_solve(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule,
               gbd_result *result);
 
+/* Learned Davidson preconditioner (not in the paper, which names Jacobi,
+ * deflation-aware diagonal, Olsen and shift-and-invert members of a
+ * run-time-selectable family, Sec. "Computational details"; the reading used
+ * here): a pointwise two-layer MLP (8 features -> 128 ReLU -> 1, FP16
+ * weights, FP32 math) rescales the Jacobi step, t_i = -r_i/(d_i-theta)(1+g_i).
+ * With schedule.preconditioner = GBD_PRECOND_LEARNED a context uses the
+ * weights it holds; a Davidson solve falls back to the diagonal when ||r||
+ * stops dropping for three iterations or a correction is not finite, so the
+ * converged energy never depends on the network. */
+/* Solve each problem with the diagonal preconditioner while recording
+ * residual samples (2048 positions per Davidson iteration) and, once each
+ * step converges, the targets; then train the network on the device
+ * (full-batch Adam, `epochs` steps, learning rate lr).  final_loss may be
+ * NULL.  The context keeps the trained weights. */
+int gbd_train_precond(gbd_ctx *ctx, int32_t n_problems, const gbd_problem *problems,
+                      const gbd_schedule *schedules, int32_t epochs, double lr, double *final_loss);
+/* Store / load the network weights (file: "GBDMLP1\n", F, H, FP32 weights). */
+int gbd_save_precond(gbd_ctx *ctx, const char *path);
+int gbd_load_precond(gbd_ctx *ctx, const char *path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,18 @@ int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32
  * absolute error and the largest |reference| element. */
 int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t nterms, uint64_t seed,
                     double *max_err, double *max_ref);
+/* Preconditioner network pieces for gradient checks: install FP32 weights
+ * (kept FP16 on the device for inference); loss and gradient over n feature
+ * rows X [n*8] with targets y and weights w (FP32 device arithmetic, FP64
+ * reduction; params [1281] = W1 (128x8), b1, w2, b2); the fused
+ * preconditioner t = -r/(d-theta)(1+g) on host vectors (iteration counter
+ * `iter` enters the features). */
+int gbd_set_precond_weights(gbd_ctx *ctx, const float *params);
+int gbd_mlp_loss_grad(gbd_ctx *ctx, const float *X, const float *y, const float *w, int64_t n, const float *params,
+                      double *loss, double *grad);
+int gbd_mlp_precond(gbd_ctx *ctx, const double *r, const double *d, double theta, double iter, int64_t n, double *t);
+/* Davidson iteration count and learned-preconditioner fallbacks so far. */
+int gbd_davidson_counts(gbd_ctx *ctx, int64_t *iterations, int64_t *fallbacks, int64_t *samples);
 /* FP64 and FP32 CUDA-core FMA throughput of `device` (TFLOP/s), measured
  * with independent FMA chains on every SM; the peak of the FP64 path. */
 int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);

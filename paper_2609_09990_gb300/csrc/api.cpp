@@ -79,7 +79,6 @@ int validate(gbd_ctx* c, const gbd_problem* p, const gbd_schedule* s) {
   if (s->fp64_refine < 0) return fail(c, GBD_ERR_ARG, "fp64_refine < 0");
   if (s->preconditioner != GBD_PRECOND_DIAG && s->preconditioner != GBD_PRECOND_LEARNED)
     return fail(c, GBD_ERR_ARG, "unknown preconditioner");
-  if (s->preconditioner != GBD_PRECOND_DIAG) return fail(c, GBD_ERR_ARG, "learned preconditioner not loaded");
   if (s->svd_cutoff < 0 || !std::isfinite(s->svd_cutoff)) return fail(c, GBD_ERR_ARG, "svd_cutoff invalid");
   return GBD_OK;
 }
@@ -142,6 +141,8 @@ int gbd_solve(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, gbd_res
     int rc = setup(ctx, p, s);
     if (rc != GBD_OK) return rc;
     gbd::Engine& e = *ctx->eng;
+    if (s->preconditioner == GBD_PRECOND_LEARNED && !e.mlp_loaded)
+      return fail(ctx, GBD_ERR_STATE, "learned preconditioner requested but no weights are loaded");
     e.init_state();
     for (int i = 0; i < s->n_sweeps; ++i) {
       double en = e.sweep(i);
@@ -325,6 +326,83 @@ int gbd_multi_dot(gbd_ctx* ctx, const double* V, int64_t stride, int32_t k, cons
     if (k < 1 || k > 32 || n < 0 || stride < n) return fail(ctx, GBD_ERR_ARG, "bad k, n or stride");
     if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
     ctx->eng->multi_dot(V, stride, k, x, n, out);
+    return GBD_OK;
+  });
+}
+
+int gbd_train_precond(gbd_ctx* ctx, int32_t n_problems, const gbd_problem* problems, const gbd_schedule* schedules,
+                      int32_t epochs, double lr, double* final_loss) {
+  return guarded(ctx, [&]() {
+    if (n_problems < 1 || !problems || !schedules || epochs < 1 || !(lr > 0)) return fail(ctx, GBD_ERR_ARG, "bad training arguments");
+    for (int i = 0; i < n_problems; ++i) {
+      gbd_schedule s = schedules[i];
+      s.preconditioner = GBD_PRECOND_DIAG;
+      int rc = setup(ctx, &problems[i], &s);
+      if (rc != GBD_OK) return rc;
+      gbd::Engine& e = *ctx->eng;
+      e.init_state();
+      e.recording = true;
+      for (int k = 0; k < s.n_sweeps; ++k) e.sweep(k);
+      e.recording = false;
+    }
+    double loss = ctx->eng->train_precond(epochs, lr, 1);
+    if (final_loss) *final_loss = loss;
+    return GBD_OK;
+  });
+}
+
+int gbd_save_precond(gbd_ctx* ctx, const char* path) {
+  return guarded(ctx, [&]() {
+    if (!path) return fail(ctx, GBD_ERR_ARG, "NULL path");
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "no preconditioner weights");
+    ctx->eng->save_precond(path);
+    return GBD_OK;
+  });
+}
+
+int gbd_load_precond(gbd_ctx* ctx, const char* path) {
+  return guarded(ctx, [&]() {
+    if (!path) return fail(ctx, GBD_ERR_ARG, "NULL path");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->load_precond(path);
+    return GBD_OK;
+  });
+}
+
+int gbd_set_precond_weights(gbd_ctx* ctx, const float* params) {
+  return guarded(ctx, [&]() {
+    if (!params) return fail(ctx, GBD_ERR_ARG, "NULL params");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->set_precond_weights(params);
+    return GBD_OK;
+  });
+}
+
+int gbd_mlp_loss_grad(gbd_ctx* ctx, const float* X, const float* y, const float* w, int64_t n, const float* params,
+                      double* loss, double* grad) {
+  return guarded(ctx, [&]() {
+    if (!X || !y || !w || !params || !loss || !grad || n < 1) return fail(ctx, GBD_ERR_ARG, "bad arguments");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->mlp_loss_grad(X, y, w, n, params, loss, grad);
+    return GBD_OK;
+  });
+}
+
+int gbd_mlp_precond(gbd_ctx* ctx, const double* r, const double* d, double theta, double iter, int64_t n, double* t) {
+  return guarded(ctx, [&]() {
+    if (!r || !d || !t || n < 1) return fail(ctx, GBD_ERR_ARG, "bad arguments");
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "no preconditioner weights");
+    ctx->eng->mlp_apply(r, d, theta, iter, n, t);
+    return GBD_OK;
+  });
+}
+
+int gbd_davidson_counts(gbd_ctx* ctx, int64_t* iterations, int64_t* fallbacks, int64_t* samples) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "no engine");
+    if (iterations) *iterations = ctx->eng->stats.davidson_iters;
+    if (fallbacks) *fallbacks = ctx->eng->stats.precond_fallbacks;
+    if (samples) *samples = ctx->eng->n_samples();
     return GBD_OK;
   });
 }

@@ -207,6 +207,8 @@ Engine::Engine(int dev) : device(dev) {
   CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
+  CK(cudaMallocHost(&tc_err_host, sizeof(int)));
+  *tc_err_host = 0;
   cudaMemPool_t pool;
   CK(cudaDeviceGetDefaultMemPool(&pool, device));
   uint64_t thr = UINT64_MAX;
@@ -215,6 +217,7 @@ Engine::Engine(int dev) : device(dev) {
 
 Engine::~Engine() {
   cudaSetDevice(device);
+  if (tc_err_host) cudaFreeHost(tc_err_host);
   for (auto& e : Lenv) free_env(e);
   for (auto& e : Renv) free_env(e);
   for (auto& s : sites) free_site(s);
@@ -454,21 +457,31 @@ void Engine::make_env(int bond, Env& e) {
 
 // ------------------------------------------------------------------ enlarged operators
 namespace {
-struct TermKey {
-  int sec;
-  std::vector<std::pair<int, double>> t;
-  bool operator==(const TermKey& o) const { return sec == o.sec && t == o.t; }
-};
-struct TermKeyHash {
-  size_t operator()(const TermKey& k) const {
-    uint64_t h = 1469598103934665603ull ^ (uint64_t)k.sec;
-    for (auto& x : k.t) {
-      uint64_t v;
-      std::memcpy(&v, &x.second, 8);
-      h = (h ^ (uint64_t)x.first) * 1099511628211ull;
-      h = (h ^ v) * 1099511628211ull;
+// entries of one channel grouped into the 16 local matrix elements (so, si);
+// rep[p] / ratio[p]: bucket p equals ratio * bucket rep (same channels), so
+// its sub-blocks alias the combination formed for rep
+struct Buckets {
+  std::vector<std::pair<int, double>> lst[16];
+  int rep[16];
+  double ratio[16];
+  void classify() {
+    for (int p = 0; p < 16; ++p) {
+      rep[p] = p;
+      ratio[p] = 1.0;
+      if (lst[p].empty()) continue;
+      for (int q = 0; q < p; ++q) {
+        if (rep[q] != q || lst[q].size() != lst[p].size()) continue;
+        const double r = lst[p][0].second / lst[q][0].second;
+        bool same = true;
+        for (size_t i = 0; i < lst[p].size() && same; ++i)
+          same = lst[p][i].first == lst[q][i].first && lst[p][i].second == r * lst[q][i].second;
+        if (same) {
+          rep[p] = q;
+          ratio[p] = r;
+          break;
+        }
+      }
     }
-    return (size_t)h;
   }
 };
 }  // namespace
@@ -476,64 +489,61 @@ struct TermKeyHash {
 // Lenl[b] over E_L(Q) (Q in el), from L_k and W_k.  Sub-block (b, Qin, sin,
 // sout) maps rows (q_l, sin) of E_L(Qin) to rows (q_l', sout) of E_L(Qout):
 //   sum_a W_k[a,b](sout, sin) L_k[a](q_l' <- q_l).
-// A single +-1 term aliases the environment block; other combinations are
-// formed once (shared between sub-blocks with proportional term lists).
+// All channels a of one (b, sout, sin) bucket share delta_a, so a sector has
+// either every block or none.  A single +-1 term aliases the environment
+// block; other combinations are formed once and shared by proportional
+// buckets (identity-like local operators give four of them).
 void Engine::build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPlan& ax) {
   const Bond& bk = bonds[k];
   const auto& W = mpo.W[k];
   op.subs.clear();
   op.own_size = 0;
-  std::unordered_map<TermKey, std::pair<int64_t, double>, TermKeyHash> combos;
+  const int ns = bk.nsec();
+  std::vector<int64_t> combo(16 * (size_t)ns);
   size_t e0 = 0;
   while (e0 < W.size()) {
-    int b = W[e0].b;
+    const int b = W[e0].b;
     size_t e1 = e0;
-    while (e1 < W.size() && W[e1].b == b) ++e1;
-    // group by (sout, sin)
-    for (int so = 0; so < 4; ++so)
-      for (int si = 0; si < 4; ++si) {
-        std::vector<std::pair<int, double>> lst;
-        for (size_t e = e0; e < e1; ++e)
-          if (W[e].sout == so && W[e].sin == si) lst.push_back({W[e].a, W[e].v});
-        if (lst.empty()) continue;
-        int da = mpo.dA[k + 1][b] - (QA[so] - QA[si]);
-        int db = mpo.dB[k + 1][b] - (QB[so] - QB[si]);
-        for (int il = 0; il < bk.nsec(); ++il) {
-          int qin = el.find(bk.na[il] + QA[si], bk.nb[il] + QB[si]);
-          if (qin < 0) continue;
-          int ilp = bk.find(bk.na[il] + da, bk.nb[il] + db);
-          if (ilp < 0) continue;
-          int qout = el.find(bk.na[ilp] + QA[so], bk.nb[ilp] + QB[so]);
-          if (qout < 0) continue;
-          TermKey key;
-          key.sec = il;
-          for (auto& t : lst)
-            if (Lk.at(t.first, il) >= 0) key.t.push_back(t);
-          if (key.t.empty()) continue;
-          EnlSub sub{b, qin, si, qout, so, bk.dim[ilp], bk.dim[il], nullptr, -1, 1.0};
-          if (key.t.size() == 1 && std::fabs(key.t[0].second) == 1.0) {
-            sub.ptr = Lk.d + Lk.at(key.t[0].first, il);
-            sub.sign = key.t[0].second;
-          } else {
-            double sg = key.t[0].second < 0 ? -1.0 : 1.0;
-            for (auto& t : key.t) t.second *= sg;
-            auto it = combos.find(key);
-            if (it == combos.end()) {
-              int64_t len = (int64_t)sub.rows * sub.cols;
-              it = combos.emplace(key, std::make_pair(op.own_size, 1.0)).first;
-              AxpyOut o{nullptr, len, (int)ax.terms.size(), 0};
-              for (auto& t : key.t) ax.terms.push_back({Lk.d + Lk.at(t.first, il), t.second});
-              o.t1 = (int)ax.terms.size();
-              o.dst = (double*)(intptr_t)(op.own_size);   // resolved in finish_enl
-              ax.outs.push_back(o);
-              op.own_size += len;
-            }
-            sub.own_off = it->second.first;
-            sub.sign = sg;
+    Buckets B;
+    for (; e1 < W.size() && W[e1].b == b; ++e1) B.lst[W[e1].sout * 4 + W[e1].sin].push_back({W[e1].a, W[e1].v});
+    B.classify();
+    std::fill(combo.begin(), combo.end(), -1);
+    for (int p = 0; p < 16; ++p) {
+      const auto& lst = B.lst[p];
+      if (lst.empty()) continue;
+      const int so = p / 4, si = p % 4;
+      const int da = mpo.dA[k + 1][b] - (QA[so] - QA[si]);
+      const int db = mpo.dB[k + 1][b] - (QB[so] - QB[si]);
+      for (int il = 0; il < ns; ++il) {
+        const int qin = el.find(bk.na[il] + QA[si], bk.nb[il] + QB[si]);
+        if (qin < 0) continue;
+        const int ilp = bk.find(bk.na[il] + da, bk.nb[il] + db);
+        if (ilp < 0) continue;
+        const int qout = el.find(bk.na[ilp] + QA[so], bk.nb[ilp] + QB[so]);
+        if (qout < 0) continue;
+        if (Lk.at(lst[0].first, il) < 0) continue;
+        EnlSub sub{b, qin, si, qout, so, bk.dim[ilp], bk.dim[il], nullptr, -1, 1.0};
+        if (lst.size() == 1) {
+          sub.ptr = Lk.d + Lk.at(lst[0].first, il);
+          sub.sign = lst[0].second;
+        } else {
+          const int r = B.rep[p];
+          int64_t& off = combo[(size_t)r * ns + il];
+          if (off < 0) {
+            const int64_t len = (int64_t)sub.rows * sub.cols;
+            off = op.own_size;
+            AxpyOut o{(double*)(intptr_t)off, len, (int)ax.terms.size(), 0};
+            for (auto& t : B.lst[r]) ax.terms.push_back({Lk.d + Lk.at(t.first, il), t.second});
+            o.t1 = (int)ax.terms.size();
+            ax.outs.push_back(o);
+            op.own_size += len;
           }
-          op.subs.push_back(sub);
+          sub.own_off = off;
+          sub.sign = B.ratio[p];
         }
+        op.subs.push_back(sub);
       }
+    }
     e0 = e1;
   }
 }
@@ -546,57 +556,53 @@ void Engine::build_renl(int i, const Env& R, const Space& er, EnlOp& op, AxpyPla
   const auto& W = mpo.W[i];
   op.subs.clear();
   op.own_size = 0;
-  // entries sorted by b; regroup per b
-  std::unordered_map<TermKey, std::pair<int64_t, double>, TermKeyHash> combos;
-  // group the entries of W_i by their left channel (called b here)
-  std::map<int, std::vector<const MpoEntry*>> bya;
+  const int ns = br.nsec();
+  // entries of W_i grouped by their left channel (called b here)
+  std::vector<std::vector<const MpoEntry*>> bya(mpo.labels[i].size());
   for (const auto& e : W) bya[e.a].push_back(&e);
-  for (auto& kv : bya) {
-    int b = kv.first;   // channel at bond i (left of site i)
-    for (int so = 0; so < 4; ++so)
-      for (int si = 0; si < 4; ++si) {
-        std::vector<std::pair<int, double>> lst;
-        for (const MpoEntry* e : kv.second)
-          if (e->sout == so && e->sin == si) lst.push_back({e->b, e->v});
-        if (lst.empty()) continue;
-        int dca = mpo.dA[i][b] + (QA[so] - QA[si]);
-        int dcb = mpo.dB[i][b] + (QB[so] - QB[si]);
-        for (int ir = 0; ir < br.nsec(); ++ir) {
-          int qin = er.find(br.na[ir] - QA[si], br.nb[ir] - QB[si]);
-          if (qin < 0) continue;
-          int irp = br.find(br.na[ir] + dca, br.nb[ir] + dcb);
-          if (irp < 0) continue;
-          int qout = er.find(br.na[irp] - QA[so], br.nb[irp] - QB[so]);
-          if (qout < 0) continue;
-          TermKey key;
-          key.sec = ir;
-          for (auto& t : lst)
-            if (R.at(t.first, ir) >= 0) key.t.push_back(t);
-          if (key.t.empty()) continue;
-          EnlSub sub{b, qin, si, qout, so, br.dim[irp], br.dim[ir], nullptr, -1, 1.0};
-          if (key.t.size() == 1 && std::fabs(key.t[0].second) == 1.0) {
-            sub.ptr = R.d + R.at(key.t[0].first, ir);
-            sub.sign = key.t[0].second;
-          } else {
-            double sg = key.t[0].second < 0 ? -1.0 : 1.0;
-            for (auto& t : key.t) t.second *= sg;
-            auto it = combos.find(key);
-            if (it == combos.end()) {
-              int64_t len = (int64_t)sub.rows * sub.cols;
-              it = combos.emplace(key, std::make_pair(op.own_size, 1.0)).first;
-              AxpyOut o{nullptr, len, (int)ax.terms.size(), 0};
-              for (auto& t : key.t) ax.terms.push_back({R.d + R.at(t.first, ir), t.second});
-              o.t1 = (int)ax.terms.size();
-              o.dst = (double*)(intptr_t)(op.own_size);
-              ax.outs.push_back(o);
-              op.own_size += len;
-            }
-            sub.own_off = it->second.first;
-            sub.sign = sg;
+  std::vector<int64_t> combo(16 * (size_t)ns);
+  for (int b = 0; b < (int)bya.size(); ++b) {
+    if (bya[b].empty()) continue;
+    Buckets B;
+    for (const MpoEntry* e : bya[b]) B.lst[e->sout * 4 + e->sin].push_back({e->b, e->v});
+    B.classify();
+    std::fill(combo.begin(), combo.end(), -1);
+    for (int p = 0; p < 16; ++p) {
+      const auto& lst = B.lst[p];
+      if (lst.empty()) continue;
+      const int so = p / 4, si = p % 4;
+      const int dca = mpo.dA[i][b] + (QA[so] - QA[si]);
+      const int dcb = mpo.dB[i][b] + (QB[so] - QB[si]);
+      for (int ir = 0; ir < ns; ++ir) {
+        const int qin = er.find(br.na[ir] - QA[si], br.nb[ir] - QB[si]);
+        if (qin < 0) continue;
+        const int irp = br.find(br.na[ir] + dca, br.nb[ir] + dcb);
+        if (irp < 0) continue;
+        const int qout = er.find(br.na[irp] - QA[so], br.nb[irp] - QB[so]);
+        if (qout < 0) continue;
+        if (R.at(lst[0].first, ir) < 0) continue;
+        EnlSub sub{b, qin, si, qout, so, br.dim[irp], br.dim[ir], nullptr, -1, 1.0};
+        if (lst.size() == 1) {
+          sub.ptr = R.d + R.at(lst[0].first, ir);
+          sub.sign = lst[0].second;
+        } else {
+          const int r = B.rep[p];
+          int64_t& off = combo[(size_t)r * ns + ir];
+          if (off < 0) {
+            const int64_t len = (int64_t)sub.rows * sub.cols;
+            off = op.own_size;
+            AxpyOut o{(double*)(intptr_t)off, len, (int)ax.terms.size(), 0};
+            for (auto& t : B.lst[r]) ax.terms.push_back({R.d + R.at(t.first, ir), t.second});
+            o.t1 = (int)ax.terms.size();
+            ax.outs.push_back(o);
+            op.own_size += len;
           }
-          op.subs.push_back(sub);
+          sub.own_off = off;
+          sub.sign = B.ratio[p];
         }
+        op.subs.push_back(sub);
       }
+    }
   }
 }
 
@@ -885,16 +891,14 @@ void Engine::plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg) {
 }
 
 void Engine::sigma(Sigma& sg, const double* x, double* y) {
+  settle();
   CK(cudaMemcpyAsync(sg.in, x, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   CK(cudaEventRecord(ev0, stream));
   run(sg.A);
   run(sg.B);
   CK(cudaEventRecord(ev1, stream));
   CK(cudaMemcpyAsync(y, sg.out, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  CK(cudaEventSynchronize(ev1));
-  float ms = 0;
-  CK(cudaEventElapsedTime(&ms, ev0, ev1));
-  stats.sigma_ms += ms;
+  sigma_pending = 1;
   stats.sigma_flops += sg.A.flops + sg.B.flops;
   stats.n_sigma++;
 }
@@ -963,6 +967,9 @@ void Engine::compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag) {
 // restart from the 4 lowest Ritz vectors when the space is full.
 double Engine::davidson(const std::function<void(const double*, double*)>& op, const double* diag, double tol,
                         int max_iter, int max_space, bool stop_on_stagnation) {
+  // Two host synchronisations per iteration: the residual norm (convergence
+  // test) and the new row of the projected matrix.  Gram-Schmidt
+  // coefficients and the normalisation never leave the device.
   const int64_t n = psi_size;
   const int keep = 4;
   double* V = dalloc<double>((size_t)max_space * n);
@@ -974,37 +981,60 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
   double* r = dalloc<double>(n);
   double* t = dalloc<double>(n);
   int nblk = reduction_blocks(n);
-  double* partial = dalloc<double>((size_t)nblk * (max_space + 1));
-  double* dots = dalloc<double>(max_space + 1);
+  double* partial = dalloc<double>((size_t)nblk * (max_space + 2));
+  double* dres = dalloc<double>(1);                 // ||r||^2
+  double* dorth = dalloc<double>(max_space);        // Gram-Schmidt overlaps
+  double* drow = dalloc<double>(max_space + 2);     // [V^T s_k, |t|^2]
   double* coef = dalloc<double>((size_t)max_space * keep + max_space);
-  std::vector<double> Hs((size_t)max_space * max_space, 0.0), hd(max_space + 1);
+  std::vector<double> Hs((size_t)max_space * max_space, 0.0), hd(max_space + 2);
   auto d2h = [&](double* host, const double* dev, int cnt) {
     CK(cudaMemcpyAsync(host, dev, cnt * sizeof(double), cudaMemcpyDeviceToHost, stream));
     sync();
+    settle();
     stats.d2h += cnt * sizeof(double);
   };
   auto h2d = [&](double* dev, const double* host, int cnt) {
     CK(cudaMemcpyAsync(dev, host, cnt * sizeof(double), cudaMemcpyHostToDevice, stream));
     stats.h2d += cnt * sizeof(double);
   };
-  auto dot_many = [&](const double* base, int k, const double* vec, double* host) {
-    launch_multi_dot(base, n, k, vec, n, dots, partial, nblk, stream);
+  auto dots = [&](const double* base, int k, const double* vec, double* out_dev) {
+    launch_multi_dot(base, n, k, vec, n, out_dev, partial, nblk, stream);
     stats.launches += 2;
-    d2h(host, dots, k);
   };
-  // v0 = psi / |psi|
-  CK(cudaMemcpyAsync(V, psi, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  dot_many(V, 1, V, hd.data());
-  double nrm = std::sqrt(hd[0]);
-  if (!(nrm > 0)) throw Error(-4, "two-site guess vector has zero norm");
-  launch_scale(V, 1.0 / nrm, n, stream);
+  // v0 = psi / |psi|, s0 = H v0
+  dots(psi, 1, psi, drow + max_space + 1);
+  launch_normalize(psi, drow + max_space + 1, n, V, stream);
   stats.launches++;
   op(V, S);
-  dot_many(V, 1, S, hd.data());
+  dots(V, 1, S, drow);
+  CK(cudaMemcpyAsync(hd.data(), drow, (max_space + 2) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  settle();
+  if (!(hd[max_space + 1] > 0)) throw Error(-4, "two-site guess vector has zero norm");
   Hs[0] = hd[0];
   std::vector<double> rhist;
   int k = 1;
   double theta = hd[0];
+  // learned preconditioner: RMS of (d - theta) from sums of d and d^2
+  const bool learned = sched.precond == 1 && mlp_loaded;
+  bool fallback = false;
+  double sum_d = 0, sum_dd = 0;
+  int* dbad = nullptr;
+  if (learned || recording) {
+    std::vector<double> hdiag(n);
+    CK(cudaMemcpyAsync(hdiag.data(), diag, n * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    sync();
+    for (double v : hdiag) {
+      sum_d += v;
+      sum_dd += v * v;
+    }
+    dbad = dalloc<int>(1);
+    CK(cudaMemsetAsync(dbad, 0, sizeof(int), stream));
+  }
+  auto scalars = [&](double th, double rn, int it) {
+    double var = (sum_dd - 2.0 * th * sum_d) / (double)n + th * th;
+    return MlpScalars{th, rn + 1e-300, std::sqrt(std::max(var, 0.0)) + 1e-300, (double)it};
+  };
   std::vector<double> w(max_space), Z((size_t)max_space * max_space), hk((size_t)max_space * max_space);
   for (int it = 0;; ++it) {
     for (int i = 0; i < k; ++i)
@@ -1016,10 +1046,10 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     h2d(coef, c.data(), k);
     launch_lincomb(x, V, n, coef, k, n, 0, stream);
     launch_lincomb(sx, S, n, coef, k, n, 0, stream);
-    launch_residual_precond(x, sx, diag, theta, n, r, t, partial, nblk, dots, stream);
+    launch_residual_precond(x, sx, diag, theta, n, r, t, partial, nblk, dres, stream);
     stats.launches += 4;
     double rr;
-    d2h(&rr, dots, 1);
+    d2h(&rr, dres, 1);
     double rn = std::sqrt(std::max(rr, 0.0));
     stats.last_residual = rn;
     if (rn < tol || it >= max_iter) break;
@@ -1027,6 +1057,19 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     // when six iterations have not reduced ||r|| by 30 %
     rhist.push_back(rn);
     if (stop_on_stagnation && rhist.size() > 6 && rn > 0.7 * rhist[rhist.size() - 7]) break;
+    stats.davidson_iters++;
+    if (recording) record_iteration(r, diag, x, scalars(theta, rn, it));
+    if (learned && !fallback) {
+      // back to the diagonal preconditioner when ||r|| has not dropped over
+      // three iterations
+      if (rhist.size() > 3 && rn >= rhist[rhist.size() - 4]) {
+        fallback = true;
+        stats.precond_fallbacks++;
+      } else {
+        launch_mlp_precond(r, diag, scalars(theta, rn, it), n, mlp_w16, t, dbad, stream);
+        stats.launches++;
+      }
+    }
     if (k == max_space) {
       int kk = std::min(keep, k);
       std::vector<double> cc((size_t)kk * k);
@@ -1044,22 +1087,30 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
       for (int j = 0; j < kk; ++j) Hs[(size_t)j * max_space + j] = w[j];
       k = kk;
     }
-    // orthogonalise t against V (two passes) and normalise
+    // t <- t - V (V^T t), twice; v_k = t / |t|; s_k = H v_k
     for (int pass = 0; pass < 2; ++pass) {
-      dot_many(V, k, t, hd.data());
-      for (int i = 0; i < k; ++i) hd[i] = -hd[i];
-      h2d(coef, hd.data(), k);
-      launch_lincomb(t, V, n, coef, k, n, 1, stream);
+      dots(V, k, t, dorth);
+      launch_lincomb(t, V, n, dorth, k, n, 1, stream, -1.0);
       stats.launches++;
     }
-    dot_many(t, 1, t, hd.data());
-    double tn = std::sqrt(std::max(hd[0], 0.0));
-    if (tn < 1e-14) break;
-    launch_scale(t, 1.0 / tn, n, stream);
+    dots(t, 1, t, drow + max_space + 1);
+    launch_normalize(t, drow + max_space + 1, n, V + (size_t)k * n, stream);
     stats.launches++;
-    CK(cudaMemcpyAsync(V + (size_t)k * n, t, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
     op(V + (size_t)k * n, S + (size_t)k * n);
-    dot_many(V, k + 1, S + (size_t)k * n, hd.data());
+    dots(V, k + 1, S + (size_t)k * n, drow);
+    CK(cudaMemcpyAsync(hd.data(), drow, (max_space + 2) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    int hbad = 0;
+    if (dbad) CK(cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    sync();
+    settle();
+    stats.d2h += (max_space + 2) * sizeof(double);
+    if (hbad) {   // non-finite learned correction: drop it, use the diagonal from now on
+      fallback = true;
+      stats.precond_fallbacks++;
+      CK(cudaMemsetAsync(dbad, 0, sizeof(int), stream));
+      continue;
+    }
+    if (!(hd[max_space + 1] > 1e-28)) break;   // breakdown: t had no new direction
     for (int i = 0; i <= k; ++i) {
       Hs[(size_t)i * max_space + k] = hd[i];
       Hs[(size_t)k * max_space + i] = hd[i];
@@ -1067,14 +1118,31 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     ++k;
   }
   // psi <- normalised Ritz vector
-  dot_many(x, 1, x, hd.data());
-  CK(cudaMemcpyAsync(psi, x, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  launch_scale(psi, 1.0 / std::sqrt(hd[0]), n, stream);
+  dots(x, 1, x, drow + max_space + 1);
+  launch_normalize(x, drow + max_space + 1, n, psi, stream);
   stats.launches++;
+  sync();
+  if (recording) record_converged(psi);
+  if (dbad) dfree(dbad);
   for (void* p : {(void*)V, (void*)S, (void*)Vt, (void*)St, (void*)x, (void*)sx, (void*)r, (void*)t, (void*)partial,
-                  (void*)dots, (void*)coef})
+                  (void*)dres, (void*)dorth, (void*)drow, (void*)coef})
     dfree(p);
   return theta;
+}
+
+// account the sigma build recorded by the last sigma()/tc_apply() once the
+// stream has passed it
+void Engine::settle() {
+  if (!sigma_pending) return;
+  CK(cudaEventSynchronize(ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  stats.sigma_ms += ms;
+  if (sigma_pending == 2) {
+    stats.tc_ms += ms;
+    if (*tc_err_host) throw Error(-5, "tensor-core sigma: a bounded device wait ran out");
+  }
+  sigma_pending = 0;
 }
 
 // ------------------------------------------------------------------ decimation

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "gbd_internal.h"
+#include "mlp.h"
 
 namespace gbd {
 
@@ -81,6 +82,7 @@ struct Stats {
   double sigma_flops_exec = 0, tc_ms = 0, tc_flops = 0, last_residual = 0;
   int64_t n_sigma_tc = 0;
   int64_t n_sigma = 0, n_steps = 0, launches = 0, h2d = 0, d2h = 0;
+  int64_t davidson_iters = 0, precond_fallbacks = 0;
   double max_discarded = 0;
 };
 
@@ -114,6 +116,20 @@ class Engine {
   std::vector<uint64_t> mpo_labels(int bond) const;
   void env_block(int side, int bond, int channel, int sector, std::vector<double>& out, int& rows, int& cols);
   void multi_dot(const double* V, int64_t stride, int k, const double* x, int64_t n, double* out_host);
+
+  // learned preconditioner
+  void record_iteration(const double* r_dev, const double* diag_dev, const double* x_dev, const MlpScalars& s);
+  void record_converged(const double* x_dev);
+  double train_precond(int epochs, double lr, uint64_t seed);
+  void set_precond_weights(const float* params);
+  void mlp_loss_grad(const float* X, const float* y, const float* w, int64_t n, const float* params, double* loss,
+                     double* grad);
+  void mlp_apply(const double* r, const double* d, double theta, double iter, int64_t n, double* t);
+  void save_precond(const char* path) const;
+  void load_precond(const char* path);
+  bool recording = false;
+  bool mlp_loaded = false;
+  int64_t n_samples() const { return (int64_t)data_y.size(); }
 
   Stats stats;
   std::vector<double> sweep_E;
@@ -161,6 +177,9 @@ class Engine {
   void run(GemmPlan& p);
   void run(AxpyPlan& p);
   void sync();
+  void settle();
+  int sigma_pending = 0;          // 1: FP64 sigma, 2: tensor-core sigma awaiting accounting
+  int* tc_err_host = nullptr;     // pinned copy of the tensor-core error flag
 
   void free_env(Env& e);
   void make_env(int bond, Env& e);
@@ -191,8 +210,15 @@ class Engine {
   void init_mps(uint64_t seed, int M);
   void build_right_envs(int from_k);
   void build_left_envs(int to_k);
-  std::vector<int> last_pattern;
-  int psi_pattern(int k, int dir);
+  struct Rec {
+    MlpScalars s;
+    std::vector<double> r, d, x;
+  };
+  std::vector<Rec> rec_iters;
+  std::vector<int64_t> rec_idx;
+  int64_t rec_n = 0;
+  std::vector<float> data_X, data_y, data_w, mlp_f32;
+  uint16_t* mlp_w16 = nullptr;
 };
 
 }  // namespace gbd

@@ -145,12 +145,21 @@ __global__ void finish_sums(const double* partial, int nblk, int k, double* out)
 }
 
 __global__ void lincomb_kernel(double* out, const double* __restrict__ V, int64_t stride,
-                               const double* __restrict__ coef, int k, int64_t n, int accumulate) {
+                               const double* __restrict__ coef, int k, int64_t n, int accumulate, double cs) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = accumulate ? out[i] : 0.0;
-    for (int j = 0; j < k; ++j) s = fma(coef[j], V[(int64_t)j * stride + i], s);
+    for (int j = 0; j < k; ++j) s = fma(cs * coef[j], V[(int64_t)j * stride + i], s);
     out[i] = s;
   }
+}
+
+// out = t / sqrt(nrm2[0]) (zero vector when the norm has vanished)
+__global__ void normalize_kernel(const double* __restrict__ t, const double* __restrict__ nrm2, int64_t n,
+                                 double* __restrict__ out) {
+  const double q = nrm2[0];
+  const double s = q > 1e-28 ? 1.0 / sqrt(q) : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = t[i] * s;
 }
 
 // r = sx - theta x ; t = -r / clamp(diag - theta) ; partial sums of r^2
@@ -216,8 +225,12 @@ void launch_multi_dot(const double* V, int64_t stride, int k, const double* x, i
 }
 
 void launch_lincomb(double* out, const double* V, int64_t stride, const double* coef_dev, int k, int64_t n,
-                    int accumulate, cudaStream_t s) {
-  lincomb_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, V, stride, coef_dev, k, n, accumulate);
+                    int accumulate, cudaStream_t s, double coef_scale) {
+  lincomb_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, V, stride, coef_dev, k, n, accumulate, coef_scale);
+}
+
+void launch_normalize(const double* t, const double* nrm2_dev, int64_t n, double* out, cudaStream_t s) {
+  normalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(t, nrm2_dev, n, out);
 }
 
 void launch_residual_precond(const double* x, const double* sx, const double* diag, double theta, int64_t n,

@@ -311,7 +311,7 @@ __global__ void tc_convert_kernel(const TcConv* __restrict__ tasks, int ntasks, 
     const int64_t n = (int64_t)c.rows * c.cols;
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       const int r = (int)(e / c.cols), col = (int)(e % c.cols);
-      store_conv(c.src[(int64_t)r * c.ld_src + col], prec, hi, lo, (int64_t)(c.r0 + r) * pitch + c.c0 + col);
+      store_conv(c.scale * c.src[(int64_t)r * c.ld_src + col], prec, hi, lo, (int64_t)(c.r0 + r) * pitch + c.c0 + col);
     }
   }
 }

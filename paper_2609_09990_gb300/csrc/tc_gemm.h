@@ -72,6 +72,7 @@ void launch_tc_gemm(const TcMaps& maps, const TcLaunch& L, int num_sms, cudaStre
 // written at panel row r0, column c0 (pitch); lo != nullptr for TF32x3
 struct TcConv {
   const double* src;
+  double scale;          // multiplies every element (the sub-block's coefficient)
   int32_t rows, cols, ld_src;
   int32_t r0, c0;
 };

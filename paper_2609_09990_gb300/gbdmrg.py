@@ -95,6 +95,15 @@ def lib():
         "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
         "gbd_multi_dot_noalloc": (C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                             C.c_void_p, C.c_void_p]),
+        "gbd_train_precond": (C.c_int, [vp, C.c_int32, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), C.c_int32,
+                                        C.c_double, _dp]),
+        "gbd_save_precond": (C.c_int, [vp, C.c_char_p]),
+        "gbd_load_precond": (C.c_int, [vp, C.c_char_p]),
+        "gbd_set_precond_weights": (C.c_int, [vp, C.POINTER(C.c_float)]),
+        "gbd_mlp_loss_grad": (C.c_int, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                        C.c_int64, C.POINTER(C.c_float), _dp, _dp]),
+        "gbd_mlp_precond": (C.c_int, [vp, _dp, _dp, C.c_double, C.c_double, C.c_int64, _dp]),
+        "gbd_davidson_counts": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
         "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
                                       _dp]),
@@ -260,6 +269,55 @@ class Context:
         out = np.zeros(k)
         self._check(self.L.gbd_multi_dot(self.ptr, V_ptr, stride, k, x_ptr, n, _d(out)), "gbd_multi_dot")
         return out
+
+    def train_precond(self, problems, epochs=400, lr=3e-3):
+        """problems: list of (h, chol, n_elec, two_sz, bond_dims, tols, kwargs)."""
+        ps = (gbd_problem * len(problems))()
+        ss = (gbd_schedule * len(problems))()
+        keep = []
+        for i, (h, chol, ne, sz, bd, tl, kw) in enumerate(problems):
+            p, s = self._structs(h, chol, ne, sz, bd, tl, **kw)
+            keep.append(self._keep)
+            ps[i] = p
+            ss[i] = s
+        loss = C.c_double()
+        self._check(self.L.gbd_train_precond(self.ptr, len(problems), ps, ss, epochs, lr, C.byref(loss)),
+                    "gbd_train_precond")
+        return loss.value
+
+    def save_precond(self, path):
+        self._check(self.L.gbd_save_precond(self.ptr, path.encode()), "gbd_save_precond")
+
+    def load_precond(self, path):
+        self._check(self.L.gbd_load_precond(self.ptr, path.encode()), "gbd_load_precond")
+
+    def set_precond_weights(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.L.gbd_set_precond_weights(self.ptr, p.ctypes.data_as(C.POINTER(C.c_float))),
+                    "gbd_set_precond_weights")
+
+    def mlp_loss_grad(self, X, y, w, params):
+        fp = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+        X, y, w, params = fp(X), fp(y), fp(w), fp(params)
+        loss = C.c_double()
+        grad = np.zeros(params.size)
+        f = C.POINTER(C.c_float)
+        self._check(self.L.gbd_mlp_loss_grad(self.ptr, X.ctypes.data_as(f), y.ctypes.data_as(f), w.ctypes.data_as(f),
+                                             len(y), params.ctypes.data_as(f), C.byref(loss), _d(grad)),
+                    "gbd_mlp_loss_grad")
+        return loss.value, grad
+
+    def mlp_precond(self, r, d, theta, it):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        t = np.zeros_like(r)
+        self._check(self.L.gbd_mlp_precond(self.ptr, _d(r), _d(d), theta, it, len(r), _d(t)), "gbd_mlp_precond")
+        return t
+
+    def davidson_counts(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.L.gbd_davidson_counts(self.ptr, C.byref(a), C.byref(b), C.byref(c)), "gbd_davidson_counts")
+        return a.value, b.value, c.value
 
     def stats(self):
         s = gbd_stats()

@@ -1,0 +1,94 @@
+"""Learned Davidson preconditioner: device gradients and inference against
+the FP64 CPU reference (oracle/mlp.py), training on solver residuals, and the
+converged energy unchanged with respect to the diagonal preconditioner."""
+import os
+
+import numpy as np
+import pytest
+
+from gbd_synth import make_integrals
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2609_09990_gb300 import build, gbdmrg
+    build.build()
+    return gbdmrg
+
+
+def rand_params(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, scale, (mlp.H, mlp.F))
+    b1 = rng.normal(0, 0.1, mlp.H)
+    w2 = rng.normal(0, 0.1, mlp.H)
+    return np.concatenate([W1.ravel(), b1, w2, [0.05]])
+
+
+def test_gradients_match_cpu_reference(G):
+    rng = np.random.default_rng(7)
+    n = 5000
+    r = rng.normal(size=n)
+    d = rng.normal(size=n) * 2
+    X = mlp.features(r, d, -0.3, 4).astype(np.float32)
+    y = (rng.normal(size=n) * 0.3).astype(np.float32)
+    w = rng.uniform(0.1, 1.0, n).astype(np.float32)
+    p = rand_params(3).astype(np.float32)
+    ctx = G.Context(0)
+    loss, grad = ctx.mlp_loss_grad(X, y, w, p)
+    net = mlp.MLP.from_params(p.astype(np.float64))
+    L, g = net.loss_and_grad(X.astype(np.float64), y.astype(np.float64), w.astype(np.float64))
+    assert abs(loss - L) <= 1e-5 * abs(L)
+    assert np.abs(grad - g).max() <= 1e-5 * np.abs(g).max()
+    ctx.close()
+
+
+def test_fused_inference_matches_cpu_reference(G):
+    rng = np.random.default_rng(8)
+    n = 20000
+    r = rng.normal(size=n) * 1e-3
+    d = rng.normal(size=n) * 3 - 10
+    p = rand_params(4)
+    p16 = p.astype(np.float16).astype(np.float64)      # the device keeps FP16 weights
+    ctx = G.Context(0)
+    ctx.set_precond_weights(p.astype(np.float32))
+    t = ctx.mlp_precond(r, d, -10.5, 3.0)
+    ref = mlp.precondition(r, d, -10.5, 3.0, mlp.MLP.from_params(p16))
+    assert np.abs(t - ref).max() <= 1e-5 * np.abs(ref).max()
+    ctx.close()
+
+
+def test_training_keeps_the_converged_energy(G, tmp_path):
+    h, chol = make_integrals(6, 18, 1)
+    ctx = G.Context(0)
+    loss = ctx.train_precond([(h, chol, 6, 0, [64, 64], [1e-9, 1e-9], {"seed": 1})], epochs=300, lr=3e-3)
+    assert np.isfinite(loss)
+    _, _, ns = ctx.davidson_counts()
+    assert ns > 1000
+    path = str(tmp_path / "precond.bin")
+    ctx.save_precond(path)
+    r_learn = ctx.solve(h, chol, 6, 0, [64] * 4, [1e-10] * 4, seed=1, preconditioner=1)
+    it1, fb, _ = ctx.davidson_counts()
+    ctx.close()
+    ctx2 = G.Context(0)
+    r_diag = ctx2.solve(h, chol, 6, 0, [64] * 4, [1e-10] * 4, seed=1, preconditioner=0)
+    it2, _, _ = ctx2.davidson_counts()
+    ctx2.close()
+    # Davidson is preconditioner-agnostic: same converged energy
+    assert abs(r_learn["energy"] - r_diag["energy"]) < 1e-10
+    ctx3 = G.Context(0)
+    ctx3.load_precond(path)
+    r_load = ctx3.solve(h, chol, 6, 0, [64] * 4, [1e-10] * 4, seed=1, preconditioner=1)
+    assert abs(r_load["energy"] - r_diag["energy"]) < 1e-10
+    ctx3.close()
+    print("Davidson iterations: learned", it1, "diagonal", it2, "fallbacks", fb)
+
+
+def test_learned_without_weights_is_rejected(G):
+    h, chol = make_integrals(4, 4, 1)
+    ctx = G.Context(0)
+    with pytest.raises(G.GbdError, match="GBD_ERR_STATE"):
+        ctx.solve(h, chol, 4, 0, [8], [1e-8], preconditioner=1)
+    ctx.close()
