@@ -114,6 +114,26 @@ const char *gbd_last_error(const gbd_ctx *ctx);
 int gbd_solve(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule,
               gbd_result *result);
 
+/* Many independent active spaces in one call (the paper solves one active
+ * space per call; batching is this library's addition).  problems[i] is
+ * solved with schedules[i] into results[i] (caller-owned, as for
+ * gbd_solve), i = 0..n-1.  Every problem and schedule is validated before
+ * any work starts: on a bad one nothing runs, no result is touched, and
+ * GBD_ERR_ARG names its index.  The problems are then handed, most expensive first (n_orb x
+ * M^3 x sweeps), to a pool of host worker threads, each with its own
+ * engine, CUDA stream and device memory, so that the kernels of different
+ * problems run concurrently on the device.  Results do not depend on the
+ * number of workers or on the order of completion.  A problem that fails
+ * at run time sets results[i].status to its error code; the others still
+ * run, and the call returns the code of the failed problem with the
+ * lowest index (its message in gbd_last_error).  Learned preconditioning
+ * uses the weights this context holds. */
+int gbd_solve_batched(gbd_ctx *ctx, int32_t n, const gbd_problem *problems, const gbd_schedule *schedules,
+                      gbd_result *results);
+/* Worker threads of gbd_solve_batched: 0 (default) = min(n, 16, host
+ * hardware threads); otherwise at most `workers`. */
+int gbd_set_batch_workers(gbd_ctx *ctx, int32_t workers);
+
 /* Learned Davidson preconditioner (not in the paper, which names Jacobi,
  * deflation-aware diagonal, Olsen and shift-and-invert members of a
  * run-time-selectable family, Sec. "Computational details"; the reading used

@@ -35,7 +35,32 @@ typedef struct {
   double sigma_flops_exec;   /* flops executed by the tensor-core tiles (with padding) */
   double tc_ms, tc_flops;    /* tensor-core sigma builds only: device time, algorithmic flops */
   int64_t n_sigma_tc;
+  int64_t tier_iterations[3];   /* Davidson iterations in the BF16/TF32 tier, the TF32x3 tier, FP64 */
+  double max_final_residual;    /* largest ||r|| at the end of a step's Davidson solve */
+  double sum_final_residual;    /* sum of those over the steps */
+  int64_t graph_launches;       /* sigma builds replayed from a captured CUDA graph */
+  int64_t autotune_trials;      /* tensor-core plans built and timed by the tile-shape autotuner */
 } gbd_stats;
+
+/* Sigma launch sequences replayed as CUDA graphs (1, the default) or
+ * launched kernel by kernel (0); results are identical either way. */
+int gbd_set_graphs(gbd_ctx *ctx, int32_t enable);
+
+/* Tile shape of the tensor-core sigma: 0 (default) = autotuned per shape
+ * class; 64, 128 or 256 = that largest N tile for both stages.  The shape
+ * never changes the arithmetic (same products, same summation order). */
+int gbd_set_tc_tile(gbd_ctx *ctx, int32_t ncap);
+
+/* One Davidson solve at the current centre k (environments k and k+2
+ * valid, as after gbd_init_state for k = 0 or after steps up to k-1) in
+ * schedule precision `precision` (GBD_FP64/TF32/BF16) with at most
+ * `fp64_refine` FP64 iterations and residual tolerance `tol`, without
+ * decimation or environment update.  theta = its Ritz value, e64 = the FP64
+ * Rayleigh quotient <x|H|x>/<x|x> of the resulting vector, r64 = the FP64
+ * residual norm ||Hx - e64 x|| / ||x||.  Isolates the effect of the matvec
+ * precision on one step. */
+int gbd_probe_step(gbd_ctx *ctx, int32_t k, int32_t precision, int32_t fp64_refine, double tol, double *theta,
+                   double *e64, double *r64);
 
 /* Validate the problem and schedule, build the MPO; no MPS yet. */
 int gbd_setup(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule);
@@ -77,6 +102,8 @@ int gbd_mpo_labels(gbd_ctx *ctx, int32_t bond, uint64_t *keys, int32_t cap, int3
 int gbd_env_block(gbd_ctx *ctx, int32_t side, int32_t bond, int32_t channel, int32_t sector, double *out,
                   int64_t cap, int32_t *rows, int32_t *cols);
 int gbd_get_stats(const gbd_ctx *ctx, gbd_stats *stats);
+/* Counters summed over the workers of the last gbd_solve_batched call. */
+int gbd_get_batch_stats(const gbd_ctx *ctx, gbd_stats *s);
 /* Counter-based initial-MPS entry (splitmix64; the same definition as the
  * synthetic-input generator), for checking that both agree. */
 double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, int32_t s, int32_t row,

@@ -1,9 +1,16 @@
 // C ABI of the sweep engine: argument validation, error codes, and the
 // translation of exceptions into status codes (none crosses the boundary).
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <numeric>
 #include <string>
+#include <system_error>
+#include <thread>
+#include <vector>
 
 #include "../../include/gbdmrg.h"
 #include "../../include/gbdmrg_test.h"
@@ -17,6 +24,9 @@ struct gbd_ctx {
   int device = 0;
   std::unique_ptr<gbd::Engine> eng;
   std::string err;
+  int batch_workers = 0;
+  bool graphs = true;
+  gbd::Stats batch_stats;   // summed over the workers of the last batched solve
 };
 
 namespace {
@@ -135,6 +145,22 @@ void gbd_destroy(gbd_ctx* ctx) {
 
 const char* gbd_last_error(const gbd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+namespace {
+// the whole schedule of one prepared problem on engine e
+void run_solve(gbd::Engine& e, const gbd_problem* p, const gbd_schedule* s, gbd_result* r) {
+  e.init_state();
+  for (int i = 0; i < s->n_sweeps; ++i) {
+    double en = e.sweep(i);
+    if (r->sweep_energies) r->sweep_energies[i] = en + p->e_core;
+  }
+  r->energy = e.final_energy() + p->e_core;
+  if (r->rdm1 || r->rdm2) e.rdms(r->rdm1, r->rdm2);
+  r->max_discarded_weight = e.stats.max_discarded;
+  r->n_matvec = e.stats.n_sigma;
+  r->status = GBD_OK;
+}
+}  // namespace
+
 int gbd_solve(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, gbd_result* r) {
   return guarded(ctx, [&]() {
     if (!r) return fail(ctx, GBD_ERR_ARG, "result is NULL");
@@ -143,16 +169,129 @@ int gbd_solve(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, gbd_res
     gbd::Engine& e = *ctx->eng;
     if (s->preconditioner == GBD_PRECOND_LEARNED && !e.mlp_loaded)
       return fail(ctx, GBD_ERR_STATE, "learned preconditioner requested but no weights are loaded");
-    e.init_state();
-    for (int i = 0; i < s->n_sweeps; ++i) {
-      double en = e.sweep(i);
-      if (r->sweep_energies) r->sweep_energies[i] = en + p->e_core;
+    run_solve(e, p, s, r);
+    return GBD_OK;
+  });
+}
+
+int gbd_set_batch_workers(gbd_ctx* ctx, int32_t workers) {
+  if (!ctx || workers < 0) return GBD_ERR_ARG;
+  ctx->batch_workers = workers;
+  return GBD_OK;
+}
+
+int gbd_solve_batched(gbd_ctx* ctx, int32_t n, const gbd_problem* problems, const gbd_schedule* schedules,
+                      gbd_result* results) {
+  return guarded(ctx, [&]() {
+    if (n < 0) return fail(ctx, GBD_ERR_ARG, "n < 0");
+    if (n == 0) return GBD_OK;
+    if (!problems || !schedules || !results) return fail(ctx, GBD_ERR_ARG, "problems, schedules or results is NULL");
+    bool learned = false;
+    for (int i = 0; i < n; ++i) {
+      int rc = validate(ctx, &problems[i], &schedules[i]);
+      if (rc != GBD_OK) return fail(ctx, rc, "problem " + std::to_string(i) + ": " + ctx->err);
+      learned |= schedules[i].preconditioner == GBD_PRECOND_LEARNED;
     }
-    r->energy = e.final_energy() + p->e_core;
-    if (r->rdm1 || r->rdm2) e.rdms(r->rdm1, r->rdm2);
-    r->max_discarded_weight = e.stats.max_discarded;
-    r->n_matvec = e.stats.n_sigma;
-    r->status = GBD_OK;
+    const std::vector<float>* weights = nullptr;
+    if (learned) {
+      if (!ctx->eng || !ctx->eng->mlp_loaded)
+        return fail(ctx, GBD_ERR_STATE, "learned preconditioner requested but no weights are loaded");
+      weights = &ctx->eng->precond_weights();
+    }
+    for (int i = 0; i < n; ++i) results[i].status = GBD_ERR_STATE;   // until solved
+    // most expensive first (longest-processing-time order)
+    std::vector<int> order(n);
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) {
+      int mmax = 1;
+      for (int k = 0; k < schedules[i].n_sweeps; ++k) mmax = std::max(mmax, schedules[i].bond_dim[k]);
+      cost[i] = (double)problems[i].n_orb * mmax * (double)mmax * mmax * schedules[i].n_sweeps;
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    int nw = std::min({n, 16, hw});
+    if (ctx->batch_workers > 0) nw = std::min(n, ctx->batch_workers);
+    std::atomic<int> next{0};
+    std::mutex mu;
+    ctx->batch_stats = gbd::Stats();
+    int first_bad = n;
+    std::string first_msg;
+    auto record = [&](int i, int code, const std::string& msg) {
+      results[i].status = code;
+      std::lock_guard<std::mutex> g(mu);
+      if (i < first_bad) {
+        first_bad = i;
+        first_msg = "problem " + std::to_string(i) + ": " + msg;
+      }
+    };
+    auto worker = [&]() {
+      std::unique_ptr<gbd::Engine> eng;
+      try {
+        eng.reset(new gbd::Engine(ctx->device));
+        eng->use_graphs = ctx->graphs;
+        if (weights) eng->set_precond_weights(weights->data());
+      } catch (const std::exception& ex) {
+        // no engine: fail every problem this worker would have taken
+        for (int j; (j = next.fetch_add(1)) < n;) record(order[j], GBD_ERR_CUDA, ex.what());
+        return;
+      }
+      for (int j; (j = next.fetch_add(1)) < n;) {
+        const int i = order[j];
+        const gbd_problem* p = &problems[i];
+        const gbd_schedule* s = &schedules[i];
+        try {
+          eng->prepare(p->n_orb, p->n_elec, p->two_sz, p->n_chol, p->h, p->chol, p->e_core, to_schedule(s));
+          run_solve(*eng, p, s, &results[i]);
+          std::lock_guard<std::mutex> g(mu);
+          ctx->batch_stats.add(eng->stats);
+        } catch (const gbd::Error& ex) {
+          record(i, ex.code, ex.what());
+        } catch (const std::bad_alloc&) {
+          record(i, GBD_ERR_OOM, "host allocation failed");
+        } catch (const std::exception& ex) {
+          record(i, GBD_ERR_CUDA, ex.what());
+        }
+      }
+    };
+    std::vector<std::thread> pool;
+    try {
+      for (int w = 1; w < nw; ++w) pool.emplace_back(worker);
+    } catch (const std::system_error&) {
+      // fewer threads than asked for: the started ones and this one share the queue
+    }
+    worker();
+    for (auto& t : pool) t.join();
+    if (first_bad < n) return fail(ctx, results[first_bad].status, first_msg);
+    return GBD_OK;
+  });
+}
+
+int gbd_set_graphs(gbd_ctx* ctx, int32_t enable) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->use_graphs = enable != 0;
+    ctx->graphs = enable != 0;
+    return GBD_OK;
+  });
+}
+
+int gbd_set_tc_tile(gbd_ctx* ctx, int32_t ncap) {
+  return guarded(ctx, [&]() {
+    if (ncap != 0 && ncap != 64 && ncap != 128 && ncap != 256) return fail(ctx, GBD_ERR_ARG, "ncap not in {0,64,128,256}");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tc_fixed_cap = ncap;
+    return GBD_OK;
+  });
+}
+
+int gbd_probe_step(gbd_ctx* ctx, int32_t k, int32_t precision, int32_t fp64_refine, double tol, double* theta,
+                   double* e64, double* r64) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    if (precision < 0 || precision > 2 || fp64_refine < 0 || !(tol > 0) || !theta || !e64 || !r64)
+      return fail(ctx, GBD_ERR_ARG, "bad probe arguments");
+    ctx->eng->probe_step(k, precision, fp64_refine, tol, theta, e64, r64);
     return GBD_OK;
   });
 }
@@ -407,11 +546,8 @@ int gbd_davidson_counts(gbd_ctx* ctx, int64_t* iterations, int64_t* fallbacks, i
   });
 }
 
-int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {
-  if (!ctx || !s) return GBD_ERR_ARG;
+static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   std::memset(s, 0, sizeof(*s));
-  if (!ctx->eng) return GBD_OK;
-  const gbd::Stats& t = ctx->eng->stats;
   s->sigma_flops = t.sigma_flops;
   s->sigma_ms = t.sigma_ms;
   s->env_flops = t.env_flops;
@@ -430,6 +566,23 @@ int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {
   s->tc_ms = t.tc_ms;
   s->tc_flops = t.tc_flops;
   s->n_sigma_tc = t.n_sigma_tc;
+  for (int i = 0; i < 3; ++i) s->tier_iterations[i] = t.tier_iters[i];
+  s->max_final_residual = t.max_final_residual;
+  s->sum_final_residual = t.sum_final_residual;
+  s->graph_launches = t.graph_launches;
+  s->autotune_trials = t.autotune_trials;
+}
+
+int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {
+  if (!ctx || !s) return GBD_ERR_ARG;
+  std::memset(s, 0, sizeof(*s));
+  if (ctx->eng) copy_stats(ctx->eng->stats, s);
+  return GBD_OK;
+}
+
+int gbd_get_batch_stats(const gbd_ctx* ctx, gbd_stats* s) {
+  if (!ctx || !s) return GBD_ERR_ARG;
+  copy_stats(ctx->batch_stats, s);
   return GBD_OK;
 }
 

@@ -829,6 +829,7 @@ struct Engine::Sigma {
   double* in = nullptr;
   double* out = nullptr;
   GemmPlan A, B;
+  GraphSeq graph;
 };
 
 void Engine::plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg) {
@@ -894,8 +895,10 @@ void Engine::sigma(Sigma& sg, const double* x, double* y) {
   settle();
   CK(cudaMemcpyAsync(sg.in, x, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   CK(cudaEventRecord(ev0, stream));
-  run(sg.A);
-  run(sg.B);
+  replay(sg.graph, [&]() {
+    run(sg.A);
+    run(sg.B);
+  });
   CK(cudaEventRecord(ev1, stream));
   CK(cudaMemcpyAsync(y, sg.out, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   sigma_pending = 1;
@@ -966,7 +969,7 @@ void Engine::compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag) {
 // with |diag - theta| clamped to 1e-8; two classical Gram-Schmidt passes;
 // restart from the 4 lowest Ritz vectors when the space is full.
 double Engine::davidson(const std::function<void(const double*, double*)>& op, const double* diag, double tol,
-                        int max_iter, int max_space, bool stop_on_stagnation) {
+                        int max_iter, int max_space, double stag_floor) {
   // Two host synchronisations per iteration: the residual norm (convergence
   // test) and the new row of the projected matrix.  Gram-Schmidt
   // coefficients and the normalisation never leave the device.
@@ -1053,10 +1056,12 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     double rn = std::sqrt(std::max(rr, 0.0));
     stats.last_residual = rn;
     if (rn < tol || it >= max_iter) break;
-    // reduced-precision operators have a residual floor near u ||H||: stop
-    // when six iterations have not reduced ||r|| by 30 %
+    // reduced-precision operators have a residual floor near u ||H||: below
+    // stag_floor, stop when three iterations have not reduced ||r|| by 30 %;
+    // anywhere, when eight have not
     rhist.push_back(rn);
-    if (stop_on_stagnation && rhist.size() > 6 && rn > 0.7 * rhist[rhist.size() - 7]) break;
+    if (stag_floor > 0 && rhist.size() > 3 && rn > 0.7 * rhist[rhist.size() - 4] && rn < stag_floor) break;
+    if (stag_floor > 0 && rhist.size() > 8 && rn > 0.7 * rhist[rhist.size() - 9]) break;
     stats.davidson_iters++;
     if (recording) record_iteration(r, diag, x, scalars(theta, rn, it));
     if (learned && !fallback) {
@@ -1256,6 +1261,121 @@ void Engine::truncate(int k, int dir, int M, double* tau_out, std::vector<double
 }
 
 // ------------------------------------------------------------------ one step
+// Davidson of one step.  FP64 schedule: plain FP64 Davidson.  Reduced
+// precision: tier 1 (BF16 or TF32 single pass) while the residual is large,
+// tier 2 (TF32x3, split-K FP64 sums) to its floor, then at most `refine`
+// FP64 iterations.  Each tier restarts from the previous tier's Ritz vector.
+double Engine::solve_tiers(Sigma& sg, const double* diag, double tol, int precision, int refine, bool& planned) {
+  double theta = 0;
+  auto fp64op = [&](const double* x, double* y) {
+    if (!planned) {
+      plan_sigma(sg.lenl, sg.renl, sg);
+      planned = true;
+    }
+    sigma(sg, x, y);
+  };
+  int64_t it0 = stats.davidson_iters;
+  auto tier_done = [&](int t) {
+    stats.tier_iters[t] += stats.davidson_iters - it0;
+    it0 = stats.davidson_iters;
+  };
+  // scale of |H_eff| for the stagnation floors: the diagonal's largest magnitude
+  double hscale = 1.0;
+  if (precision != 0) {
+    double* dmax = dalloc<double>(1);
+    launch_absmax(diag, psi_size, dmax, stream);
+    CK(cudaMemcpyAsync(&hscale, dmax, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    sync();
+    dfree(dmax);
+    hscale = std::max(hscale, 1.0);
+  }
+  if (precision == 0) {
+    theta = davidson(fp64op, diag, tol, sched.max_iter, sched.max_space, 0.0);
+    tier_done(2);
+  } else {
+    const int p1 = precision == 2 ? kBF16 : kTF32;
+    const double floor1 = p1 == kBF16 ? 5e-2 : 1e-2;
+    // measured relative sigma errors: BF16 2e-3, TF32 3e-4, TF32x3 3e-6
+    const double u1 = p1 == kBF16 ? 2e-3 : 3e-4, u2 = 3e-6;
+    TcPlan* P = tc_plan(sg.lenl, sg.renl, p1);
+    theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, std::max(tol, floor1),
+                     sched.max_iter, sched.max_space, 30.0 * u1 * hscale);
+    tc_free(P);
+    tier_done(0);
+    if (stats.last_residual >= tol) {
+      P = tc_plan(sg.lenl, sg.renl, kTF32x3);
+      theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, tol, sched.max_iter,
+                       sched.max_space, 30.0 * u2 * hscale);
+      tc_free(P);
+      tier_done(1);
+    }
+    if (refine > 0 && stats.last_residual >= tol) {
+      theta = davidson(fp64op, diag, tol, refine, sched.max_space, 0.0);
+      tier_done(2);
+    }
+  }
+  stats.max_final_residual = std::max(stats.max_final_residual, stats.last_residual);
+  stats.sum_final_residual += stats.last_residual;
+  return theta;
+}
+
+void Engine::free_sigma(Sigma& sg, bool planned) {
+  if (!planned) return;
+  drop(sg.graph);
+  release(sg.A);
+  release(sg.B);
+  dfree(sg.Y);
+  dfree(sg.in);
+  dfree(sg.out);
+}
+
+void Engine::probe_step(int k, int precision, int refine, double tol, double* theta, double* e64, double* r64) {
+  if (k < 0 || k + 1 >= n || !Lenv[k].valid || !Renv[k + 2].valid)
+    throw Error(-6, "probe_step needs valid environments at the centre k");
+  setup_two_site(k);
+  form_psi(k, 0);
+  Sigma sg;
+  AxpyPlan ax;
+  build_lenl(k, Lenv[k], EL, sg.lenl, ax);
+  finish_enl(sg.lenl, ax);
+  build_renl(k + 1, Renv[k + 2], ER, sg.renl, ax);
+  finish_enl(sg.renl, ax);
+  double* diag = dalloc<double>(psi_size);
+  compute_diag(sg.lenl, sg.renl, diag);
+  bool planned = false;
+  *theta = solve_tiers(sg, diag, tol, precision, refine, planned);
+  if (!planned) {
+    plan_sigma(sg.lenl, sg.renl, sg);
+    planned = true;
+  }
+  double* y = dalloc<double>(psi_size);
+  sigma(sg, psi, y);
+  std::vector<double> hx(psi_size), hy(psi_size);
+  CK(cudaMemcpyAsync(hx.data(), psi, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  settle();
+  double xx = 0, xy = 0;
+  for (int64_t i = 0; i < psi_size; ++i) {
+    xx += hx[i] * hx[i];
+    xy += hx[i] * hy[i];
+  }
+  const double e = xy / xx;
+  double rr = 0;
+  for (int64_t i = 0; i < psi_size; ++i) {
+    const double d = hy[i] - e * hx[i];
+    rr += d * d;
+  }
+  *e64 = e;
+  *r64 = std::sqrt(rr / xx);
+  dfree(y);
+  dfree(diag);
+  free_sigma(sg, planned);
+  free_enl(sg.lenl);
+  free_enl(sg.renl);
+  sync();
+}
+
 double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept) {
   double t0 = now_ms();
   setup_two_site(k);
@@ -1274,42 +1394,10 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
   double td = now_ms();
   double theta = 0;
   bool planned = false;
-  auto fp64op = [&](const double* x, double* y) {
-    if (!planned) {
-      plan_sigma(sg.lenl, sg.renl, sg);
-      planned = true;
-    }
-    sigma(sg, x, y);
-  };
-  if (sched.precision == 0) {
-    theta = davidson(fp64op, diag, tol, sched.max_iter, sched.max_space, false);
-  } else {
-    // tier 1: BF16 or TF32 single pass while the residual is large; tier 2:
-    // TF32x3 to its floor; then at most `refine` FP64 iterations
-    const int p1 = sched.precision == 2 ? kBF16 : kTF32;
-    const double floor1 = p1 == kBF16 ? 5e-2 : 1e-2;
-    TcPlan* P = tc_build(sg.lenl, sg.renl, p1);
-    theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, std::max(tol, floor1),
-                     sched.max_iter, sched.max_space, true);
-    tc_free(P);
-    if (stats.last_residual >= tol) {
-      P = tc_build(sg.lenl, sg.renl, kTF32x3);
-      theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, tol, sched.max_iter,
-                       sched.max_space, true);
-      tc_free(P);
-    }
-    if (sched.refine > 0 && stats.last_residual >= tol)
-      theta = davidson(fp64op, diag, tol, sched.refine, sched.max_space, false);
-  }
+  theta = solve_tiers(sg, diag, tol, sched.precision, sched.refine, planned);
   stats.davidson_ms += now_ms() - td;
   dfree(diag);
-  if (planned) {
-    release(sg.A);
-    release(sg.B);
-    dfree(sg.Y);
-    dfree(sg.in);
-    dfree(sg.out);
-  }
+  free_sigma(sg, planned);
   double tt = now_ms();
   truncate(k, dir, M, tau, kept);
   stats.trunc_ms += now_ms() - tt;
@@ -1644,7 +1732,7 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, 
     plan_sigma(sg.lenl, sg.renl, sg);
     sigma(sg, psi, y);
   } else {
-    TcPlan* P = tc_build(sg.lenl, sg.renl, prec == 1 ? kTF32 : prec == 2 ? kBF16 : kTF32x3);
+    TcPlan* P = tc_plan(sg.lenl, sg.renl, prec == 1 ? kTF32 : prec == 2 ? kBF16 : kTF32x3);
     tc_apply(P, psi, y);
     tc_free(P);
   }

@@ -83,6 +83,21 @@ struct Stats {
   int64_t n_sigma_tc = 0;
   int64_t n_sigma = 0, n_steps = 0, launches = 0, h2d = 0, d2h = 0;
   int64_t davidson_iters = 0, precond_fallbacks = 0;
+  int64_t tier_iters[3] = {0, 0, 0};
+  double max_final_residual = 0, sum_final_residual = 0;   // over Davidson solves
+  int64_t graph_launches = 0, autotune_trials = 0;
+  void add(const Stats& o) {   // sum of the additive counters (batched solves)
+    sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
+    enl_ms += o.enl_ms; step_ms += o.step_ms; trunc_ms += o.trunc_ms; davidson_ms += o.davidson_ms;
+    sigma_flops_exec += o.sigma_flops_exec; tc_ms += o.tc_ms; tc_flops += o.tc_flops;
+    n_sigma_tc += o.n_sigma_tc; n_sigma += o.n_sigma; n_steps += o.n_steps; launches += o.launches;
+    h2d += o.h2d; d2h += o.d2h; davidson_iters += o.davidson_iters; precond_fallbacks += o.precond_fallbacks;
+    for (int i = 0; i < 3; ++i) tier_iters[i] += o.tier_iters[i];
+    max_final_residual = std::max(max_final_residual, o.max_final_residual);
+    sum_final_residual += o.sum_final_residual;
+    graph_launches += o.graph_launches; autotune_trials += o.autotune_trials;
+    max_discarded = std::max(max_discarded, o.max_discarded);
+  }   // Davidson iterations: low-precision tier, TF32x3 tier, FP64
   double max_discarded = 0;
 };
 
@@ -95,6 +110,15 @@ struct Schedule {
 };
 
 struct TcPlan;
+
+struct TcTune {     // numerics-neutral tile shape of the tensor-core sigma
+  int ncap[2] = {256, 256};   // largest N tile of stage A and of stage B (64, 128, 256)
+};
+
+struct GraphSeq {   // one captured launch sequence (see Engine::replay)
+  cudaGraphExec_t exec = nullptr;
+  int calls = 0;
+};
 
 class Engine {
  public:
@@ -129,6 +153,10 @@ class Engine {
   void load_precond(const char* path);
   bool recording = false;
   bool mlp_loaded = false;
+  bool use_graphs = true;     // replay the sigma launch sequences as CUDA graphs
+  bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
+  int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
+  const std::vector<float>& precond_weights() const { return mlp_f32; }
   int64_t n_samples() const { return (int64_t)data_y.size(); }
 
   Stats stats;
@@ -200,13 +228,53 @@ class Engine {
   void plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg);
   void sigma(Sigma& sg, const double* x, double* y);
   void compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag);
+  // stag_floor > 0: stop on stagnation (reduced-precision operators); see the definition
   double davidson(const std::function<void(const double*, double*)>& op, const double* diag, double tol,
-                  int max_iter, int max_space, bool stop_on_stagnation);
-  TcPlan* tc_build(const EnlOp& lenl, const EnlOp& renl, int prec);
+                  int max_iter, int max_space, double stag_floor);
+  // the Davidson solve of one step in schedule precision `precision` with at
+  // most `refine` FP64 iterations; the Ritz vector is left in psi
+  double solve_tiers(Sigma& sg, const double* diag, double tol, int precision, int refine, bool& planned);
+  void free_sigma(Sigma& sg, bool planned);
+  TcPlan* tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune tune = TcTune());
+  TcPlan* tc_plan(const EnlOp& lenl, const EnlOp& renl, int prec);   // tc_build with the tuned shape
+  std::map<int64_t, TcTune> tuned;
   void tc_apply(TcPlan* p, const double* x, double* y);
   void tc_free(TcPlan* p);
   void truncate(int k, int dir, int M, double* tau, std::vector<double>* kept);
+  // A fixed launch sequence on `stream`: run directly on its first use,
+  // captured into a CUDA graph on the second, replayed from then on.
+  template <class F>
+  void replay(GraphSeq& g, F&& launches) {
+    if (!use_graphs || g.calls++ == 0) {
+      launches();
+      return;
+    }
+    if (!g.exec) {
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      launches();
+      CK(cudaStreamEndCapture(stream, &graph));
+      cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(e);
+    }
+    CK(cudaGraphLaunch(g.exec, stream));
+    stats.graph_launches++;
+  }
+  static void drop(GraphSeq& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.calls = 0;
+  }
   double step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept);
+
+ public:
+  // Davidson at the current centre k in the given schedule precision
+  // without decimation or environment update: Ritz value, and the FP64
+  // Rayleigh quotient and FP64 residual norm of the resulting vector
+  void probe_step(int k, int precision, int refine, double tol, double* theta, double* e64, double* r64);
+
+ private:
   void init_mps(uint64_t seed, int M);
   void build_right_envs(int from_k);
   void build_left_envs(int to_k);

@@ -132,6 +132,8 @@ void launch_multi_dot(const double* V, int64_t stride, int k, const double* x, i
 void launch_lincomb(double* out, const double* V, int64_t stride, const double* coef_dev, int k, int64_t n,
                     int accumulate, cudaStream_t s, double coef_scale = 1.0);
 void launch_normalize(const double* t, const double* nrm2_dev, int64_t n, double* out, cudaStream_t s);
+// *out = max_i |x_i| (out is overwritten)
+void launch_absmax(const double* x, int64_t n, double* out, cudaStream_t s);
 void launch_residual_precond(const double* x, const double* sx, const double* diag, double theta, int64_t n,
                              double* r, double* t, double* partial, int nblk, double* out_dev, cudaStream_t s);
 void launch_scale(double* x, double a, int64_t n, cudaStream_t s);

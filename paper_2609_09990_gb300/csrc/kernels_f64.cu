@@ -243,6 +243,26 @@ void launch_scale(double* x, double a, int64_t n, cudaStream_t s) {
   scale_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, a, n);
 }
 
+namespace {
+// the bit patterns of non-negative doubles order like the values, so the
+// maximum of |x| is an unsigned 64-bit atomicMax
+__global__ void absmax_kernel(const double* __restrict__ x, int64_t n, unsigned long long* out) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+}  // namespace
+
+void launch_absmax(const double* x, int64_t n, double* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(double), s);
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  absmax_kernel<<<(int)b, 256, 0, s>>>(x, n, reinterpret_cast<unsigned long long*>(out));
+}
+
 }  // namespace gbd
 
 // ---------------------------------------------------------------------------

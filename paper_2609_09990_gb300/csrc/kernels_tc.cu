@@ -14,6 +14,8 @@
 // hi*hi + hi*lo + lo*hi into the same accumulator.
 // Every mbarrier wait is bounded: on timeout the kernel raises *err, all
 // roles stop issuing, and TMEM is released before the CTA exits.
+#include <mutex>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -26,7 +28,8 @@ namespace {
 constexpr int kThreads = 192;
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int kStageA = 128 * 128;          // bytes of one A box (128 rows x 128 B)
-constexpr int kStageB = 256 * 128;          // bytes of the largest B box
+constexpr int kSmemBudget = 232448;         // dynamic shared memory per CTA
+constexpr int kMaxStages = 8;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -124,8 +127,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const bool x3 = L.prec == kTF32x3;
   const bool bf = L.prec == kBF16;
-  const int stages = 4 / (x3 ? 2 : 1);
-  const int stage_bytes = (kStageA + kStageB) * (x3 ? 2 : 1);
+  // B boxes of this launch are at most L.ncap rows; the ring holds as many
+  // stages as fit (tc_stages)
+  const int bstage = L.ncap * 128;
+  const int stages = L.stages;
+  const int stage_bytes = (kStageA + bstage) * (x3 ? 2 : 1);
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(base + stages * stage_bytes);
   uint64_t* empty = full + stages;
@@ -173,11 +179,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           uint8_t* sb = sa + kStageA;
           mbar_expect_tx(&full[stage], tx);
           tma_load_2d(sa, &maps.a[0], tm.ax + k0, tm.ay + T.m0, &full[stage]);
-          tma_load_2d(sb, &maps.b[0][T.bsel], k0, tm.by, &full[stage]);
+          tma_load_2d(sb, &maps.b[0][T.bsel], tm.bx + k0, tm.by, &full[stage]);
           if (x3) {
-            uint8_t* sa2 = sb + kStageB;
+            uint8_t* sa2 = sb + bstage;
             tma_load_2d(sa2, &maps.a[1], tm.ax + k0, tm.ay + T.m0, &full[stage]);
-            tma_load_2d(sa2 + kStageA, &maps.b[1][T.bsel], k0, tm.by, &full[stage]);
+            tma_load_2d(sa2 + kStageA, &maps.b[1][T.bsel], tm.bx + k0, tm.by, &full[stage]);
           }
           if (++stage == stages) { stage = 0; ph ^= 1; }
         }
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             } else {
               mma_tf32(dt, ad, bd, idesc, first ? 0u : 1u);
               if (x3) {
-                const uint32_t sa2 = sb + kStageB, sb2 = sa2 + kStageA;
+                const uint32_t sa2 = sb + bstage, sb2 = sa2 + kStageA;
                 mma_tf32(dt, ad, smem_desc(sb2 + kk * 32), idesc, 1u);                 // hi * lo
                 mma_tf32(dt, smem_desc(sa2 + kk * 32), bd, idesc, 1u);                 // lo * hi
               }
@@ -249,11 +255,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const bool has = T.t1 > T.t0;
       const bool live = row < T.m_valid;
       int pcol = 0;
+      int64_t prow = 0;
       if (T.mode == kTcYT && live) {
         int r = T.m0 + row, s = 0;
         for (int u = 1; u < 4; ++u)
           if (r >= T.rbreak[u]) s = u;
         pcol = T.rpad[s] + (r - T.rbreak[s]);
+      } else if (T.mode == kTcYTmap && live) {
+        prow = L.rowmap[T.out + row];
       }
       for (int c0 = 0; c0 < T.n_mma; c0 += 16) {
         float v[16];
@@ -271,8 +280,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (T.mode == kTcSigma) {
             double* o = L.f64 + T.out + (int64_t)j * T.ld + T.m0 + row;
             *o = T.beta ? (*o + (double)v[i]) : (double)v[i];
+          } else if (T.mode == kTcPart) {
+            L.part[T.out + (int64_t)j * 128 + row] = v[i];
           } else {
-            const int64_t idx = (T.out + j) * (int64_t)T.ld + pcol;
+            int64_t idx;
+            if (T.mode == kTcYTmap) {
+              const int p = T.n0 + j;
+              int s = 0;
+              for (int u = 1; u < 4; ++u)
+                if (p >= T.rbreak[u]) s = u;
+              idx = prow * T.ld + T.rpad[s] + (p - T.rbreak[s]);
+            } else {
+              idx = (T.out + j) * (int64_t)T.ld + pcol;
+            }
             if (bf) {
               reinterpret_cast<__nv_bfloat16*>(L.yt_hi)[idx] = __float2bfloat16_rn(v[i]);
             } else {
@@ -291,6 +311,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// ---------------------------------------------------------------- split-K sum
+// one thread per output element; the slots are summed in FP64 with four
+// interleaved partial sums combined in a fixed order (deterministic)
+__global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, int64_t total,
+                                 const float* __restrict__ part, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].e0 <= e) lo = mid; else hi = mid - 1;
+    }
+    const TcRed R = tasks[lo];
+    const int loc = (int)(e - R.e0);
+    const int j = loc / R.m_valid, i = loc - j * R.m_valid;
+    const int64_t ss = (int64_t)128 * R.n_stride;
+    const float* p = part + R.slot0 + (int64_t)j * 128 + i;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int s = 0;
+    for (; s + 4 <= R.nslot; s += 4) {
+      a0 += (double)p[s * ss];
+      a1 += (double)p[(s + 1) * ss];
+      a2 += (double)p[(s + 2) * ss];
+      a3 += (double)p[(s + 3) * ss];
+    }
+    for (; s < R.nslot; ++s) a0 += (double)p[s * ss];
+    out[R.out + (int64_t)j * R.ld + R.m0 + i] = (a0 + a1) + (a2 + a3);
+  }
 }
 
 // ---------------------------------------------------------------- conversions
@@ -336,22 +385,38 @@ __global__ void tc_convert_psi_kernel(const double* __restrict__ psi, const TcPs
 
 }  // namespace
 
-int tc_smem_bytes(int prec) {
-  const int stages = prec == kTF32x3 ? 2 : 4;
-  const int stage_bytes = (kStageA + kStageB) * (prec == kTF32x3 ? 2 : 1);
+void launch_tc_reduce(const TcRed* tasks, int ntasks, int64_t total, const float* part, double* out,
+                      cudaStream_t s) {
+  if (ntasks <= 0 || total <= 0) return;
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  tc_reduce_kernel<<<(int)b, 256, 0, s>>>(tasks, ntasks, total, part, out);
+}
+
+int tc_stages(int prec, int ncap) {
+  const int stage_bytes = (kStageA + ncap * 128) * (prec == kTF32x3 ? 2 : 1);
+  int s = (kSmemBudget - 1024 - 256) / stage_bytes;
+  return s < kMaxStages ? s : kMaxStages;
+}
+
+int tc_smem_bytes(int prec, int ncap) {
+  const int stages = tc_stages(prec, ncap);
+  const int stage_bytes = (kStageA + ncap * 128) * (prec == kTF32x3 ? 2 : 1);
   return 1024 + stages * stage_bytes + (2 * stages + 4) * 8 + 16;
 }
 
-void launch_tc_gemm(const TcMaps& maps, const TcLaunch& L, int num_sms, cudaStream_t s) {
-  if (L.ntiles <= 0) return;
-  const int smem = tc_smem_bytes(L.prec);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    attr_set = true;
-  }
+bool launch_tc_gemm(const TcMaps& maps, const TcLaunch& L, int num_sms, cudaStream_t s) {
+  if (L.ncap != 64 && L.ncap != 128 && L.ncap != 256) return false;
+  if (L.stages != tc_stages(L.prec, L.ncap)) return false;
+  if (L.ntiles <= 0) return true;
+  const int smem = tc_smem_bytes(L.prec, L.ncap);
+  static std::once_flag attr_once;   // engines on several host threads share the kernel
+  std::call_once(attr_once, []() {
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  });
   const int grid = L.ntiles < num_sms ? L.ntiles : num_sms;
   tc_gemm_kernel<<<grid, kThreads, smem, s>>>(maps, L);
+  return true;
 }
 
 void launch_tc_convert(const TcConv* tasks, int ntasks, int prec, void* hi, void* lo, int64_t pitch,

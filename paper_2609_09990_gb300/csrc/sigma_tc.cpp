@@ -9,19 +9,22 @@
 // (TMEM) and stores it as FP64.  The enlarged operators and environments
 // stay FP64; only the matvec inside Davidson changes precision.
 #include <algorithm>
+#include <array>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 
 #include "engine.h"
 #include "tc_gemm.h"
 
 namespace gbd {
 
-int tc_smem_bytes(int prec);
 
 struct TcPlan {
   int prec = 0, eb = 2;
+  TcTune tune;
   void *psi[2] = {nullptr, nullptr}, *rs[2] = {nullptr, nullptr}, *ls[2] = {nullptr, nullptr},
        *yt[2] = {nullptr, nullptr};
   int64_t psi_pitch = 0, rs_pitch = 0, ls_pitch = 0, yt_pitch = 0;
@@ -31,6 +34,14 @@ struct TcPlan {
   TcTerm* d_terms[2] = {nullptr, nullptr};
   int ntiles[2] = {0, 0};
   TcMaps maps[2];
+  float* part = nullptr;         // split-K partial slots of stage B
+  int64_t* d_rowmap = nullptr;   // stage A: Y^T row of every stacked Renl row
+  double *xin = nullptr, *yout = nullptr;   // fixed sigma input/output of the replayed graph
+  GraphSeq graph;
+  TcRed* d_red = nullptr;
+  int nred = 0;
+  int64_t red_total = 0;
+  int64_t kc = 0;                // split-K chunk length (summed K of whole terms)
   int* d_err = nullptr;
   double flops_alg = 0, flops_exec = 0;
 };
@@ -45,9 +56,10 @@ inline int bsel_for(int n) {
 }
 }  // namespace
 
-TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
+TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune tune) {
   TcPlan* P = new TcPlan();
   P->prec = prec;
+  P->tune = tune;
   P->eb = prec == kBF16 ? 2 : 4;
   const int nh = prec == kTF32x3 ? 2 : 1;
   const int nq = EL.n();
@@ -79,7 +91,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
     }
   }
   P->psi_pitch = up64(wmax);
-  const int64_t psi_rows = std::max<int64_t>(rows, 1);
+  const int64_t psi_rows = std::max<int64_t>(rows, 256);   // >= the largest B box
   // ---- sub-block panels
   auto sub_panel = [&](const EnlOp& op, std::vector<int64_t>& rowof, int64_t& pitch) {
     int64_t r = 0, w = 0;
@@ -92,9 +104,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
     pitch = up64(w);
     return std::max<int64_t>(r, 1);
   };
-  std::vector<int64_t> rs_row, ls_row;
-  const int64_t rs_rows = sub_panel(renl, rs_row, P->rs_pitch);
-  const int64_t ls_rows = sub_panel(lenl, ls_row, P->ls_pitch);
+  std::vector<int64_t> ls_row;
+  const int64_t ls_rows = std::max<int64_t>(sub_panel(lenl, ls_row, P->ls_pitch), 256);
   // ---- Y blocks (b, Qin) -> rows E_R(Qout) of the Y^T panel
   std::map<std::pair<int, int>, std::vector<int>> rby, lout;
   std::map<std::pair<int, int>, int> lhas;
@@ -112,7 +123,68 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
     yrows += ER.dim[qout];
   }
   P->yt_pitch = up64(wlmax);
-  yrows = std::max<int64_t>(yrows, 1);
+  yrows = std::max<int64_t>(yrows, 128);
+  // ---- stage A operand: the Renl sub-blocks with the same (qin, qout, so)
+  //      and the same set of input local states si, stacked over b (rows
+  //      m(so) per b), one 16-aligned column section per si.  Every stacked
+  //      row is one row of Y^T, so a 128-row A box covers many channels b.
+  struct AGroup {
+    int qin, qout, so, mask;
+    std::vector<std::array<int, 4>> mem;   // per b: sub index for each si (-1: none)
+    std::vector<int> b;
+    int64_t row0 = 0;
+    std::array<int, 4> col{};
+  };
+  std::vector<AGroup> groups;
+  std::vector<int64_t> rowmap;
+  int64_t rs_rows = 0, rs_width = 0;
+  {
+    std::map<std::tuple<int, int, int>, std::array<int, 4>> bso;   // (b, qin, so) -> subs per si
+    for (size_t i = 0; i < renl.subs.size(); ++i) {
+      const EnlSub& s = renl.subs[i];
+      if (!ybase.count({s.b, s.qin})) continue;
+      auto it = bso.find({s.b, s.qin, s.sout});
+      if (it == bso.end()) it = bso.emplace(std::make_tuple(s.b, s.qin, s.sout), std::array<int, 4>{-1, -1, -1, -1}).first;
+      if (it->second[s.sin] >= 0) throw Error(-3, "duplicate enlarged-operator sub-block");
+      it->second[s.sin] = (int)i;
+    }
+    std::map<std::tuple<int, int, int, int>, int> gidx;
+    for (auto& kv : bso) {
+      const int b = std::get<0>(kv.first), qin = std::get<1>(kv.first), so = std::get<2>(kv.first);
+      int mask = 0, any = -1;
+      for (int si = 0; si < 4; ++si)
+        if (kv.second[si] >= 0) {
+          mask |= 1 << si;
+          any = kv.second[si];
+        }
+      const int qout = renl.subs[any].qout;
+      auto key = std::make_tuple(qin, qout, so, mask);
+      auto g = gidx.find(key);
+      if (g == gidx.end()) {
+        g = gidx.emplace(key, (int)groups.size()).first;
+        groups.push_back(AGroup{qin, qout, so, mask, {}, {}, 0, {}});
+      }
+      groups[g->second].mem.push_back(kv.second);
+      groups[g->second].b.push_back(b);
+    }
+    for (AGroup& g : groups) {
+      const int mso = ER.sdim[g.qout][g.so];
+      g.row0 = rs_rows;
+      int64_t w = 0;
+      for (int si = 0; si < 4; ++si) {
+        g.col[si] = (int)w;
+        if (g.mask >> si & 1) w += up16(ER.sdim[g.qin][si]);
+      }
+      rs_width = std::max(rs_width, w);
+      for (size_t bi = 0; bi < g.b.size(); ++bi) {
+        const int64_t y0 = ybase[{g.b[bi], g.qin}] + ER.soff[g.qout][g.so];
+        for (int r = 0; r < mso; ++r) rowmap.push_back(y0 + r);
+      }
+      rs_rows += (int64_t)g.b.size() * mso;
+    }
+  }
+  P->rs_pitch = up64(rs_width);
+  rs_rows = std::max<int64_t>(rs_rows, 128);
   // ---- allocate and zero the panels
   for (int h = 0; h < nh; ++h) {
     P->psi[h] = dalloc<uint8_t>((size_t)(psi_rows * P->psi_pitch * P->eb));
@@ -125,12 +197,14 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
     CK(cudaMemsetAsync(P->yt[h], 0, yrows * P->yt_pitch * P->eb, stream));
   }
   // ---- convert the sub-blocks (once per step)
-  auto convert = [&](const EnlOp& op, const std::vector<int64_t>& rowof, void** panel, int64_t pitch) {
+  auto convert = [&](const EnlOp& op, const std::vector<int64_t>& rowof, const std::vector<int64_t>& colof,
+                     void** panel, int64_t pitch) {
     std::vector<TcConv> tasks;
     for (size_t i = 0; i < op.subs.size(); ++i) {
       const EnlSub& s = op.subs[i];
+      if (rowof[i] < 0) continue;   // not used by any product
       check_range(s.ptr, s.rows, s.cols, s.cols, "tc convert source");
-      tasks.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], 0});
+      tasks.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], (int32_t)colof[i]});
     }
     if (tasks.empty()) return;
     TcConv* d = dalloc<TcConv>(tasks.size());
@@ -141,57 +215,83 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
     sync();
     dfree(d);
   };
-  convert(renl, rs_row, P->rs, P->rs_pitch);
-  convert(lenl, ls_row, P->ls, P->ls_pitch);
+  {
+    std::vector<int64_t> r0(renl.subs.size(), -1), c0(renl.subs.size(), 0);
+    for (const AGroup& g : groups) {
+      const int mso = ER.sdim[g.qout][g.so];
+      for (size_t bi = 0; bi < g.b.size(); ++bi)
+        for (int si = 0; si < 4; ++si) {
+          const int i = g.mem[bi][si];
+          if (i < 0) continue;
+          r0[i] = g.row0 + (int64_t)bi * mso;
+          c0[i] = g.col[si];
+        }
+    }
+    convert(renl, r0, c0, P->rs, P->rs_pitch);
+  }
+  convert(lenl, ls_row, std::vector<int64_t>(lenl.subs.size(), 0), P->ls, P->ls_pitch);
+  if (!rowmap.empty()) {
+    P->d_rowmap = dalloc<int64_t>(rowmap.size());
+    CK(cudaMemcpyAsync(P->d_rowmap, rowmap.data(), rowmap.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  }
   P->nsec = nq;
   P->d_sec = dalloc<TcPsiSector>(std::max(nq, 1));
   CK(cudaMemcpyAsync(P->d_sec, sec.data(), nq * sizeof(TcPsiSector), cudaMemcpyHostToDevice, stream));
-  // ---- stage A tiles: Y_b(Qin)[:, (so, q_r')] = sum psi(Qin)[:, (si, q_r)] Rsub^T
+  // ---- stage A tiles: Y^T rows (b, so part of E_R(qout)) x E_L(qin)
+  //      columns = sum over si  Rsub(b; si -> so) psi(qin)[:, si part]^T
   std::vector<TcTile> tiles;
   std::vector<TcTerm> terms;
-  for (auto& kv : rby) {
-    auto yb = ybase.find(kv.first);
-    if (yb == ybase.end()) continue;
-    const int qin = kv.first.second;
-    const int qout = renl.subs[kv.second[0]].qout;
-    for (int so = 0; so < 4; ++so) {
-      if (ER.soff[qout][so] < 0) continue;
-      const int N = ER.sdim[qout][so];
-      for (int m0 = 0; m0 < EL.dim[qin]; m0 += 128)
-        for (int n0 = 0; n0 < N; n0 += 256) {
-          TcTile T{};
-          T.t0 = (int)terms.size();
-          for (int i : kv.second) {
-            const EnlSub& s = renl.subs[i];
-            if (s.sout != so) continue;
-            terms.push_back({cpadR[qin][s.sin], (int32_t)psi_row[qin], (int32_t)(rs_row[i] + n0),
-                             (int32_t)up16(s.cols), 0, 0});
-            P->flops_alg += m0 == 0 && n0 == 0 ? 2.0 * EL.dim[qin] * N * s.cols : 0.0;
-          }
-          T.t1 = (int)terms.size();
-          T.m0 = m0;
-          T.m_valid = std::min(128, EL.dim[qin] - m0);
-          const int nv = std::min(256, N - n0);
-          T.n_mma = (int)up16(nv);
-          T.n_valid = nv;
-          T.bsel = bsel_for(T.n_mma);
-          T.mode = kTcYT;
-          T.beta = 0;
-          T.ld = (int32_t)P->yt_pitch;
-          T.out = yb->second + ER.soff[qout][so] + n0;
-          for (int s = 0; s < 4; ++s) {
-            T.rbreak[s] = EL.soff[qin][s] >= 0 ? EL.soff[qin][s] : INT_MAX;
-            T.rpad[s] = cpadL[qin][s];
-          }
-          for (int t = T.t0; t < T.t1; ++t) P->flops_exec += 2.0 * 128 * T.n_mma * terms[t].k;
-          tiles.push_back(T);
+  for (const AGroup& g : groups) {
+    const int mso = ER.sdim[g.qout][g.so];
+    const int64_t grows = (int64_t)g.b.size() * mso;
+    for (size_t bi = 0; bi < g.b.size(); ++bi)
+      for (int si = 0; si < 4; ++si)
+        if (g.mem[bi][si] >= 0) P->flops_alg += 2.0 * EL.dim[g.qin] * mso * ER.sdim[g.qin][si];
+    for (int64_t m0 = 0; m0 < grows; m0 += 128)
+      for (int n0 = 0; n0 < EL.dim[g.qin]; n0 += tune.ncap[0]) {
+        TcTile T{};
+        T.t0 = (int)terms.size();
+        for (int si = 0; si < 4; ++si)
+          if (g.mask >> si & 1)
+            terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)(psi_row[g.qin] + n0),
+                             (int32_t)up16(ER.sdim[g.qin][si]), 0, cpadR[g.qin][si]});
+        T.t1 = (int)terms.size();
+        T.m0 = (int32_t)m0;
+        T.m_valid = (int32_t)std::min<int64_t>(128, grows - m0);
+        const int nv = std::min(tune.ncap[0], EL.dim[g.qin] - n0);
+        T.n_mma = (int)up16(nv);
+        T.n_valid = nv;
+        T.bsel = bsel_for(T.n_mma);
+        T.mode = kTcYTmap;
+        T.beta = 0;
+        T.ld = (int32_t)P->yt_pitch;
+        T.out = g.row0 + m0;
+        T.n0 = n0;
+        for (int s = 0; s < 4; ++s) {
+          T.rbreak[s] = EL.soff[g.qin][s] >= 0 ? EL.soff[g.qin][s] : INT_MAX;
+          T.rpad[s] = cpadL[g.qin][s];
         }
-    }
+        for (int t = T.t0; t < T.t1; ++t) P->flops_exec += 2.0 * 128 * T.n_mma * terms[t].k;
+        tiles.push_back(T);
+      }
   }
   auto upload_tiles = [&](int which) {
     P->ntiles[which] = (int)tiles.size();
-    std::stable_sort(tiles.begin(), tiles.end(),
-                     [](const TcTile& a, const TcTile& b) { return (a.t1 - a.t0) > (b.t1 - b.t0); });
+    // most expensive first: the persistent CTAs stride over the list
+    std::vector<double> cost(tiles.size());
+    std::vector<int> order(tiles.size());
+    for (size_t i = 0; i < tiles.size(); ++i) {
+      double c = 0;
+      for (int t = tiles[i].t0; t < tiles[i].t1; ++t) c += terms[t].k;
+      cost[i] = c * tiles[i].n_mma + 4096.0;   // + per-tile fixed cost (epilogue)
+      order[i] = (int)i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    {
+      std::vector<TcTile> sorted(tiles.size());
+      for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
+      tiles.swap(sorted);
+    }
     P->d_tiles[which] = dalloc<TcTile>(std::max<size_t>(tiles.size(), 1));
     P->d_terms[which] = dalloc<TcTerm>(std::max<size_t>(terms.size(), 1));
     if (!tiles.empty())
@@ -212,7 +312,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
       const int N = EL.sdim[q][so];
       auto it = lout.find({q, so});
       for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
-        for (int n0 = 0; n0 < N; n0 += 256) {
+        for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
           TcTile T{};
           T.t0 = (int)terms.size();
           if (it != lout.end())
@@ -227,7 +327,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
           T.t1 = (int)terms.size();
           T.m0 = m0;
           T.m_valid = std::min(128, ER.dim[q] - m0);
-          const int nv = std::min(256, N - n0);
+          const int nv = std::min(tune.ncap[1], N - n0);
           T.n_mma = (int)up16(nv);
           T.n_valid = nv;
           T.bsel = bsel_for(T.n_mma);
@@ -239,14 +339,66 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
           tiles.push_back(T);
         }
     }
+  // ---- split K: a stage-B tile whose summed K exceeds kc becomes chunks of
+  //      whole terms (summed K <= kc) writing FP32 partial slots, summed in
+  //      FP64 by tc_reduce.  The chunks fill the SMs when sigma has few
+  //      output tiles, and they bound the length of every FP32 accumulation
+  //      in TMEM (its rounding error grows with that length).
+  {
+    // summed K x columns, independent of the N tiling (so that the tuned
+    // tile shape never changes the chunking, i.e. the arithmetic)
+    int64_t work = 0;
+    for (const TcTile& T : tiles)
+      for (int t = T.t0; t < T.t1; ++t) work += (int64_t)terms[t].k * T.n_valid;
+    int64_t kc = work / ((int64_t)4 * num_sms * 256);
+    kc = (kc + 63) / 64 * 64;
+    kc = std::max<int64_t>(256, std::min<int64_t>(prec == kTF32x3 ? 512 : 2048, kc));
+    P->kc = kc;
+    std::vector<TcTile> split;
+    std::vector<TcRed> red;
+    int64_t slot = 0, red_total = 0;
+    for (const TcTile& T : tiles) {
+      int64_t ktot = 0;
+      for (int t = T.t0; t < T.t1; ++t) ktot += terms[t].k;
+      if (ktot <= kc) {
+        split.push_back(T);
+        continue;
+      }
+      TcRed R{T.out, slot, red_total, T.ld, T.m0, T.m_valid, T.n_valid, T.n_mma, 0};
+      red_total += (int64_t)T.m_valid * T.n_valid;
+      int t = T.t0;
+      while (t < T.t1) {
+        TcTile Cc = T;
+        Cc.t0 = t;
+        int64_t k = 0;
+        while (t < T.t1 && (t == Cc.t0 || k + terms[t].k <= kc)) k += terms[t++].k;
+        Cc.t1 = t;
+        Cc.mode = kTcPart;
+        Cc.out = slot;
+        Cc.ld = 128;
+        slot += (int64_t)128 * T.n_mma;
+        R.nslot++;
+        split.push_back(Cc);
+      }
+      red.push_back(R);
+    }
+    tiles.swap(split);
+    P->nred = (int)red.size();
+    P->red_total = red_total;
+    if (!red.empty()) {
+      P->part = dalloc<float>((size_t)slot);
+      P->d_red = dalloc<TcRed>(red.size());
+      CK(cudaMemcpyAsync(P->d_red, red.data(), red.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
+    }
+  }
   upload_tiles(1);
   // ---- tensor maps
   std::memset(P->maps, 0, sizeof(P->maps));
   for (int h = 0; h < nh; ++h) {
-    bool ok = tc_encode_panel(&P->maps[0].a[h], P->eb, P->psi[h], P->psi_pitch, psi_rows, 128) &&
+    bool ok = tc_encode_panel(&P->maps[0].a[h], P->eb, P->rs[h], P->rs_pitch, rs_rows, 128) &&
               tc_encode_panel(&P->maps[1].a[h], P->eb, P->yt[h], P->yt_pitch, yrows, 128);
     for (int b = 0; b < 5 && ok; ++b)
-      ok = tc_encode_panel(&P->maps[0].b[h][b], P->eb, P->rs[h], P->rs_pitch, rs_rows, 16u << b) &&
+      ok = tc_encode_panel(&P->maps[0].b[h][b], P->eb, P->psi[h], P->psi_pitch, psi_rows, 16u << b) &&
            tc_encode_panel(&P->maps[1].b[h][b], P->eb, P->ls[h], P->ls_pitch, ls_rows, 16u << b);
     if (!ok) {
       tc_free(P);
@@ -259,6 +411,59 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec) {
   return P;
 }
 
+// Autotuner of the numerics-neutral tile shape: on the first plan of a
+// shape class (precision, size of the two-site state, number of Renl
+// sub-blocks), every N cap in {256, 128, 64} is built and its stage A and
+// stage B launches are timed separately on the current two-site state (one
+// untimed run, then the best of two); each stage keeps its fastest cap.
+TcPlan* Engine::tc_plan(const EnlOp& lenl, const EnlOp& renl, int prec) {
+  if (tc_fixed_cap) return tc_build(lenl, renl, prec, TcTune{{tc_fixed_cap, tc_fixed_cap}});
+  if (!autotune) return tc_build(lenl, renl, prec, TcTune());
+  auto lg = [](double x) { return (int64_t)std::lround(2.0 * std::log2(std::max(x, 1.0))); };
+  const int64_t key = ((int64_t)prec << 40) | (lg((double)psi_size) << 20) | lg((double)renl.subs.size());
+  auto it = tuned.find(key);
+  if (it != tuned.end()) return tc_build(lenl, renl, prec, it->second);
+  cudaEvent_t e[4];
+  for (auto& x : e) CK(cudaEventCreate(&x));
+  double* y = dalloc<double>(psi_size);
+  TcTune best;
+  float bt[2] = {1e30f, 1e30f};
+  for (int c : {256, 128, 64}) {
+    TcPlan* P = tc_build(lenl, renl, prec, TcTune{{c, c}});
+    for (int rep = 0; rep < 3; ++rep) {
+      launch_tc_convert_psi(psi, P->d_sec, P->nsec, psi_size, P->prec, P->psi[0], P->psi[1], P->psi_pitch, stream);
+      TcLaunch A{P->d_tiles[0], P->d_terms[0], P->ntiles[0], P->prec, P->yt[0], P->yt[1], nullptr, P->d_err,
+                 nullptr, P->d_rowmap, c, tc_stages(prec, c)};
+      TcLaunch B{P->d_tiles[1], P->d_terms[1], P->ntiles[1], P->prec, nullptr, nullptr, y, P->d_err, P->part,
+                 nullptr, c, tc_stages(prec, c)};
+      CK(cudaEventRecord(e[0], stream));
+      bool ok = launch_tc_gemm(P->maps[0], A, num_sms, stream);
+      CK(cudaEventRecord(e[1], stream));
+      ok = ok && launch_tc_gemm(P->maps[1], B, num_sms, stream);
+      launch_tc_reduce(P->d_red, P->nred, P->red_total, P->part, y, stream);
+      CK(cudaEventRecord(e[2], stream));
+      if (!ok) throw Error(-3, "invalid tensor-core launch configuration");
+      CK(cudaEventSynchronize(e[2]));
+      float ta = 0, tb = 0;
+      CK(cudaEventElapsedTime(&ta, e[0], e[1]));
+      CK(cudaEventElapsedTime(&tb, e[1], e[2]));
+      if (rep == 0) continue;
+      if (ta < bt[0]) { bt[0] = ta; best.ncap[0] = c; }
+      if (tb < bt[1]) { bt[1] = tb; best.ncap[1] = c; }
+    }
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    sync();
+    tc_free(P);
+    if (herr) throw Error(-5, "tensor-core pipeline wait timed out");
+    stats.autotune_trials++;
+  }
+  dfree(y);
+  for (auto& x : e) cudaEventDestroy(x);
+  tuned[key] = best;
+  return tc_build(lenl, renl, prec, best);
+}
+
 void Engine::tc_free(TcPlan* P) {
   if (!P) return;
   for (int h = 0; h < 2; ++h)
@@ -269,6 +474,12 @@ void Engine::tc_free(TcPlan* P) {
     if (P->d_terms[w]) dfree(P->d_terms[w]);
   }
   if (P->d_sec) dfree(P->d_sec);
+  if (P->part) dfree(P->part);
+  if (P->d_rowmap) dfree(P->d_rowmap);
+  if (P->xin) dfree(P->xin);
+  if (P->yout) dfree(P->yout);
+  Engine::drop(P->graph);
+  if (P->d_red) dfree(P->d_red);
   if (P->d_err) dfree(P->d_err);
   delete P;
 }
@@ -278,14 +489,31 @@ void Engine::tc_free(TcPlan* P) {
 void Engine::tc_apply(TcPlan* P, const double* x, double* y) {
   settle();
   CK(cudaEventRecord(ev0, stream));
-  launch_tc_convert_psi(x, P->d_sec, P->nsec, psi_size, P->prec, P->psi[0], P->psi[1], P->psi_pitch, stream);
-  TcLaunch A{P->d_tiles[0], P->d_terms[0], P->ntiles[0], P->prec, P->yt[0], P->yt[1], nullptr, P->d_err};
-  launch_tc_gemm(P->maps[0], A, num_sms, stream);
-  TcLaunch B{P->d_tiles[1], P->d_terms[1], P->ntiles[1], P->prec, nullptr, nullptr, y, P->d_err};
-  launch_tc_gemm(P->maps[1], B, num_sms, stream);
+  auto launches = [&](const double* xi, double* yo) {
+    launch_tc_convert_psi(xi, P->d_sec, P->nsec, psi_size, P->prec, P->psi[0], P->psi[1], P->psi_pitch, stream);
+    TcLaunch A{P->d_tiles[0], P->d_terms[0], P->ntiles[0], P->prec, P->yt[0], P->yt[1], nullptr, P->d_err,
+               nullptr, P->d_rowmap, P->tune.ncap[0], tc_stages(P->prec, P->tune.ncap[0])};
+    TcLaunch B{P->d_tiles[1], P->d_terms[1], P->ntiles[1], P->prec, nullptr, nullptr, yo, P->d_err, P->part,
+               nullptr, P->tune.ncap[1], tc_stages(P->prec, P->tune.ncap[1])};
+    if (!launch_tc_gemm(P->maps[0], A, num_sms, stream) || !launch_tc_gemm(P->maps[1], B, num_sms, stream))
+      throw Error(-3, "invalid tensor-core launch configuration");
+    launch_tc_reduce(P->d_red, P->nred, P->red_total, P->part, yo, stream);
+  };
+  if (use_graphs) {
+    // the graph reads and writes fixed buffers
+    if (!P->xin) {
+      P->xin = dalloc<double>(psi_size);
+      P->yout = dalloc<double>(psi_size);
+    }
+    CK(cudaMemcpyAsync(P->xin, x, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    replay(P->graph, [&]() { launches(P->xin, P->yout); });
+    CK(cudaMemcpyAsync(y, P->yout, psi_size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  } else {
+    launches(x, y);
+  }
   CK(cudaEventRecord(ev1, stream));
   CK(cudaMemcpyAsync(tc_err_host, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
-  stats.launches += 3;
+  stats.launches += P->nred ? 4 : 3;
   CK(cudaGetLastError());
   sigma_pending = 2;
   stats.sigma_flops += P->flops_alg;

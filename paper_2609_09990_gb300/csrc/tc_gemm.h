@@ -13,7 +13,12 @@
 //   kTcYT    : C^T into a panel (BF16, TF32, or TF32 hi/lo), row j of the
 //              output is panel row out + j, output column = the padded
 //              position of tile row m0 + i (rmap: 4 breaks + 4 pads),
-//   kTcSigma : C^T into FP64, out[j * ld + m0 + i] (= or +=).
+//   kTcYTmap : C into a panel: row i goes to panel row rowmap[out + i],
+//              column j to the padded position of n0 + j (same rmap),
+//   kTcSigma : C^T into FP64, out[j * ld + m0 + i] (= or +=),
+//   kTcPart  : C^T into an FP32 partial slot, part[out + j * 128 + i]; the
+//              partial slots of one output tile (split K) are summed in FP64
+//              by tc_reduce in a fixed order.
 #pragma once
 
 #include <cstdint>
@@ -24,14 +29,14 @@
 namespace gbd {
 
 enum TcPrec { kBF16 = 0, kTF32 = 1, kTF32x3 = 2 };
-enum TcMode { kTcYT = 0, kTcSigma = 1 };
+enum TcMode { kTcYT = 0, kTcSigma = 1, kTcPart = 2, kTcYTmap = 3 };
 
 struct TcTerm {
   int32_t ax, ay;   // A box origin: column (K) and row (before adding the tile's m0)
-  int32_t by;       // B sub-block first row (K starts at column 0)
+  int32_t by;       // B sub-block first row
   int32_t k;        // K, a multiple of the MMA K step (16 BF16, 8 TF32)
   int32_t neg;      // 1: subtract the product
-  int32_t pad;
+  int32_t bx;       // B box first column (K origin)
 };
 
 struct TcTile {
@@ -40,8 +45,10 @@ struct TcTile {
   int32_t n_mma, n_valid;
   int32_t bsel;          // B box height index: 16 << bsel rows
   int32_t mode, beta, ld;
-  int64_t out;           // output element offset (panel row for kTcYT)
+  int64_t out;           // output element offset (panel row for kTcYT, row-map index for kTcYTmap)
   int32_t rbreak[4], rpad[4];
+  int32_t n0;            // kTcYTmap: position of the tile's first B row
+  int32_t unused;
 };
 
 struct TcMaps {
@@ -58,7 +65,24 @@ struct TcLaunch {
   void* yt_lo;           // TF32x3 low part
   double* f64;           // kTcSigma output
   int* err;              // device flag: 1 = a bounded wait ran out
+  float* part;           // kTcPart output slots
+  const int64_t* rowmap; // kTcYTmap output rows
+  int ncap;              // largest n_mma of the launch's tiles: 64, 128 or 256
+  int stages;            // = tc_stages(prec, ncap)
 };
+// shared-memory pipeline depth for B boxes of at most ncap rows
+int tc_stages(int prec, int ncap);
+
+// out[j * ld + m0 + i] = sum over the nslot consecutive partial slots
+// starting at float offset slot0 (slot s at slot0 + s * 128 * n_stride)
+// (e0: first element of the task in the flattened list of all tasks'
+// m_valid x n_valid elements; total = sum of those counts)
+struct TcRed {
+  int64_t out, slot0, e0;
+  int32_t ld, m0, m_valid, n_valid, n_stride, nslot;
+};
+void launch_tc_reduce(const TcRed* tasks, int ntasks, int64_t total, const float* part, double* out,
+                      cudaStream_t s);
 
 constexpr int kTcKChunk16 = 64;   // BF16 elements per 128-byte TMA box row
 constexpr int kTcKChunk32 = 32;   // TF32 elements per 128-byte TMA box row
@@ -66,7 +90,8 @@ constexpr int kTcKChunk32 = 32;   // TF32 elements per 128-byte TMA box row
 // encode the tensor maps of one panel (pitch in elements)
 bool tc_encode_panel(CUtensorMap* m, int prec_elem_bytes, const void* base, uint64_t pitch, uint64_t rows,
                      uint32_t box_rows);
-void launch_tc_gemm(const TcMaps& maps, const TcLaunch& L, int num_sms, cudaStream_t s);
+// false (nothing launched) when ncap/stages are not a valid pair
+bool launch_tc_gemm(const TcMaps& maps, const TcLaunch& L, int num_sms, cudaStream_t s);
 
 // conversion of FP64 blocks into panels: rows x cols block at src (ld_src)
 // written at panel row r0, column c0 (pitch); lo != nullptr for TF32x3

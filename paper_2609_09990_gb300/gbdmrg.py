@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbdmrg.so")
 
 GBD_OK = 0
+GBD_ERR_ARG, GBD_ERR_OOM, GBD_ERR_CUDA, GBD_ERR_NOCONV, GBD_ERR_TIMEOUT, GBD_ERR_STATE = -1, -2, -3, -4, -5, -6
 GBD_FP64, GBD_TF32, GBD_BF16 = 0, 1, 2
 GBD_PRECOND_DIAG, GBD_PRECOND_LEARNED = 0, 1
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_OOM", -3: "GBD_ERR_CUDA", -4: "GBD_ERR_NOCONV",
@@ -48,10 +49,14 @@ class gbd_stats(C.Structure):
                 ("n_steps", C.c_int64), ("kernel_launches", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("max_discarded_weight", C.c_double),
                 ("sigma_flops_exec", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
-                ("n_sigma_tc", C.c_int64)]
+                ("n_sigma_tc", C.c_int64), ("tier_iterations", C.c_int64 * 3),
+                ("max_final_residual", C.c_double), ("sum_final_residual", C.c_double),
+                ("graph_launches", C.c_int64), ("autotune_trials", C.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["tier_iterations"] = list(d["tier_iterations"])
+        return d
 
 
 _lib = None
@@ -72,6 +77,12 @@ def lib():
         "gbd_last_error": (C.c_char_p, [vp]),
         "gbd_solve": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), C.POINTER(gbd_result)]),
         "gbd_setup": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule)]),
+        "gbd_solve_batched": (C.c_int, [vp, C.c_int32, C.POINTER(gbd_problem), C.POINTER(gbd_schedule),
+                                        C.POINTER(gbd_result)]),
+        "gbd_set_batch_workers": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_graphs": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
+        "gbd_probe_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
         "gbd_init_state": (C.c_int, [vp]),
         "gbd_set_precision": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "gbd_run_sweep": (C.c_int, [vp, C.c_int32, _dp]),
@@ -87,6 +98,7 @@ def lib():
         "gbd_mpo_labels": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, _ip]),
         "gbd_env_block": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_int64, _ip, _ip]),
         "gbd_get_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
+        "gbd_get_batch_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
         "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32]),
         "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
@@ -141,6 +153,9 @@ class Context:
             raise GbdError(f"gbd_create failed: {ERRORS.get(rc, rc)}")
         self._keep = []
 
+    def last_error(self):
+        return self.L.gbd_last_error(self.ptr).decode(errors="replace")
+
     def close(self):
         if self.ptr:
             self.L.gbd_destroy(self.ptr)
@@ -181,6 +196,34 @@ class Context:
         self._check(self.L.gbd_solve(self.ptr, C.byref(p), C.byref(s), C.byref(res)), "gbd_solve")
         return dict(energy=res.energy, sweep_energies=se, rdm1=r1, rdm2=r2,
                     max_discarded_weight=res.max_discarded_weight, n_matvec=res.n_matvec)
+
+    def solve_batched(self, problems, rdms=False, workers=0, check=True):
+        """gbd_solve_batched over a list of (h, chol, n_elec, two_sz, bond_dims, tols, kwargs); returns
+        (return code, list of result dicts with their own status)."""
+        n = len(problems)
+        ps = (gbd_problem * max(n, 1))()
+        ss = (gbd_schedule * max(n, 1))()
+        rs = (gbd_result * max(n, 1))()
+        keep, outs = [], []
+        for i, (h, chol, ne, sz, bd, tl, kw) in enumerate(problems):
+            p, s = self._structs(h, chol, ne, sz, bd, tl, **kw)
+            keep.append(self._keep)
+            ps[i] = p
+            ss[i] = s
+            no = p.n_orb
+            se = np.zeros(len(bd))
+            r1 = np.zeros((no, no)) if rdms else None
+            r2 = np.zeros((no, no, no, no)) if rdms else None
+            outs.append((se, r1, r2))
+            rs[i] = gbd_result(0.0, _d(se), _d(r1), _d(r2), 0.0, 0, 0)
+        self._check(self.L.gbd_set_batch_workers(self.ptr, workers), "gbd_set_batch_workers")
+        rc = self.L.gbd_solve_batched(self.ptr, n, ps, ss, rs)
+        if check:
+            self._check(rc, "gbd_solve_batched")
+        res = [dict(energy=rs[i].energy, sweep_energies=outs[i][0], rdm1=outs[i][1], rdm2=outs[i][2],
+                    max_discarded_weight=rs[i].max_discarded_weight, n_matvec=rs[i].n_matvec,
+                    status=rs[i].status) for i in range(n)]
+        return rc, res
 
     def setup(self, h, chol, n_elec, two_sz, bond_dims, tols, **kw):
         p, s = self._structs(h, chol, n_elec, two_sz, bond_dims, tols, **kw)
@@ -233,6 +276,19 @@ class Context:
         y = np.zeros_like(x)
         self._check(self.L.gbd_apply_heff_prec(self.ptr, k, prec, _d(x), _d(y)), "gbd_apply_heff_prec")
         return y
+
+    def set_tc_tile(self, ncap):
+        self._check(self.L.gbd_set_tc_tile(self.ptr, ncap), "gbd_set_tc_tile")
+
+    def set_graphs(self, enable):
+        self._check(self.L.gbd_set_graphs(self.ptr, 1 if enable else 0), "gbd_set_graphs")
+
+    def probe_step(self, k, precision, fp64_refine, tol):
+        """(Ritz value, FP64 Rayleigh quotient, FP64 residual) of one Davidson solve at centre k."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.L.gbd_probe_step(self.ptr, k, precision, fp64_refine, tol, C.byref(a), C.byref(b),
+                                          C.byref(c)), "gbd_probe_step")
+        return a.value, b.value, c.value
 
     def run_step(self, k, direction, M, tol):
         e, tau, nk = C.c_double(), C.c_double(), C.c_int32()
@@ -322,6 +378,11 @@ class Context:
     def stats(self):
         s = gbd_stats()
         self.L.gbd_get_stats(self.ptr, C.byref(s))
+        return s.as_dict()
+
+    def batch_stats(self):
+        s = gbd_stats()
+        self.L.gbd_get_batch_stats(self.ptr, C.byref(s))
         return s.as_dict()
 
 

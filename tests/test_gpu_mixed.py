@@ -61,3 +61,58 @@ def test_mixed_solve_cas6_reaches_fci(G, precision):
     st = ctx.stats()
     assert st["n_sigma_tc"] > 0
     ctx.close()
+
+
+def test_tile_shape_does_not_change_sigma(G):
+    # the autotuned N cap only regroups columns: the same products are summed
+    # in the same order, so sigma is bit-identical for every cap
+    h, chol = make_integrals(10, 12, 21)
+    ctx = G.Context(0)
+    ctx.setup(h, chol, 10, 0, [64], [1e-8], seed=21)
+    ctx.init_state()
+    for k in range(3):
+        ctx.run_step(k, 0, 64, 1e-6)
+    x = np.random.default_rng(5).standard_normal(ctx.two_site_size(3))
+    for prec in (2, 3):
+        ys = []
+        for cap in (256, 128, 64):
+            ctx.set_tc_tile(cap)
+            ys.append(ctx.apply_heff_prec(3, x, prec))
+        assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2]), prec
+    ctx.close()
+
+
+def test_graphs_and_autotune_do_not_change_the_solve(G):
+    h, chol = make_integrals(8, 10, 22)
+    out = []
+    for graphs, cap in ((True, 0), (False, 64)):
+        ctx = G.Context(0)
+        ctx.set_graphs(graphs)
+        ctx.set_tc_tile(cap)
+        r = ctx.solve(h, chol, 8, 0, [48] * 3, [1e-7] * 3, seed=22, precision=2, fp64_refine=0)
+        st = ctx.stats()
+        assert (st["graph_launches"] > 0) == graphs
+        assert (st["autotune_trials"] > 0) == (cap == 0)
+        out.append(r)
+        ctx.close()
+    assert np.array_equal(out[0]["sweep_energies"], out[1]["sweep_energies"])
+    assert out[0]["energy"] == out[1]["energy"]
+
+
+def test_probe_step_isolates_matvec_precision(G):
+    # same input state: FP64 Davidson and mixed Davidson refined in FP64 reach
+    # the same Rayleigh quotient; the mixed solve alone stays within its floor
+    h, chol = make_integrals(10, 12, 23)
+    ctx = G.Context(0)
+    ctx.setup(h, chol, 10, 0, [96], [1e-8], seed=23)
+    ctx.init_state()
+    for k in range(4):
+        ctx.run_step(k, 0, 96, 1e-7)
+    th, e_ref, r_ref = ctx.probe_step(4, 0, 0, 1e-9)
+    assert r_ref < 1e-8 and abs(th - e_ref) < 1e-12
+    _, e_mix, r_mix = ctx.probe_step(4, 2, 50, 1e-9)
+    assert r_mix < 1e-8 and abs(e_mix - e_ref) < 1e-11
+    _, e_lo, r_lo = ctx.probe_step(4, 2, 0, 1e-9)
+    assert e_lo >= e_ref - 1e-12           # Rayleigh quotient: variational
+    assert e_lo - e_ref < 1e-6
+    ctx.close()
