@@ -132,10 +132,14 @@ def run_ours(args, rank, world):
     clocks = clk.stop()
     st1 = ctx.stats()
     dt = t1 - t0
-    keys = ["sigma_ms", "tc_ms", "env_ms", "enlarge_ms", "davidson_ms", "truncate_ms", "step_ms"]
+    keys = ["sigma_ms", "tc_ms", "tc_gemm_ms", "tc_build_ms", "env_ms", "enlarge_ms", "davidson_ms", "truncate_ms",
+            "step_ms"]
     breakdown = {k: (st1[k] - st0[k]) / args.steps for k in keys}
     breakdown["sigma_builds"] = (st1["n_sigma"] - st0["n_sigma"]) / args.steps
     breakdown["tc_sigma_builds"] = (st1["n_sigma_tc"] - st0["n_sigma_tc"]) / args.steps
+    breakdown["tc_build_phase_ms"] = {
+        nm: (st1["tc_build_phase_ms"][i] - st0["tc_build_phase_ms"][i]) / args.steps
+        for i, nm in enumerate(["layout_groups", "panels", "tiles", "upload", "maps"])}
     breakdown["davidson_iterations_by_tier"] = {
         t: (st1["tier_iterations"][i] - st0["tier_iterations"][i]) / args.steps
         for i, t in enumerate(["bf16_or_tf32", "tf32x3", "fp64"])}
@@ -154,6 +158,18 @@ def run_ours(args, rank, world):
         e64 = ctx.run_sweep(nsw)
         torch.cuda.synchronize()
         fp64 = dict(sweep_s=time.perf_counter() - t4, sweep_energy=e64, final_energy=ctx.final_energy())
+    # per-step effect of the matvec precision: at a few bonds of a further
+    # left-to-right pass, the FP64 Rayleigh quotient of the mixed-precision
+    # Davidson solution against the FP64 Davidson solution on the same input
+    probes = []
+    if prec != 0 and args.probes > 0:
+        ks = [int(round(1 + i * (n - 4) / max(args.probes - 1, 1))) for i in range(args.probes)]
+        for k in range(max(ks) + 1):
+            if k in ks:
+                _, e_ref, r_ref = ctx.probe_step(k, 0, 0, 1e-9)
+                _, e_mix, r_mix = ctx.probe_step(k, prec, args.refine, args.tol)
+                probes.append({"bond": k, "dE": e_mix - e_ref, "r_fp64_solve": r_ref, "r_mixed_solve": r_mix})
+            ctx.run_step(k, 0, M, args.tol)
     ctx.close()
     # end to end through gbd_solve: host integrals in, energies out
     e2e = None
@@ -168,20 +184,25 @@ def run_ours(args, rank, world):
         ctx.close()
         e2e = dict(flops=se["sigma_flops"], time=t3 - t2, h2d=int(h.nbytes + chol.nbytes),
                    d2h=int(8 * (1 + args.steps)), energy=r["energy"])
+    tc = {k: [b - a for a, b in zip(st0[k], st1[k])] for k in ("tc_flops_by_type", "tc_gemm_ms_by_type")}
+    tc["tc_bytes"] = st1["tc_bytes"] - st0["tc_bytes"]
+    tc["tc_gemm_ms"] = st1["tc_gemm_ms"] - st0["tc_gemm_ms"]
     return dict(time=dt, flops=flops, sigma_ms=sig_ms, launches=launches, clocks=clocks,
                 energies=energies, e2e=e2e, n=n, M=M, st=st1, tc_ms=tc_ms, tc_flops=tc_flops,
-                e_final=e_final, fp64=fp64, breakdown=breakdown)
+                e_final=e_final, fp64=fp64, breakdown=breakdown, tc=tc, probes=probes)
 
 
 def batched_problems(args, rank):
     """64 independent active spaces: orbital counts U{8..14} and M from
-    {128, 256, 512} (seed-1000 stream), half filling, S_z = 0, integrals of
+    {128, 256, 512} (seed-1000 stream), half filling, S_z = 0 (1/2 for odd
+    electron counts), integrals of
     problem s from seed s with 3 n Cholesky vectors; `sweeps` sweeps each."""
     from gbd_synth import batched_problem_sizes
     out = []
     for s, (n, M) in enumerate(batched_problem_sizes(64)):
         h, chol = make_integrals(n, 3 * n, s + 64 * rank)
-        out.append((h, chol, n, 0, [M] * args.batch_sweeps, [args.tol] * args.batch_sweeps,
+        # half filling; odd electron counts take S_z = 1/2
+        out.append((h, chol, n, n % 2, [M] * args.batch_sweeps, [args.tol] * args.batch_sweeps,
                     {"seed": s, "precision": PREC[args.precision], "fp64_refine": args.refine}))
     return out
 
@@ -282,12 +303,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--precision", default="bf16", choices=list(PREC))
     ap.add_argument("--workload", default="cas16_m512")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--refine", type=int, default=2, help="FP64 Davidson iterations after the tensor-core tiers")
+    ap.add_argument("--refine", type=int, default=0, help="FP64 Davidson iterations after the tensor-core tiers")
+    ap.add_argument("--probes", type=int, default=3, help="bonds probed for the per-step energy error vs FP64")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--batch-sweeps", type=int, default=2, help="sweeps per problem (batched64)")
     ap.add_argument("--workers", type=int, default=0, help="host worker threads (batched64; 0 = auto)")
@@ -322,7 +344,7 @@ def main():
                 "ms_per_step": 1000 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": "batched64: 64 active spaces, n_orb U{8..14}, M in {128,256,512}, "
-                                       f"half filling, {args.batch_sweeps} sweeps each; one step = one batched call",
+                                       f"half filling (S_z = 0, or 1/2 when odd), {args.batch_sweeps} sweeps each; one step = one batched call",
                            "workers": args.workers, "graphs": not args.no_graphs,
                            "l2": "per-problem state re-created every step (> L2 in total)"},
                 "problems_per_s": res["n_problems"] * world * args.steps / tmax,
@@ -372,15 +394,37 @@ def main():
         peak, bound, punit, kind = 152 * 2 * 2 * 2.07e9 / 1e12, "alu", "TFLOP/s", "derived (FP64 unit count x max clock)"
         kname, achieved = "gemm_f64_kernel (sigma stages A+B)", kern_tflops
     else:
-        # tensor-core sigma builds of every tier (BF16/TF32 single pass and
-        # TF32x3), algorithmic flops over their device time, against the
-        # measured sustained BF16 peak
-        peak, bound, punit, kind = pk["bf16_tflops_sustained"], "tensor", "TFLOP/s", pk_kind + " (bf16 sustained)"
-        kname = "tc_gemm_kernel (tcgen05; sigma stages A+B, all tiers)"
-        achieved = res["tc_flops"] / (res["tc_ms"] / 1000) / 1e12 if res["tc_ms"] > 0 else 0.0
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak,
+        # tc_gemm_kernel (stage A + stage B launches, CUDA events around them
+        # on the engine stream).  Tensor view: algorithmic flops per operand
+        # type against that type's peak (BF16: measured sustained; TF32:
+        # x 1.1/2.25, the nominal ratio; TF32x3: three TF32 passes), i.e. the
+        # time the flops need at peak over the time they took.  HBM view:
+        # algorithmic bytes (enlarged operators once, Y^T written and read
+        # once, psi and sigma) over the same time.  The larger fraction binds.
+        tc = res["tc"]
+        pb = pk["bf16_tflops_sustained"]
+        tpk = [pb, pb * 1.1 / 2.25, pb * 1.1 / 2.25 / 3]
+        gms = tc["tc_gemm_ms"]
+        at_peak = sum(f / (p * 1e12) for f, p in zip(tc["tc_flops_by_type"], tpk))
+        tfrac = at_peak / (gms / 1000) if gms > 0 else 0.0
+        tflops = sum(tc["tc_flops_by_type"]) / (gms / 1000) / 1e12 if gms > 0 else 0.0
+        gbs = tc["tc_bytes"] / (gms / 1000) / 1e9 if gms > 0 else 0.0
+        hfrac = gbs / pk["hbm_gbs"]
+        kname = "tc_gemm_kernel (tcgen05 + TMA; sigma stages A and B, all tiers)"
+        tview = {"bound": "tensor", "achieved": tflops, "peak": tfrac and tflops / tfrac, "unit": "TFLOP/s",
+                 "frac": tfrac, "peak_kind": pk_kind + " bf16 sustained x type ratio (time-weighted over tiers)"}
+        hview = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hfrac,
+                 "peak_kind": pk_kind + " copy bandwidth"}
+        main_v, alt_v = (hview, tview) if hfrac >= tfrac else (tview, hview)
+        peak, bound, punit, kind, achieved = main_v["peak"], main_v["bound"], main_v["unit"], main_v["peak_kind"], \
+            main_v["achieved"]
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak if peak else 0.0,
             "traffic": None, "kernel": kname, "peak_kind": kind}
-    line = {"metric": "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512", "value": flops / tmax / 1e12,
+    if args.precision != "fp64":
+        roof["other_view"] = alt_v
+        roof["tc_gemm_ms_per_sweep"] = res["tc"]["tc_gemm_ms"] / args.steps
+        roof["launches_per_sweep"] = res["breakdown"]["tc_sigma_builds"] * 2
+    line = {"metric": "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u22641e-6 Ha", "value": flops / tmax / 1e12,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic", "config": config,
@@ -389,6 +433,11 @@ def main():
             "per_sweep": res["breakdown"], "roofline": roof,
             "clocks": res["clocks"],
             "gpu_launches": int(res["launches"])}
+    if res["probes"]:
+        line["per_step_energy_error_vs_fp64"] = {
+            "max_abs_dE_Ha": max(abs(p["dE"]) for p in res["probes"]), "probes": res["probes"],
+            "how": "same input state: FP64 Rayleigh quotient of the mixed-precision Davidson solution minus that "
+                   "of an FP64 Davidson solution (residual 1e-9)"}
     if res["fp64"]:
         line["fp64_gpu_sweep_s"] = res["fp64"]["sweep_s"]
         line["speedup_vs_fp64_sweep"] = res["fp64"]["sweep_s"] / (tmax / args.steps)

@@ -40,6 +40,12 @@ typedef struct {
   double sum_final_residual;    /* sum of those over the steps */
   int64_t graph_launches;       /* sigma builds replayed from a captured CUDA graph */
   int64_t autotune_trials;      /* tensor-core plans built and timed by the tile-shape autotuner */
+  double tc_gemm_ms;            /* device time of the tc_gemm_kernel launches alone (CUDA events) */
+  double tc_bytes;              /* algorithmic HBM bytes of the tensor-core sigma builds */
+  double tc_flops_by_type[3];   /* algorithmic flops of those builds with BF16, TF32, TF32x3 operands */
+  double tc_gemm_ms_by_type[3]; /* tc_gemm_kernel device time of those builds */
+  double tc_build_ms;           /* host wall time building tensor-core plans, autotuning included */
+  double tc_build_phase_ms[5];  /* of which: layouts and groups, panels, tile lists, upload, tensor maps */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or
@@ -50,6 +56,10 @@ int gbd_set_graphs(gbd_ctx *ctx, int32_t enable);
  * class; 64, 128 or 256 = that largest N tile for both stages.  The shape
  * never changes the arithmetic (same products, same summation order). */
 int gbd_set_tc_tile(gbd_ctx *ctx, int32_t ncap);
+
+/* Preconditioner of the following Davidson solves (GBD_PRECOND_DIAG or
+ * GBD_PRECOND_LEARNED; the latter needs weights in the context). */
+int gbd_set_preconditioner(gbd_ctx *ctx, int32_t preconditioner);
 
 /* One Davidson solve at the current centre k (environments k and k+2
  * valid, as after gbd_init_state for k = 0 or after steps up to k-1) in
@@ -142,14 +152,15 @@ int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32
 int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t nterms, uint64_t seed,
                     double *max_err, double *max_ref);
 /* Preconditioner network pieces for gradient checks: install FP32 weights
- * (kept FP16 on the device for inference); loss and gradient over n feature
- * rows X [n*8] with targets y and weights w (FP32 device arithmetic, FP64
- * reduction; params [1281] = W1 (128x8), b1, w2, b2); the fused
- * preconditioner t = -r/(d-theta)(1+g) on host vectors (iteration counter
+ * (kept FP16 on the device for inference); loss sum w (g-y)^2 / sum w +
+ * lam mean(g^2) and its gradient over n feature rows X [n*8] with targets y
+ * and weights w (FP32 device arithmetic, FP64 reduction; params [1281] =
+ * W1 (128x8), b1, w2, b2); the fused preconditioner
+ * t = -r/(d-theta)(1+clip(g,-0.9,4)) on host vectors (iteration counter
  * `iter` enters the features). */
 int gbd_set_precond_weights(gbd_ctx *ctx, const float *params);
 int gbd_mlp_loss_grad(gbd_ctx *ctx, const float *X, const float *y, const float *w, int64_t n, const float *params,
-                      double *loss, double *grad);
+                      double lam, double *loss, double *grad);
 int gbd_mlp_precond(gbd_ctx *ctx, const double *r, const double *d, double theta, double iter, int64_t n, double *t);
 /* Davidson iteration count and learned-preconditioner fallbacks so far. */
 int gbd_davidson_counts(gbd_ctx *ctx, int64_t *iterations, int64_t *fallbacks, int64_t *samples);

@@ -7,14 +7,18 @@ requires that the preconditioner never changes the converged energies (Sec.
 The learned member is not in the paper; its reading (stated once, used by
 both the CUDA kernels and this reference):
 
-  correction  t_i = -r_i / (d_i - theta) * (1 + g_i)       (d = H_eff diagonal)
+  correction  t_i = -r_i / (d_i - theta) * (1 + clip(g_i, -0.9, 4))   (d = H_eff diagonal;
+              the clip is the range of the targets, so an input unlike the
+              training data cannot blow a component up)
   network     g_i = w2 . relu(W1 f_i + b1) + b2, W1: 128 x F, one hidden
               layer of width 128 ("2-layer": two weight layers)
   features    f_i = [ (d_i - theta) / s,  r_i / |r|,  |r_i| / |r|,
                       log(|d_i - theta| + 1e-12),  log |r|,  it / 32,
                       sign(d_i - theta),  1 ]            (F = 8)
               with s = the RMS of (d - theta) over the vector
-  loss        L = sum_i w_i (g_i - y_i)^2 / sum_i w_i, with the target
+  loss        L = sum_i w_i (g_i - y_i)^2 / sum_i w_i + lam * mean_i g_i^2
+              (the second term is a prior towards g = 0, the Jacobi step,
+              for elements the weighted data say little about), with the target
               y_i = clip(a e_i / tj_i - 1, -0.9, 4) and weight
               w_i = tj_i^2 / (1 + (a e_i / tj_i - 1)^2) where tj = -r/(d-theta)
               is the Jacobi step, e the component of (converged vector -
@@ -85,11 +89,12 @@ class MLP:
         h = np.maximum(z, 0.0)
         return h @ self.w2 + self.b2, z, h
 
-    def loss_and_grad(self, f, y, w):
+    def loss_and_grad(self, f, y, w, lam=0.0):
         g, z, h = self.forward(f)
         W = float(np.sum(w))
-        dg = 2.0 * w * (g - y) / W
-        loss = float(np.sum(w * (g - y) ** 2) / W)
+        n = g.size
+        dg = 2.0 * w * (g - y) / W + 2.0 * lam * g / n
+        loss = float(np.sum(w * (g - y) ** 2) / W + lam * np.sum(g * g) / n)
         gw2 = h.T @ dg
         gb2 = float(np.sum(dg))
         dh = np.outer(dg, self.w2) * (z > 0)
@@ -100,7 +105,7 @@ class MLP:
 
 
 def precondition(r, d, theta, it, net: MLP):
-    """t = jacobi step * (1 + g)."""
+    """t = jacobi step * (1 + clip(g, -0.9, 4))."""
     tj = jacobi_step(r, d, theta)
     g, _, _ = net.forward(features(r, d, theta, it))
-    return tj * (1.0 + g)
+    return tj * (1.0 + np.clip(g, -0.9, 4.0))

@@ -285,6 +285,18 @@ int gbd_set_tc_tile(gbd_ctx* ctx, int32_t ncap) {
   });
 }
 
+int gbd_set_preconditioner(gbd_ctx* ctx, int32_t preconditioner) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    if (preconditioner != GBD_PRECOND_DIAG && preconditioner != GBD_PRECOND_LEARNED)
+      return fail(ctx, GBD_ERR_ARG, "unknown preconditioner");
+    if (preconditioner == GBD_PRECOND_LEARNED && !ctx->eng->mlp_loaded)
+      return fail(ctx, GBD_ERR_STATE, "no preconditioner weights loaded");
+    ctx->eng->sched.precond = preconditioner;
+    return GBD_OK;
+  });
+}
+
 int gbd_probe_step(gbd_ctx* ctx, int32_t k, int32_t precision, int32_t fp64_refine, double tol, double* theta,
                    double* e64, double* r64) {
   return guarded(ctx, [&]() {
@@ -518,11 +530,12 @@ int gbd_set_precond_weights(gbd_ctx* ctx, const float* params) {
 }
 
 int gbd_mlp_loss_grad(gbd_ctx* ctx, const float* X, const float* y, const float* w, int64_t n, const float* params,
-                      double* loss, double* grad) {
+                      double lam, double* loss, double* grad) {
   return guarded(ctx, [&]() {
-    if (!X || !y || !w || !params || !loss || !grad || n < 1) return fail(ctx, GBD_ERR_ARG, "bad arguments");
+    if (!X || !y || !w || !params || !loss || !grad || n < 1 || !(lam >= 0))
+      return fail(ctx, GBD_ERR_ARG, "bad arguments");
     if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
-    ctx->eng->mlp_loss_grad(X, y, w, n, params, loss, grad);
+    ctx->eng->mlp_loss_grad(X, y, w, n, params, lam, loss, grad);
     return GBD_OK;
   });
 }
@@ -571,6 +584,14 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->sum_final_residual = t.sum_final_residual;
   s->graph_launches = t.graph_launches;
   s->autotune_trials = t.autotune_trials;
+  s->tc_gemm_ms = t.tc_gemm_ms;
+  s->tc_bytes = t.tc_bytes;
+  s->tc_build_ms = t.tc_build_ms;
+  for (int i = 0; i < 5; ++i) s->tc_build_phase_ms[i] = t.tcb_ms[i];
+  for (int i = 0; i < 3; ++i) {
+    s->tc_flops_by_type[i] = t.tc_flops_p[i];
+    s->tc_gemm_ms_by_type[i] = t.tc_gemm_ms_p[i];
+  }
 }
 
 int gbd_get_stats(const gbd_ctx* ctx, gbd_stats* s) {

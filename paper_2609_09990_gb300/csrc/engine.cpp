@@ -35,6 +35,10 @@
 
 namespace gbd {
 
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 void Bond::finalize() {
   std::vector<int> ord(na.size());
   std::iota(ord.begin(), ord.end(), 0);
@@ -66,10 +70,6 @@ double binom(int n, int k) {
   double r = 1;
   for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
   return std::round(r);
-}
-
-double now_ms() {
-  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 void parallel_for(int n, const std::function<void(int)>& f) {
@@ -207,6 +207,8 @@ Engine::Engine(int dev) : device(dev) {
   CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
+  CK(cudaEventCreate(&evg0));
+  CK(cudaEventCreate(&evg1));
   CK(cudaMallocHost(&tc_err_host, sizeof(int)));
   *tc_err_host = 0;
   cudaMemPool_t pool;
@@ -225,6 +227,8 @@ Engine::~Engine() {
   cudaStreamSynchronize(stream);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (evg0) cudaEventDestroy(evg0);
+  if (evg1) cudaEventDestroy(evg1);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -1145,6 +1149,10 @@ void Engine::settle() {
   stats.sigma_ms += ms;
   if (sigma_pending == 2) {
     stats.tc_ms += ms;
+    float g = 0;
+    CK(cudaEventElapsedTime(&g, evg0, evg1));
+    stats.tc_gemm_ms += g;
+    stats.tc_gemm_ms_p[stats.last_tc_prec] += g;
     if (*tc_err_host) throw Error(-5, "tensor-core sigma: a bounded device wait ran out");
   }
   sigma_pending = 0;

@@ -86,6 +86,11 @@ struct Stats {
   int64_t tier_iters[3] = {0, 0, 0};
   double max_final_residual = 0, sum_final_residual = 0;   // over Davidson solves
   int64_t graph_launches = 0, autotune_trials = 0;
+  double tc_gemm_ms = 0, tc_bytes = 0;   // tc_gemm_kernel launches only; algorithmic bytes of the TC sigma builds
+  double tc_flops_p[3] = {0, 0, 0}, tc_gemm_ms_p[3] = {0, 0, 0};   // by operand type (BF16, TF32, TF32x3)
+  int last_tc_prec = 0;
+  double tc_build_ms = 0;   // host wall time building tensor-core plans (incl. autotuning)
+  double tcb_ms[5] = {0, 0, 0, 0, 0};   // plan-build phases: layout/groups, panels, tiles, upload, maps
   void add(const Stats& o) {   // sum of the additive counters (batched solves)
     sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
     enl_ms += o.enl_ms; step_ms += o.step_ms; trunc_ms += o.trunc_ms; davidson_ms += o.davidson_ms;
@@ -96,6 +101,9 @@ struct Stats {
     max_final_residual = std::max(max_final_residual, o.max_final_residual);
     sum_final_residual += o.sum_final_residual;
     graph_launches += o.graph_launches; autotune_trials += o.autotune_trials;
+    tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms;
+    for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
+    for (int i = 0; i < 3; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
     max_discarded = std::max(max_discarded, o.max_discarded);
   }   // Davidson iterations: low-precision tier, TF32x3 tier, FP64
   double max_discarded = 0;
@@ -110,6 +118,7 @@ struct Schedule {
 };
 
 struct TcPlan;
+double now_ms();   // steady-clock wall time
 
 struct TcTune {     // numerics-neutral tile shape of the tensor-core sigma
   int ncap[2] = {256, 256};   // largest N tile of stage A and of stage B (64, 128, 256)
@@ -146,7 +155,8 @@ class Engine {
   void record_converged(const double* x_dev);
   double train_precond(int epochs, double lr, uint64_t seed);
   void set_precond_weights(const float* params);
-  void mlp_loss_grad(const float* X, const float* y, const float* w, int64_t n, const float* params, double* loss,
+  void mlp_loss_grad(const float* X, const float* y, const float* w, int64_t n, const float* params, double lam,
+                     double* loss,
                      double* grad);
   void mlp_apply(const double* r, const double* d, double theta, double iter, int64_t n, double* t);
   void save_precond(const char* path) const;
@@ -170,6 +180,7 @@ class Engine {
   int device;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evg0 = nullptr, evg1 = nullptr;   // around the tensor-core GEMM launches of one sigma
   std::vector<double> h, eri;
   Mpo mpo;
   std::vector<Bond> bonds;
@@ -237,6 +248,7 @@ class Engine {
   void free_sigma(Sigma& sg, bool planned);
   TcPlan* tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune tune = TcTune());
   TcPlan* tc_plan(const EnlOp& lenl, const EnlOp& renl, int prec);   // tc_build with the tuned shape
+  TcPlan* tc_plan_impl(const EnlOp& lenl, const EnlOp& renl, int prec);
   std::map<int64_t, TcTune> tuned;
   void tc_apply(TcPlan* p, const double* x, double* y);
   void tc_free(TcPlan* p);

@@ -1,6 +1,6 @@
 // Learned Davidson preconditioner: a pointwise two-layer MLP (F = 8 features
 // -> 128 ReLU units -> 1) that rescales the Jacobi step element by element,
-//   t_i = -r_i / (d_i - theta) * (1 + g_i).
+//   t_i = -r_i / (d_i - theta) * (1 + clip(g_i, -0.9, 4)).
 // FP16 weights, FP32 arithmetic.  Inference is fused with the feature
 // computation and the preconditioner; training uses per-block partial
 // gradients (deterministic), an FP64 reduction and Adam.
@@ -76,7 +76,7 @@ __global__ void precond_kernel(const double* __restrict__ r, const double* __res
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float f[kF];
     feat(r[i], d[i], s, f);
-    const float g = net(w, f);
+    const float g = fminf(fmaxf(net(w, f), -0.9f), 4.f);   // the range of the training targets
     double den = d[i] - s.theta;
     if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
     const double v = -r[i] / den * (1.0 + (double)g);
@@ -99,11 +99,13 @@ __global__ void features_kernel(const double* __restrict__ r, const double* __re
     feat(r[i], d[i], s, X + i * kF);
 }
 
-// loss = sum w (g - y)^2 / W ; per-block partial gradients
+// loss = sum w (g - y)^2 / W + lam_n sum g^2 (lam_n = lam / n: a prior
+// towards g = 0, the Jacobi step); per-block partial gradients
 // partial layout per block: [W1 (H*F) | b1 (H) | w2 (H) | b2 | loss]
 constexpr int kTile = 256;
 __global__ void grad_kernel(const float* __restrict__ X, const float* __restrict__ y, const float* __restrict__ wt,
-                            int64_t n, double inv_W, const float* __restrict__ p, double* __restrict__ partial) {
+                            int64_t n, double inv_W, double lam_n, const float* __restrict__ p,
+                            double* __restrict__ partial) {
   __shared__ Weights w;
   __shared__ float xs[kTile][kF];
   __shared__ float dg[kTile];
@@ -120,8 +122,8 @@ __global__ void grad_kernel(const float* __restrict__ X, const float* __restrict
       for (int q = 0; q < kF; ++q) xs[threadIdx.x][q] = X[e * kF + q];
       const float g = net(w, xs[threadIdx.x]);
       const float diff = g - y[e];
-      dg[threadIdx.x] = (float)(2.0 * inv_W) * wt[e] * diff;
-      aloss += wt[e] * diff * diff;
+      dg[threadIdx.x] = (float)(2.0 * inv_W) * wt[e] * diff + (float)(2.0 * lam_n) * g;
+      aloss += (float)inv_W * wt[e] * diff * diff + (float)lam_n * g * g;
     } else {
       dg[threadIdx.x] = 0.f;
 #pragma unroll
@@ -165,7 +167,7 @@ __global__ void grad_kernel(const float* __restrict__ X, const float* __restrict
   }
   if (threadIdx.x == 0) {
     out[kMlpParams - 1] = adg;
-    out[kMlpParams] = red[0] * inv_W;
+    out[kMlpParams] = red[0];
   }
 }
 
@@ -224,9 +226,9 @@ int mlp_grad_blocks(int64_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-void launch_mlp_grad(const float* X, const float* y, const float* w, int64_t n, double inv_W, const float* p,
-                     double* partial, int nblk, double* grad_and_loss, cudaStream_t st) {
-  grad_kernel<<<nblk, kTile, 0, st>>>(X, y, w, n, inv_W, p, partial);
+void launch_mlp_grad(const float* X, const float* y, const float* w, int64_t n, double inv_W, double lam,
+                     const float* p, double* partial, int nblk, double* grad_and_loss, cudaStream_t st) {
+  grad_kernel<<<nblk, kTile, 0, st>>>(X, y, w, n, inv_W, n > 0 ? lam / (double)n : 0.0, p, partial);
   reduce_partials<<<(kMlpParams + 256) / 256, 256, 0, st>>>(partial, nblk, grad_and_loss);
 }
 

@@ -167,23 +167,31 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     int stage = 0;
     uint32_t ph = 0;
     bool ok = true;
+    // descriptors are software-pipelined: the next tile's and the next
+    // term's loads are in flight while the current ones are issued
+    TcTile Tn;
+    if (blockIdx.x < L.ntiles) Tn = L.tiles[blockIdx.x];
     for (int tile = blockIdx.x; tile < L.ntiles && ok; tile += gridDim.x) {
-      const TcTile T = L.tiles[tile];
+      const TcTile T = Tn;
+      if (tile + (int)gridDim.x < L.ntiles) Tn = L.tiles[tile + gridDim.x];
       const int bbytes = (16 << T.bsel) * 128;
       const uint32_t tx = (uint32_t)(kStageA + bbytes) * (x3 ? 2 : 1);
+      TcTerm tmn;
+      if (T.t1 > T.t0) tmn = L.terms[T.t0];
       for (int t = T.t0; t < T.t1 && ok; ++t) {
-        const TcTerm tm = L.terms[t];
+        const TcTerm tm = tmn;
+        if (t + 1 < T.t1) tmn = L.terms[t + 1];
         for (int k0 = 0; k0 < tm.k; k0 += kc) {
           if (!mbar_wait(&empty[stage], ph ^ 1, L.err)) { ok = false; break; }
           uint8_t* sa = base + stage * stage_bytes;
           uint8_t* sb = sa + kStageA;
           mbar_expect_tx(&full[stage], tx);
           tma_load_2d(sa, &maps.a[0], tm.ax + k0, tm.ay + T.m0, &full[stage]);
-          tma_load_2d(sb, &maps.b[0][T.bsel], tm.bx + k0, tm.by, &full[stage]);
+          tma_load_2d(sb, &maps.b[0][T.bsel], tm.bx + k0, tm.by + T.n0, &full[stage]);
           if (x3) {
             uint8_t* sa2 = sb + bstage;
             tma_load_2d(sa2, &maps.a[1], tm.ax + k0, tm.ay + T.m0, &full[stage]);
-            tma_load_2d(sa2 + kStageA, &maps.b[1][T.bsel], tm.bx + k0, tm.by, &full[stage]);
+            tma_load_2d(sa2 + kStageA, &maps.b[1][T.bsel], tm.bx + k0, tm.by + T.n0, &full[stage]);
           }
           if (++stage == stages) { stage = 0; ph ^= 1; }
         }
@@ -203,8 +211,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     int acc_i = 0;
     bool ok = true;
     const uint32_t fmt = bf ? 1u : 2u;
+    TcTile Tn;
+    if (blockIdx.x < L.ntiles) Tn = L.tiles[blockIdx.x];
     for (int tile = blockIdx.x; tile < L.ntiles && ok; tile += gridDim.x, ++acc_i) {
-      const TcTile T = L.tiles[tile];
+      const TcTile T = Tn;
+      if (tile + (int)gridDim.x < L.ntiles) Tn = L.tiles[tile + gridDim.x];
+      TcTerm tmn;
+      if (T.t1 > T.t0) tmn = L.terms[T.t0];
       const int a = acc_i & 1;
       const uint32_t aph = (acc_i >> 1) & 1;
       if (!mbar_wait(&tempty[a], aph ^ 1, L.err)) { ok = false; break; }
@@ -212,7 +225,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint32_t dt = tmem + (uint32_t)(a * 256);
       uint32_t first = 1;
       for (int t = T.t0; t < T.t1 && ok; ++t) {
-        const TcTerm tm = L.terms[t];
+        const TcTerm tm = tmn;
+        if (t + 1 < T.t1) tmn = L.terms[t + 1];
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tm.neg & 1) << 13) |
                                ((uint32_t)(T.n_mma >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
         for (int k0 = 0; k0 < tm.k; k0 += kc) {
@@ -247,11 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     const int row = q * 32 + lane;       // accumulator row (A row within the tile)
     int acc_i = 0;
     for (int tile = blockIdx.x; tile < L.ntiles; tile += gridDim.x, ++acc_i) {
+      // descriptor and output row are loaded before the accumulator wait
       const TcTile T = L.tiles[tile];
-      const int a = acc_i & 1;
-      const uint32_t aph = (acc_i >> 1) & 1;
-      if (!mbar_wait(&tfull[a], aph, L.err)) break;
-      tc_fence_after();
       const bool has = T.t1 > T.t0;
       const bool live = row < T.m_valid;
       int pcol = 0;
@@ -262,8 +273,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (r >= T.rbreak[u]) s = u;
         pcol = T.rpad[s] + (r - T.rbreak[s]);
       } else if (T.mode == kTcYTmap && live) {
-        prow = L.rowmap[T.out + row];
+        prow = L.rowmap[T.out + row] * (int64_t)T.ld + T.n0;
       }
+      const int a = acc_i & 1;
+      const uint32_t aph = (acc_i >> 1) & 1;
+      if (!mbar_wait(&tfull[a], aph, L.err)) break;
+      tc_fence_after();
       for (int c0 = 0; c0 < T.n_mma; c0 += 16) {
         float v[16];
         if (has) {
@@ -273,6 +288,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
         if (!live) continue;
+        if (T.mode == kTcYTmap) {
+          // 16 contiguous, 16-element aligned output columns
+          const int64_t idx = prow + c0;
+          if (bf) {
+            uint32_t w[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+              w[i] = *reinterpret_cast<uint32_t*>(&p2);
+            }
+            uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(L.yt_hi) + idx);
+            d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+          } else {
+            float h[16], l[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              h[i] = to_tf32(v[i]);
+              l[i] = to_tf32(v[i] - h[i]);
+            }
+            float4* dh = reinterpret_cast<float4*>(reinterpret_cast<float*>(L.yt_hi) + idx);
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) dh[q4] = make_float4(h[4 * q4], h[4 * q4 + 1], h[4 * q4 + 2], h[4 * q4 + 3]);
+            if (x3) {
+              float4* dl = reinterpret_cast<float4*>(reinterpret_cast<float*>(L.yt_lo) + idx);
+#pragma unroll
+              for (int q4 = 0; q4 < 4; ++q4)
+                dl[q4] = make_float4(l[4 * q4], l[4 * q4 + 1], l[4 * q4 + 2], l[4 * q4 + 3]);
+            }
+          }
+          continue;
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int j = c0 + i;
@@ -283,16 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           } else if (T.mode == kTcPart) {
             L.part[T.out + (int64_t)j * 128 + row] = v[i];
           } else {
-            int64_t idx;
-            if (T.mode == kTcYTmap) {
-              const int p = T.n0 + j;
-              int s = 0;
-              for (int u = 1; u < 4; ++u)
-                if (p >= T.rbreak[u]) s = u;
-              idx = prow * T.ld + T.rpad[s] + (p - T.rbreak[s]);
-            } else {
-              idx = (T.out + j) * (int64_t)T.ld + pcol;
-            }
+            const int64_t idx = (T.out + j) * (int64_t)T.ld + pcol;
             if (bf) {
               reinterpret_cast<__nv_bfloat16*>(L.yt_hi)[idx] = __float2bfloat16_rn(v[i]);
             } else {
@@ -374,12 +412,15 @@ __global__ void tc_convert_psi_kernel(const double* __restrict__ psi, const TcPs
       if (sec[mid].src_off <= e) lo_i = mid; else hi_i = mid - 1;
     }
     const TcPsiSector S = sec[lo_i];
-    const int64_t r = (e - S.src_off) / S.cols;
+    const int r = (int)((e - S.src_off) / S.cols);
     const int c = (int)((e - S.src_off) % S.cols);
-    int s = 0;
-    for (int u = 1; u < 4; ++u)
+    int s = 0, t = 0;
+    for (int u = 1; u < 4; ++u) {
       if (c >= S.cbreak[u]) s = u;
-    store_conv(psi[e], prec, hi, lo, (int64_t)(S.r0 + r) * pitch + S.cpad[s] + (c - S.cbreak[s]));
+      if (r >= S.rbreak[u]) t = u;
+    }
+    const int64_t prow = S.r0 + S.rpad[t] + (r - S.rbreak[t]);
+    store_conv(psi[e], prec, hi, lo, prow * pitch + S.cpad[s] + (c - S.cbreak[s]));
   }
 }
 

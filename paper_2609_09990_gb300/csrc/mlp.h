@@ -26,8 +26,11 @@ void launch_mlp_features(const double* r, const double* d, const MlpScalars& s, 
 void launch_mlp_forward(const float* X, int64_t n, const float* p, float* g, cudaStream_t st);
 int mlp_grad_blocks(int64_t n);
 // grad_and_loss: kMlpParams gradient entries then the loss
-void launch_mlp_grad(const float* X, const float* y, const float* w, int64_t n, double inv_W, const float* p,
-                     double* partial, int nblk, double* grad_and_loss, cudaStream_t st);
+// loss = sum w (g - y)^2 / W + lam mean(g^2)
+void launch_mlp_grad(const float* X, const float* y, const float* w, int64_t n, double inv_W, double lam,
+                     const float* p, double* partial, int nblk, double* grad_and_loss, cudaStream_t st);
+// strength of the prior towards the Jacobi step used in training
+constexpr double kMlpPrior = 0.5;
 void launch_mlp_adam(float* p, float* m, float* v, const double* grad, float lr, int step, void* p16,
                      cudaStream_t st);
 void launch_mlp_to_half(const float* p, void* p16, cudaStream_t st);

@@ -135,12 +135,12 @@ double Engine::train_precond(int epochs, double lr, uint64_t seed) {
   double* partial = dalloc<double>((size_t)nblk * (kMlpParams + 1));
   double* grad = dalloc<double>(kMlpParams + 1);
   for (int ep = 1; ep <= epochs; ++ep) {
-    launch_mlp_grad(X, y, w, n, 1.0 / W, p, partial, nblk, grad, stream);
+    launch_mlp_grad(X, y, w, n, 1.0 / W, kMlpPrior, p, partial, nblk, grad, stream);
     launch_mlp_adam(p, m, v, grad, (float)lr, ep, mlp_w16, stream);
     stats.launches += 3;
   }
   double loss = 0;
-  launch_mlp_grad(X, y, w, n, 1.0 / W, p, partial, nblk, grad, stream);
+  launch_mlp_grad(X, y, w, n, 1.0 / W, kMlpPrior, p, partial, nblk, grad, stream);
   CK(cudaMemcpyAsync(&loss, grad + kMlpParams, sizeof(double), cudaMemcpyDeviceToHost, stream));
   mlp_f32.resize(kMlpParams);
   CK(cudaMemcpyAsync(mlp_f32.data(), p, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, stream));
@@ -163,7 +163,7 @@ void Engine::set_precond_weights(const float* params) {
 }
 
 void Engine::mlp_loss_grad(const float* X, const float* y, const float* w, int64_t n, const float* params,
-                           double* loss, double* grad) {
+                           double lam, double* loss, double* grad) {
   double W = 0;
   for (int64_t i = 0; i < n; ++i) W += w[i];
   float* dX = dalloc<float>((size_t)n * kMlpF);
@@ -177,7 +177,7 @@ void Engine::mlp_loss_grad(const float* X, const float* y, const float* w, int64
   const int nblk = mlp_grad_blocks(n);
   double* partial = dalloc<double>((size_t)nblk * (kMlpParams + 1));
   double* out = dalloc<double>(kMlpParams + 1);
-  launch_mlp_grad(dX, dy, dw, n, 1.0 / W, dp, partial, nblk, out, stream);
+  launch_mlp_grad(dX, dy, dw, n, 1.0 / W, lam, dp, partial, nblk, out, stream);
   stats.launches += 2;
   std::vector<double> h(kMlpParams + 1);
   CK(cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));

@@ -44,6 +44,9 @@ struct TcPlan {
   int64_t kc = 0;                // split-K chunk length (summed K of whole terms)
   int* d_err = nullptr;
   double flops_alg = 0, flops_exec = 0;
+  // algorithmic HBM bytes of one sigma: the Renl and Lenl sub-blocks once,
+  // Y^T written once and read once, psi read and sigma written in FP64
+  double bytes_alg = 0;
 };
 
 namespace {
@@ -63,14 +66,20 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   P->eb = prec == kBF16 ? 2 : 4;
   const int nh = prec == kTF32x3 ? 2 : 1;
   const int nq = EL.n();
+  double tph = now_ms();
+  auto phase = [&](int i) {
+    const double t = now_ms();
+    stats.tcb_ms[i] += t - tph;
+    tph = t;
+  };
   // ---- psi panel: rows E_L(Q) stacked, columns E_R(Q) with padded sub-ranges
   std::vector<int64_t> psi_row(nq);
   std::vector<std::array<int, 4>> cpadR(nq), cpadL(nq);
   int64_t rows = 0, wmax = 0, wlmax = 0;
   std::vector<TcPsiSector> sec(nq);
+  std::vector<int> wlq(nq);   // padded width of E_L(q)
   for (int q = 0; q < nq; ++q) {
     psi_row[q] = rows;
-    rows += EL.dim[q];
     int64_t w = 0, wl = 0;
     for (int s = 0; s < 4; ++s) {
       cpadR[q][s] = (int)w;
@@ -78,6 +87,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       cpadL[q][s] = (int)wl;
       if (EL.soff[q][s] >= 0) wl += up16(EL.sdim[q][s]);
     }
+    wlq[q] = (int)wl;
+    rows += wl;   // psi rows in padded E_L positions (zero rows in the padding)
     wmax = std::max(wmax, w);
     wlmax = std::max(wlmax, wl);
     TcPsiSector& S = sec[q];
@@ -88,6 +99,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     for (int s = 0; s < 4; ++s) {
       S.cbreak[s] = ER.soff[q][s] >= 0 ? ER.soff[q][s] : INT_MAX;
       S.cpad[s] = cpadR[q][s];
+      S.rbreak[s] = EL.soff[q][s] >= 0 ? EL.soff[q][s] : INT_MAX;
+      S.rpad[s] = cpadL[q][s];
     }
   }
   P->psi_pitch = up64(wmax);
@@ -106,21 +119,28 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   };
   std::vector<int64_t> ls_row;
   const int64_t ls_rows = std::max<int64_t>(sub_panel(lenl, ls_row, P->ls_pitch), 256);
-  // ---- Y blocks (b, Qin) -> rows E_R(Qout) of the Y^T panel
-  std::map<std::pair<int, int>, std::vector<int>> rby, lout;
-  std::map<std::pair<int, int>, int> lhas;
-  for (size_t i = 0; i < renl.subs.size(); ++i) rby[{renl.subs[i].b, renl.subs[i].qin}].push_back((int)i);
-  for (size_t i = 0; i < lenl.subs.size(); ++i) {
-    lhas[{lenl.subs[i].b, lenl.subs[i].qin}] = 1;
-    lout[{lenl.subs[i].qout, lenl.subs[i].sout}].push_back((int)i);
+  // ---- Y blocks (b, Qin) -> rows E_R(Qout) of the Y^T panel.  Keys are
+  //      small dense integers: flat tables indexed by b * nq + qin.
+  int nb = 0;
+  for (const EnlSub& s : renl.subs) nb = std::max(nb, s.b + 1);
+  for (const EnlSub& s : lenl.subs) nb = std::max(nb, s.b + 1);
+  std::vector<int> rfirst((size_t)nb * nq, -1);   // first Renl sub of (b, qin)
+  std::vector<char> lhas((size_t)nb * nq, 0);
+  std::vector<std::vector<int>> lout((size_t)nq * 4);   // Lenl subs by (qout, sout)
+  for (size_t i = 0; i < renl.subs.size(); ++i) {
+    int& f = rfirst[(size_t)renl.subs[i].b * nq + renl.subs[i].qin];
+    if (f < 0) f = (int)i;
   }
-  std::map<std::pair<int, int>, int64_t> ybase;
+  for (size_t i = 0; i < lenl.subs.size(); ++i) {
+    lhas[(size_t)lenl.subs[i].b * nq + lenl.subs[i].qin] = 1;
+    lout[(size_t)lenl.subs[i].qout * 4 + lenl.subs[i].sout].push_back((int)i);
+  }
+  std::vector<int64_t> ybase((size_t)nb * nq, -1);
   int64_t yrows = 0;
-  for (auto& kv : rby) {
-    if (!lhas.count(kv.first)) continue;
-    int qout = renl.subs[kv.second[0]].qout;
-    ybase[kv.first] = yrows;
-    yrows += ER.dim[qout];
+  for (size_t bq = 0; bq < ybase.size(); ++bq) {
+    if (rfirst[bq] < 0 || !lhas[bq]) continue;
+    ybase[bq] = yrows;
+    yrows += ER.dim[renl.subs[rfirst[bq]].qout];
   }
   P->yt_pitch = up64(wlmax);
   yrows = std::max<int64_t>(yrows, 128);
@@ -139,33 +159,34 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   std::vector<int64_t> rowmap;
   int64_t rs_rows = 0, rs_width = 0;
   {
-    std::map<std::tuple<int, int, int>, std::array<int, 4>> bso;   // (b, qin, so) -> subs per si
+    // (b, qin, so) -> subs per si
+    std::vector<std::array<int, 4>> bso((size_t)nb * nq * 4, std::array<int, 4>{-1, -1, -1, -1});
     for (size_t i = 0; i < renl.subs.size(); ++i) {
       const EnlSub& s = renl.subs[i];
-      if (!ybase.count({s.b, s.qin})) continue;
-      auto it = bso.find({s.b, s.qin, s.sout});
-      if (it == bso.end()) it = bso.emplace(std::make_tuple(s.b, s.qin, s.sout), std::array<int, 4>{-1, -1, -1, -1}).first;
-      if (it->second[s.sin] >= 0) throw Error(-3, "duplicate enlarged-operator sub-block");
-      it->second[s.sin] = (int)i;
+      if (ybase[(size_t)s.b * nq + s.qin] < 0) continue;
+      int& slot = bso[((size_t)s.b * nq + s.qin) * 4 + s.sout][s.sin];
+      if (slot >= 0) throw Error(-3, "duplicate enlarged-operator sub-block");
+      slot = (int)i;
     }
-    std::map<std::tuple<int, int, int, int>, int> gidx;
-    for (auto& kv : bso) {
-      const int b = std::get<0>(kv.first), qin = std::get<1>(kv.first), so = std::get<2>(kv.first);
+    std::vector<int> gidx((size_t)nq * nq * 4 * 16, -1);   // (qin, qout, so, mask) -> group
+    for (size_t key = 0; key < bso.size(); ++key) {
+      const std::array<int, 4>& m = bso[key];
       int mask = 0, any = -1;
       for (int si = 0; si < 4; ++si)
-        if (kv.second[si] >= 0) {
+        if (m[si] >= 0) {
           mask |= 1 << si;
-          any = kv.second[si];
+          any = m[si];
         }
+      if (!mask) continue;
+      const int so = (int)(key % 4), qin = (int)((key / 4) % nq), b = (int)(key / 4 / nq);
       const int qout = renl.subs[any].qout;
-      auto key = std::make_tuple(qin, qout, so, mask);
-      auto g = gidx.find(key);
-      if (g == gidx.end()) {
-        g = gidx.emplace(key, (int)groups.size()).first;
+      int& g = gidx[(((size_t)qin * nq + qout) * 4 + so) * 16 + mask];
+      if (g < 0) {
+        g = (int)groups.size();
         groups.push_back(AGroup{qin, qout, so, mask, {}, {}, 0, {}});
       }
-      groups[g->second].mem.push_back(kv.second);
-      groups[g->second].b.push_back(b);
+      groups[g].mem.push_back(m);
+      groups[g].b.push_back(b);
     }
     for (AGroup& g : groups) {
       const int mso = ER.sdim[g.qout][g.so];
@@ -177,7 +198,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       }
       rs_width = std::max(rs_width, w);
       for (size_t bi = 0; bi < g.b.size(); ++bi) {
-        const int64_t y0 = ybase[{g.b[bi], g.qin}] + ER.soff[g.qout][g.so];
+        const int64_t y0 = ybase[(size_t)g.b[bi] * nq + g.qin] + ER.soff[g.qout][g.so];
         for (int r = 0; r < mso; ++r) rowmap.push_back(y0 + r);
       }
       rs_rows += (int64_t)g.b.size() * mso;
@@ -185,6 +206,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   }
   P->rs_pitch = up64(rs_width);
   rs_rows = std::max<int64_t>(rs_rows, 128);
+  phase(0);   // host: layouts, groups, row map
   // ---- allocate and zero the panels
   for (int h = 0; h < nh; ++h) {
     P->psi[h] = dalloc<uint8_t>((size_t)(psi_rows * P->psi_pitch * P->eb));
@@ -237,6 +259,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   P->nsec = nq;
   P->d_sec = dalloc<TcPsiSector>(std::max(nq, 1));
   CK(cudaMemcpyAsync(P->d_sec, sec.data(), nq * sizeof(TcPsiSector), cudaMemcpyHostToDevice, stream));
+  phase(1);   // panels allocated, zeroed and converted
   // ---- stage A tiles: Y^T rows (b, so part of E_R(qout)) x E_L(qin)
   //      columns = sum over si  Rsub(b; si -> so) psi(qin)[:, si part]^T
   std::vector<TcTile> tiles;
@@ -246,19 +269,26 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     const int64_t grows = (int64_t)g.b.size() * mso;
     for (size_t bi = 0; bi < g.b.size(); ++bi)
       for (int si = 0; si < 4; ++si)
-        if (g.mem[bi][si] >= 0) P->flops_alg += 2.0 * EL.dim[g.qin] * mso * ER.sdim[g.qin][si];
+        if (g.mem[bi][si] >= 0) {
+          P->flops_alg += 2.0 * EL.dim[g.qin] * mso * ER.sdim[g.qin][si];
+          P->bytes_alg += (double)P->eb * nh * mso * ER.sdim[g.qin][si];           // Renl sub-block
+        }
+    P->bytes_alg += 2.0 * P->eb * nh * grows * EL.dim[g.qin];                     // Y^T write + read
+    // one term list per group, shared by its tiles
+    const int gt0 = (int)terms.size();
+    for (int si = 0; si < 4; ++si)
+      if (g.mask >> si & 1)
+        terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)psi_row[g.qin], (int32_t)up16(ER.sdim[g.qin][si]),
+                         0, cpadR[g.qin][si]});
+    const int gt1 = (int)terms.size();
     for (int64_t m0 = 0; m0 < grows; m0 += 128)
-      for (int n0 = 0; n0 < EL.dim[g.qin]; n0 += tune.ncap[0]) {
+      for (int n0 = 0; n0 < wlq[g.qin]; n0 += tune.ncap[0]) {
         TcTile T{};
-        T.t0 = (int)terms.size();
-        for (int si = 0; si < 4; ++si)
-          if (g.mask >> si & 1)
-            terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)(psi_row[g.qin] + n0),
-                             (int32_t)up16(ER.sdim[g.qin][si]), 0, cpadR[g.qin][si]});
-        T.t1 = (int)terms.size();
+        T.t0 = gt0;
+        T.t1 = gt1;
         T.m0 = (int32_t)m0;
         T.m_valid = (int32_t)std::min<int64_t>(128, grows - m0);
-        const int nv = std::min(tune.ncap[0], EL.dim[g.qin] - n0);
+        const int nv = std::min(tune.ncap[0], wlq[g.qin] - n0);   // a multiple of 16
         T.n_mma = (int)up16(nv);
         T.n_valid = nv;
         T.bsel = bsel_for(T.n_mma);
@@ -267,10 +297,6 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         T.ld = (int32_t)P->yt_pitch;
         T.out = g.row0 + m0;
         T.n0 = n0;
-        for (int s = 0; s < 4; ++s) {
-          T.rbreak[s] = EL.soff[g.qin][s] >= 0 ? EL.soff[g.qin][s] : INT_MAX;
-          T.rpad[s] = cpadL[g.qin][s];
-        }
         for (int t = T.t0; t < T.t1; ++t) P->flops_exec += 2.0 * 128 * T.n_mma * terms[t].k;
         tiles.push_back(T);
       }
@@ -304,27 +330,34 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     tiles.clear();
     terms.clear();
   };
+  phase(2);   // host: stage A tiles
   upload_tiles(0);
+  phase(3);   // upload
   // ---- stage B tiles: sigma(Qout)[rows (q_l', so), E_R tile] = sum Y^T Lsub^T
   for (int q = 0; q < nq; ++q)
     for (int so = 0; so < 4; ++so) {
       if (EL.soff[q][so] < 0) continue;
       const int N = EL.sdim[q][so];
-      auto it = lout.find({q, so});
+      const std::vector<int>& lo = lout[(size_t)q * 4 + so];
+      // one term list per output block (q, so), shared by its tiles
+      const int ot0 = (int)terms.size();
+      for (int i : lo) {
+        const EnlSub& s = lenl.subs[i];
+        const int64_t yb = ybase[(size_t)s.b * nq + s.qin];
+        if (yb < 0) continue;
+        terms.push_back({cpadL[s.qin][s.sin], (int32_t)yb, (int32_t)ls_row[i], (int32_t)up16(s.cols), 0, 0});
+        P->flops_alg += 2.0 * ER.dim[q] * N * s.cols;
+        P->bytes_alg += (double)P->eb * nh * N * s.cols;                          // Lenl sub-block
+      }
+      const int ot1 = (int)terms.size();
+      int64_t ksum = 0;
+      for (int t = ot0; t < ot1; ++t) ksum += terms[t].k;
       for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
         for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
           TcTile T{};
-          T.t0 = (int)terms.size();
-          if (it != lout.end())
-            for (int i : it->second) {
-              const EnlSub& s = lenl.subs[i];
-              auto yb = ybase.find({s.b, s.qin});
-              if (yb == ybase.end()) continue;
-              terms.push_back({cpadL[s.qin][s.sin], (int32_t)yb->second, (int32_t)(ls_row[i] + n0),
-                               (int32_t)up16(s.cols), 0, 0});
-              P->flops_alg += m0 == 0 && n0 == 0 ? 2.0 * ER.dim[q] * N * s.cols : 0.0;
-            }
-          T.t1 = (int)terms.size();
+          T.t0 = ot0;
+          T.t1 = ot1;
+          T.n0 = n0;
           T.m0 = m0;
           T.m_valid = std::min(128, ER.dim[q] - m0);
           const int nv = std::min(tune.ncap[1], N - n0);
@@ -335,7 +368,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           T.beta = 0;
           T.ld = ER.dim[q];
           T.out = psi_off[q] + (int64_t)(EL.soff[q][so] + n0) * ER.dim[q];
-          for (int t = T.t0; t < T.t1; ++t) P->flops_exec += 2.0 * 128 * T.n_mma * terms[t].k;
+          P->flops_exec += 2.0 * 128 * T.n_mma * (double)ksum;
           tiles.push_back(T);
         }
     }
@@ -391,7 +424,10 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       CK(cudaMemcpyAsync(P->d_red, red.data(), red.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
     }
   }
+  phase(2);   // host: stage B tiles and split K
   upload_tiles(1);
+  phase(3);
+  P->bytes_alg += 2.0 * 8.0 * psi_size;                                          // psi in, sigma out
   // ---- tensor maps
   std::memset(P->maps, 0, sizeof(P->maps));
   for (int h = 0; h < nh; ++h) {
@@ -405,6 +441,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       throw Error(-3, "tensor map encoding failed");
     }
   }
+  phase(4);   // tensor maps
   P->d_err = dalloc<int>(1);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), stream));
   sync();
@@ -417,6 +454,13 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
 // stage B launches are timed separately on the current two-site state (one
 // untimed run, then the best of two); each stage keeps its fastest cap.
 TcPlan* Engine::tc_plan(const EnlOp& lenl, const EnlOp& renl, int prec) {
+  const double t0 = now_ms();
+  TcPlan* P = tc_plan_impl(lenl, renl, prec);
+  stats.tc_build_ms += now_ms() - t0;
+  return P;
+}
+
+TcPlan* Engine::tc_plan_impl(const EnlOp& lenl, const EnlOp& renl, int prec) {
   if (tc_fixed_cap) return tc_build(lenl, renl, prec, TcTune{{tc_fixed_cap, tc_fixed_cap}});
   if (!autotune) return tc_build(lenl, renl, prec, TcTune());
   auto lg = [](double x) { return (int64_t)std::lround(2.0 * std::log2(std::max(x, 1.0))); };
@@ -491,12 +535,19 @@ void Engine::tc_apply(TcPlan* P, const double* x, double* y) {
   CK(cudaEventRecord(ev0, stream));
   auto launches = [&](const double* xi, double* yo) {
     launch_tc_convert_psi(xi, P->d_sec, P->nsec, psi_size, P->prec, P->psi[0], P->psi[1], P->psi_pitch, stream);
+    // external event nodes when captured (they time every replay), plain
+    // records otherwise
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(stream, &cs));
+    const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaEventRecordWithFlags(evg0, stream, evf));
     TcLaunch A{P->d_tiles[0], P->d_terms[0], P->ntiles[0], P->prec, P->yt[0], P->yt[1], nullptr, P->d_err,
                nullptr, P->d_rowmap, P->tune.ncap[0], tc_stages(P->prec, P->tune.ncap[0])};
     TcLaunch B{P->d_tiles[1], P->d_terms[1], P->ntiles[1], P->prec, nullptr, nullptr, yo, P->d_err, P->part,
                nullptr, P->tune.ncap[1], tc_stages(P->prec, P->tune.ncap[1])};
     if (!launch_tc_gemm(P->maps[0], A, num_sms, stream) || !launch_tc_gemm(P->maps[1], B, num_sms, stream))
       throw Error(-3, "invalid tensor-core launch configuration");
+    CK(cudaEventRecordWithFlags(evg1, stream, evf));
     launch_tc_reduce(P->d_red, P->nred, P->red_total, P->part, yo, stream);
   };
   if (use_graphs) {
@@ -521,6 +572,9 @@ void Engine::tc_apply(TcPlan* P, const double* x, double* y) {
   stats.n_sigma++;
   stats.n_sigma_tc++;
   stats.tc_flops += P->flops_alg;
+  stats.tc_bytes += P->bytes_alg;
+  stats.tc_flops_p[P->prec] += P->flops_alg;
+  stats.last_tc_prec = P->prec;
 }
 
 }  // namespace gbd

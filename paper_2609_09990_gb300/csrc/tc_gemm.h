@@ -8,13 +8,17 @@
 // height) then serves every block product of a launch.
 //
 // A work tile is 128 rows of A (M) by n_mma (<= 256, multiple of 16) rows
-// of B (N); it accumulates C += sign * A_t B_t^T over its terms t in TMEM
+// of B (N) starting at A row ay + m0 and B row by + n0 of each term, so that
+// all tiles of one output block share one term list; it accumulates
+// C += sign * A_t B_t^T over its terms t in TMEM
 // (FP32) and is written by one of two epilogues:
 //   kTcYT    : C^T into a panel (BF16, TF32, or TF32 hi/lo), row j of the
 //              output is panel row out + j, output column = the padded
 //              position of tile row m0 + i (rmap: 4 breaks + 4 pads),
 //   kTcYTmap : C into a panel: row i goes to panel row rowmap[out + i],
-//              column j to the padded position of n0 + j (same rmap),
+//              columns n0 + j (the B rows are already in padded positions,
+//              so every 16-column chunk is contiguous and 16-aligned:
+//              vector stores),
 //   kTcSigma : C^T into FP64, out[j * ld + m0 + i] (= or +=),
 //   kTcPart  : C^T into an FP32 partial slot, part[out + j * 128 + i]; the
 //              partial slots of one output tile (split K) are summed in FP64
@@ -33,7 +37,7 @@ enum TcMode { kTcYT = 0, kTcSigma = 1, kTcPart = 2, kTcYTmap = 3 };
 
 struct TcTerm {
   int32_t ax, ay;   // A box origin: column (K) and row (before adding the tile's m0)
-  int32_t by;       // B sub-block first row
+  int32_t by;       // B sub-block first row (before adding the tile's n0)
   int32_t k;        // K, a multiple of the MMA K step (16 BF16, 8 TF32)
   int32_t neg;      // 1: subtract the product
   int32_t bx;       // B box first column (K origin)
@@ -47,7 +51,7 @@ struct TcTile {
   int32_t mode, beta, ld;
   int64_t out;           // output element offset (panel row for kTcYT, row-map index for kTcYTmap)
   int32_t rbreak[4], rpad[4];
-  int32_t n0;            // kTcYTmap: position of the tile's first B row
+  int32_t n0;            // offset of the tile's first B row (kTcYTmap: also its first output column)
   int32_t unused;
 };
 
@@ -107,8 +111,9 @@ void launch_tc_convert(const TcConv* tasks, int ntasks, int prec, void* hi, void
 struct TcPsiSector {
   int64_t src_off;       // offset of the sector block in psi
   int32_t rows, cols;    // m_EL, m_ER
-  int32_t r0;            // panel row of its first row
+  int32_t r0;            // panel row of its first (padded) row
   int32_t cbreak[4], cpad[4];
+  int32_t rbreak[4], rpad[4];   // rows: E_L s-sections, each starting at a multiple of 16
 };
 void launch_tc_convert_psi(const double* psi, const TcPsiSector* sec, int nsec, int64_t total, int prec, void* hi,
                            void* lo, int64_t pitch, cudaStream_t s);

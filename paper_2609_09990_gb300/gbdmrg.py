@@ -51,11 +51,15 @@ class gbd_stats(C.Structure):
                 ("sigma_flops_exec", C.c_double), ("tc_ms", C.c_double), ("tc_flops", C.c_double),
                 ("n_sigma_tc", C.c_int64), ("tier_iterations", C.c_int64 * 3),
                 ("max_final_residual", C.c_double), ("sum_final_residual", C.c_double),
-                ("graph_launches", C.c_int64), ("autotune_trials", C.c_int64)]
+                ("graph_launches", C.c_int64), ("autotune_trials", C.c_int64), ("tc_gemm_ms", C.c_double),
+                ("tc_bytes", C.c_double), ("tc_flops_by_type", C.c_double * 3),
+                ("tc_gemm_ms_by_type", C.c_double * 3), ("tc_build_ms", C.c_double),
+                ("tc_build_phase_ms", C.c_double * 5)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
-        d["tier_iterations"] = list(d["tier_iterations"])
+        for k in ("tier_iterations", "tc_flops_by_type", "tc_gemm_ms_by_type", "tc_build_phase_ms"):
+            d[k] = list(d[k])
         return d
 
 
@@ -81,6 +85,7 @@ def lib():
                                         C.POINTER(gbd_result)]),
         "gbd_set_batch_workers": (C.c_int, [vp, C.c_int32]),
         "gbd_set_graphs": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
         "gbd_probe_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
         "gbd_init_state": (C.c_int, [vp]),
@@ -113,7 +118,7 @@ def lib():
         "gbd_load_precond": (C.c_int, [vp, C.c_char_p]),
         "gbd_set_precond_weights": (C.c_int, [vp, C.POINTER(C.c_float)]),
         "gbd_mlp_loss_grad": (C.c_int, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float),
-                                        C.c_int64, C.POINTER(C.c_float), _dp, _dp]),
+                                        C.c_int64, C.POINTER(C.c_float), C.c_double, _dp, _dp]),
         "gbd_mlp_precond": (C.c_int, [vp, _dp, _dp, C.c_double, C.c_double, C.c_int64, _dp]),
         "gbd_davidson_counts": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
@@ -280,6 +285,9 @@ class Context:
     def set_tc_tile(self, ncap):
         self._check(self.L.gbd_set_tc_tile(self.ptr, ncap), "gbd_set_tc_tile")
 
+    def set_preconditioner(self, preconditioner):
+        self._check(self.L.gbd_set_preconditioner(self.ptr, preconditioner), "gbd_set_preconditioner")
+
     def set_graphs(self, enable):
         self._check(self.L.gbd_set_graphs(self.ptr, 1 if enable else 0), "gbd_set_graphs")
 
@@ -352,14 +360,14 @@ class Context:
         self._check(self.L.gbd_set_precond_weights(self.ptr, p.ctypes.data_as(C.POINTER(C.c_float))),
                     "gbd_set_precond_weights")
 
-    def mlp_loss_grad(self, X, y, w, params):
+    def mlp_loss_grad(self, X, y, w, params, lam=0.0):
         fp = lambda a: np.ascontiguousarray(a, dtype=np.float32)
         X, y, w, params = fp(X), fp(y), fp(w), fp(params)
         loss = C.c_double()
         grad = np.zeros(params.size)
         f = C.POINTER(C.c_float)
         self._check(self.L.gbd_mlp_loss_grad(self.ptr, X.ctypes.data_as(f), y.ctypes.data_as(f), w.ctypes.data_as(f),
-                                             len(y), params.ctypes.data_as(f), C.byref(loss), _d(grad)),
+                                             len(y), params.ctypes.data_as(f), lam, C.byref(loss), _d(grad)),
                     "gbd_mlp_loss_grad")
         return loss.value, grad
 

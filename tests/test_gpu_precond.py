@@ -37,20 +37,22 @@ def test_gradients_match_cpu_reference(G):
     w = rng.uniform(0.1, 1.0, n).astype(np.float32)
     p = rand_params(3).astype(np.float32)
     ctx = G.Context(0)
-    loss, grad = ctx.mlp_loss_grad(X, y, w, p)
     net = mlp.MLP.from_params(p.astype(np.float64))
-    L, g = net.loss_and_grad(X.astype(np.float64), y.astype(np.float64), w.astype(np.float64))
-    assert abs(loss - L) <= 1e-5 * abs(L)
-    assert np.abs(grad - g).max() <= 1e-5 * np.abs(g).max()
+    for lam in (0.0, 0.5):
+        loss, grad = ctx.mlp_loss_grad(X, y, w, p, lam)
+        L, g = net.loss_and_grad(X.astype(np.float64), y.astype(np.float64), w.astype(np.float64), lam)
+        assert abs(loss - L) <= 1e-5 * abs(L)
+        assert np.abs(grad - g).max() <= 1e-5 * np.abs(g).max()
     ctx.close()
 
 
-def test_fused_inference_matches_cpu_reference(G):
+@pytest.mark.parametrize("scale", [0.3, 3.0])   # 3.0: outputs beyond the clip range
+def test_fused_inference_matches_cpu_reference(G, scale):
     rng = np.random.default_rng(8)
     n = 20000
     r = rng.normal(size=n) * 1e-3
     d = rng.normal(size=n) * 3 - 10
-    p = rand_params(4)
+    p = rand_params(4, scale)
     p16 = p.astype(np.float16).astype(np.float64)      # the device keeps FP16 weights
     ctx = G.Context(0)
     ctx.set_precond_weights(p.astype(np.float32))
