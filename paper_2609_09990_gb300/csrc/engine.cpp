@@ -50,7 +50,7 @@ void Bond::finalize() {
   idx.clear();
   for (size_t i = 0; i < na.size(); ++i) {
     off[i + 1] = off[i] + dim[i];
-    idx[qkey(na[i], nb[i])] = (int)i;
+    idx.set(na[i], nb[i], (int)i);
   }
 }
 
@@ -362,7 +362,7 @@ Space Engine::left_space(const Bond& bl, const std::vector<std::pair<int, int>>&
       sd[s] = i >= 0 ? bl.dim[i] : 0;
       tot += sd[s];
     }
-    sp.idx[qkey(Q.first, Q.second)] = sp.n();
+    sp.idx.set(Q.first, Q.second, sp.n());
     sp.qa.push_back(Q.first);
     sp.qb.push_back(Q.second);
     sp.dim.push_back(tot);
@@ -385,7 +385,7 @@ Space Engine::right_space(const Bond& br, const std::vector<std::pair<int, int>>
       sd[s] = i >= 0 ? br.dim[i] : 0;
       tot += sd[s];
     }
-    sp.idx[qkey(Q.first, Q.second)] = sp.n();
+    sp.idx.set(Q.first, Q.second, sp.n());
     sp.qa.push_back(Q.first);
     sp.qb.push_back(Q.second);
     sp.dim.push_back(tot);
@@ -628,36 +628,56 @@ void Engine::free_enl(EnlOp& op) {
 }
 
 // ------------------------------------------------------------------ environment updates
+namespace {
+// sub-block indices of an enlarged operator grouped by key b * nq + qin
+// (counting sort, keys ascending, sub order kept within a key)
+struct SubGroups {
+  std::vector<int> start, idx;
+  int nq = 0, nkeys = 0;
+  SubGroups(const EnlOp& op, int nq_) : nq(nq_) {
+    int nb = 0;
+    for (const auto& s : op.subs) nb = std::max(nb, s.b + 1);
+    nkeys = nb * nq;
+    start.assign((size_t)nkeys + 1, 0);
+    for (const auto& s : op.subs) start[(size_t)s.b * nq + s.qin + 1]++;
+    for (int k = 0; k < nkeys; ++k) start[k + 1] += start[k];
+    idx.resize(op.subs.size());
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (size_t i = 0; i < op.subs.size(); ++i) idx[fill[(size_t)op.subs[i].b * nq + op.subs[i].qin]++] = (int)i;
+  }
+};
+}  // namespace
+
 // L_{k+1}[b](Qout <- Qin) = U_Qout^T (Lenl[b] U_Qin); U = A_k (fused-left).
 void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, const Bond& bnew, Env& out) {
   int bond = (int)(&bnew - &bonds[0]);
   make_env(bond, out);
   // T_b(Qin) blocks: rows E_L(Qout), cols m_new(Qin)
-  std::map<std::pair<int, int>, std::vector<const EnlSub*>> groups;   // (b, qin) -> subs
-  for (const auto& s : lenl.subs) groups[{s.b, s.qin}].push_back(&s);
-  struct TB { int b, qin, qout, nin, nout; int64_t off; };
+  const SubGroups groups(lenl, el.n());   // (b, qin) -> subs
+  struct TB { int b, qin, qout, nin, nout; int64_t off; int key; };
   std::vector<TB> tbs;
   int64_t tsize = 0;
-  for (auto& g : groups) {
-    int b = g.first.first, qin = g.first.second;
+  for (int key = 0; key < groups.nkeys; ++key) {
+    if (groups.start[key] == groups.start[key + 1]) continue;
+    const int b = key / groups.nq, qin = key % groups.nq;
     int jin = bnew.find(el.qa[qin], el.qb[qin]);
     if (jin < 0) continue;
-    int qout = g.second[0]->qout;
+    int qout = lenl.subs[groups.idx[groups.start[key]]].qout;
     int jout = bnew.find(el.qa[qout], el.qb[qout]);
     if (jout < 0) continue;
-    tbs.push_back({b, qin, qout, jin, jout, tsize});
+    tbs.push_back({b, qin, qout, jin, jout, tsize, key});
     tsize += (int64_t)el.dim[qout] * bnew.dim[jin];
   }
   double* T = dalloc<double>(tsize);
   GemmPlan p1, p2;
   for (auto& tb : tbs) {
     int nin = bnew.dim[tb.nin];
-    const auto& subs = groups[{tb.b, tb.qin}];
     const double* U_in = A.d + A.off[tb.nin];
     for (int so = 0; so < 4; ++so) {
       if (el.soff[tb.qout][so] < 0) continue;
       p1.add_out(T + tb.off + (int64_t)el.soff[tb.qout][so] * nin, nin, el.sdim[tb.qout][so], nin, 0);
-      for (const EnlSub* s : subs) {
+      for (int gi = groups.start[tb.key]; gi < groups.start[tb.key + 1]; ++gi) {
+        const EnlSub* s = &lenl.subs[groups.idx[gi]];
         if (s->sout != so) continue;
         p1.add_term(s->ptr, s->cols, U_in + (int64_t)el.soff[tb.qin][s->sin] * nin, nin, s->cols, 0, s->sign);
       }
@@ -688,31 +708,31 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
 void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B, const Bond& bnew, Env& out) {
   int bond = (int)(&bnew - &bonds[0]);
   make_env(bond, out);
-  std::map<std::pair<int, int>, std::vector<const EnlSub*>> groups;
-  for (const auto& s : renl.subs) groups[{s.b, s.qin}].push_back(&s);
-  struct TB { int b, qin, qout, nin, nout; int64_t off; };
+  const SubGroups groups(renl, er.n());   // (b, qin) -> subs
+  struct TB { int b, qin, qout, nin, nout; int64_t off; int key; };
   std::vector<TB> tbs;
   int64_t tsize = 0;
-  for (auto& g : groups) {
-    int b = g.first.first, qin = g.first.second;
+  for (int key = 0; key < groups.nkeys; ++key) {
+    if (groups.start[key] == groups.start[key + 1]) continue;
+    const int b = key / groups.nq, qin = key % groups.nq;
     int jin = bnew.find(er.qa[qin], er.qb[qin]);
     if (jin < 0) continue;
-    int qout = g.second[0]->qout;
+    int qout = renl.subs[groups.idx[groups.start[key]]].qout;
     int jout = bnew.find(er.qa[qout], er.qb[qout]);
     if (jout < 0) continue;
-    tbs.push_back({b, qin, qout, jin, jout, tsize});
+    tbs.push_back({b, qin, qout, jin, jout, tsize, key});
     tsize += (int64_t)er.dim[qout] * bnew.dim[jin];
   }
   double* T = dalloc<double>(tsize);
   GemmPlan p1, p2;
   for (auto& tb : tbs) {
     int nin = bnew.dim[tb.nin];
-    const auto& subs = groups[{tb.b, tb.qin}];
     const double* B_in = B.d + B.off[tb.nin];   // nin x m_ER(qin)
     for (int so = 0; so < 4; ++so) {
       if (er.soff[tb.qout][so] < 0) continue;
       p1.add_out(T + tb.off + (int64_t)er.soff[tb.qout][so] * nin, nin, er.sdim[tb.qout][so], nin, 0);
-      for (const EnlSub* s : subs) {
+      for (int gi = groups.start[tb.key]; gi < groups.start[tb.key + 1]; ++gi) {
+        const EnlSub* s = &renl.subs[groups.idx[gi]];
         if (s->sout != so) continue;
         p1.add_term(s->ptr, s->cols, B_in + er.soff[tb.qin][s->sin], er.dim[tb.qin], s->cols, 2, s->sign);
       }
@@ -1305,11 +1325,17 @@ double Engine::solve_tiers(Sigma& sg, const double* diag, double tol, int precis
     const double floor1 = p1 == kBF16 ? 5e-2 : 1e-2;
     // measured relative sigma errors: BF16 2e-3, TF32 3e-4, TF32x3 3e-6
     const double u1 = p1 == kBF16 ? 2e-3 : 3e-4, u2 = 3e-6;
-    TcPlan* P = tc_plan(sg.lenl, sg.renl, p1);
-    theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, std::max(tol, floor1),
-                     sched.max_iter, sched.max_space, 30.0 * u1 * hscale);
-    tc_free(P);
-    tier_done(0);
+    TcPlan* P = nullptr;
+    stats.last_residual = 1e300;
+    if (!skip_tier1) {
+      P = tc_plan(sg.lenl, sg.renl, p1);
+      theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, std::max(tol, floor1),
+                       sched.max_iter, sched.max_space, 30.0 * u1 * hscale);
+      tc_free(P);
+      t1_iters_cur += stats.davidson_iters - it0;
+      t1_steps_cur++;
+      tier_done(0);
+    }
     if (stats.last_residual >= tol) {
       P = tc_plan(sg.lenl, sg.renl, kTF32x3);
       theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, tol, sched.max_iter,
@@ -1569,6 +1595,9 @@ void Engine::prepare(int n_, int n_elec, int two_sz, int n_chol, const double* h
   stats = Stats();
   sweep_E.clear();
   prepared = false;
+  t1_iters_cur = t1_steps_cur = t1_steps_prev = 0;
+  t1_iters_prev = -1;
+  skip_tier1 = false;
 }
 
 void Engine::init_state() {
@@ -1583,6 +1612,12 @@ double Engine::sweep(int s) {
   int M = sched.M[s];
   double tol = sched.tol[s];
   double e = 0;
+  if (t1_steps_cur > 0) {   // the last sweep that ran tier 1 decides
+    t1_iters_prev = t1_iters_cur;
+    t1_steps_prev = t1_steps_cur;
+  }
+  t1_iters_cur = t1_steps_cur = 0;
+  skip_tier1 = s > 0 && t1_steps_prev > 0 && t1_iters_prev < 2 * t1_steps_prev;
   for (int k = 0; k <= n - 2; ++k) e = step(k, 0, M, tol, nullptr, nullptr);
   for (int k = n - 2; k >= 0; --k) e = step(k, 1, M, tol, nullptr, nullptr);
   sweep_E.push_back(e);

@@ -34,12 +34,8 @@ struct Error : std::runtime_error {
 struct Space {
   std::vector<int> qa, qb, dim;
   std::vector<std::array<int, 4>> soff, ssec, sdim;
-  std::unordered_map<int, int> idx;
-  int find(int a, int b) const {
-    if (a < 0 || b < 0 || a > 63 || b > 63) return -1;
-    auto it = idx.find(qkey(a, b));
-    return it == idx.end() ? -1 : it->second;
-  }
+  QIndex idx;
+  int find(int a, int b) const { return idx.get(a, b); }
   int n() const { return (int)qa.size(); }
 };
 
@@ -166,6 +162,11 @@ class Engine {
   bool use_graphs = true;     // replay the sigma launch sequences as CUDA graphs
   bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
+  // tier-1 (BF16/TF32) Davidson iterations and steps of the current and the
+  // previous sweep: a warm sweep whose predecessor averaged < 2 tier-1
+  // iterations per step skips tier 1 (its plan would cost more than it saves)
+  int64_t t1_iters_cur = 0, t1_steps_cur = 0, t1_iters_prev = -1, t1_steps_prev = 0;
+  bool skip_tier1 = false;
   const std::vector<float>& precond_weights() const { return mlp_f32; }
   int64_t n_samples() const { return (int64_t)data_y.size(); }
 

@@ -28,16 +28,26 @@ constexpr int PAR[4] = {0, 1, 1, 0};
 
 inline int qkey(int a, int b) { return a * 64 + b; }
 
+// sector index by (N_alpha, N_beta), both in [0, 63]: a dense 64 x 64 table
+struct QIndex {
+  std::vector<int> t;
+  void clear() { t.assign(64 * 64, -1); }
+  void set(int a, int b, int v) {
+    if (t.empty()) clear();
+    t[a * 64 + b] = v;
+  }
+  int get(int a, int b) const {
+    if (a < 0 || b < 0 || a > 63 || b > 63 || t.empty()) return -1;
+    return t[a * 64 + b];
+  }
+};
+
 struct Bond {
   std::vector<int> na, nb, dim;   // sorted by (na, nb)
   std::vector<int64_t> off;        // prefix offsets of dims
-  std::unordered_map<int, int> idx;
+  QIndex idx;
   void finalize();
-  int find(int a, int b) const {
-    if (a < 0 || b < 0 || a > 63 || b > 63) return -1;
-    auto it = idx.find(qkey(a, b));
-    return it == idx.end() ? -1 : it->second;
-  }
+  int find(int a, int b) const { return idx.get(a, b); }
   int nsec() const { return (int)na.size(); }
   int64_t total() const { return off.empty() ? 0 : off.back(); }
 };
