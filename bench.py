@@ -111,6 +111,7 @@ def run_ours(args, rank, world):
     import torch
     torch.cuda.set_device(dev)
     ctx = G.Context(dev)
+    ctx.set_accurate_tier(3 if args.tier2 == "tf32x3" else 4)
     nsw = args.warmup + args.steps
     ctx.setup(h, chol, ne, 0, [M] * (nsw + 1), schedule(nsw + 1, args.tol), seed=seed, precision=prec,
               fp64_refine=args.refine)
@@ -132,8 +133,8 @@ def run_ours(args, rank, world):
     clocks = clk.stop()
     st1 = ctx.stats()
     dt = t1 - t0
-    keys = ["sigma_ms", "tc_ms", "tc_gemm_ms", "tc_build_ms", "env_ms", "enlarge_ms", "davidson_ms", "truncate_ms",
-            "step_ms"]
+    keys = ["sigma_ms", "tc_ms", "tc_gemm_ms", "tc_build_ms", "env_ms", "enlarge_ms", "enlarge_host_ms", "diag_ms",
+            "davidson_ms", "truncate_ms", "truncate_rho_ms", "truncate_eig_ms", "step_ms"]
     breakdown = {k: (st1[k] - st0[k]) / args.steps for k in keys}
     breakdown["sigma_builds"] = (st1["n_sigma"] - st0["n_sigma"]) / args.steps
     breakdown["tc_sigma_builds"] = (st1["n_sigma_tc"] - st0["n_sigma_tc"]) / args.steps
@@ -175,6 +176,7 @@ def run_ours(args, rank, world):
     e2e = None
     if not args.no_e2e:
         ctx = G.Context(dev)
+        ctx.set_accurate_tier(3 if args.tier2 == "tf32x3" else 4)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         r = ctx.solve(h, chol, ne, 0, [M] * args.steps, schedule(args.steps, args.tol), seed=seed,
@@ -238,6 +240,37 @@ def run_batched(args, rank, world):
     ctx.close()
     return dict(time=t1 - t0, flops=flops, launches=launches, graph_launches=graphs, clocks=clocks,
                 energies=[r["energy"] for r in res], n_problems=len(probs))
+
+
+def sigma_probe(prec):
+    """Profiling driver for the tensor-core sigma: CAS(16,16) M=512, initial
+    state, FP64 steps up to the central bond (7,8), then three sigma builds
+    there with operand type `prec` (1 TF32, 2 BF16, 3 TF32x3).  The first
+    one runs the tile-shape autotuner (3 candidate plans x 3 timed runs = 18
+    tc_gemm_kernel launches), so `ncu -k regex:tc_gemm_kernel -s 18 -c 2`
+    captures stage A and stage B of the tuned plan."""
+    from paper_2609_09990_gb300 import gbdmrg as G
+    wl = WORKLOADS["cas16_m512"]
+    n, ne, nq, M, seed = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"]
+    h, chol = make_integrals(n, nq, seed)
+    ctx = G.Context(0)
+    ctx.setup(h, chol, ne, 0, [M], [1e-6], seed=seed)
+    ctx.init_state()
+    k = n // 2 - 1
+    for j in range(k):
+        ctx.run_step(j, 0, M, 1e-3)
+    x = np.random.default_rng(0).standard_normal(ctx.two_site_size(k))
+    s0 = ctx.stats()
+    for _ in range(3):
+        ctx.apply_heff_prec(k, x, prec)
+    s1 = ctx.stats()
+    nb = s1["n_sigma_tc"] - s0["n_sigma_tc"]
+    print(json.dumps({"sigma_probe": prec, "bond": k, "psi_len": int(x.size), "builds": nb,
+                      "tc_gemm_ms_per_build": (s1["tc_gemm_ms"] - s0["tc_gemm_ms"]) / nb,
+                      "tc_ms_per_build": (s1["tc_ms"] - s0["tc_ms"]) / nb,
+                      "alg_bytes_per_build": (s1["tc_bytes"] - s0["tc_bytes"]) / nb,
+                      "alg_flops_per_build": (s1["tc_flops"] - s0["tc_flops"]) / nb}))
+    ctx.close()
 
 
 def dist_barrier(world):
@@ -314,7 +347,14 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=2, help="sweeps per problem (batched64)")
     ap.add_argument("--workers", type=int, default=0, help="host worker threads (batched64; 0 = auto)")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--tier2", default="tf32x3", choices=["tf32x3", "bf16x3"],
+                    help="operands of the accurate Davidson tier")
+    ap.add_argument("--sigma-probe", type=int, default=0, help="profiling driver: central sigma of cas16_m512 "
+                    "with operand type 1 TF32, 2 BF16, 3 TF32x3 (no bench line)")
     args = ap.parse_args()
+    if args.sigma_probe:
+        sigma_probe(args.sigma_probe)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
@@ -397,13 +437,13 @@ def main():
         # tc_gemm_kernel (stage A + stage B launches, CUDA events around them
         # on the engine stream).  Tensor view: algorithmic flops per operand
         # type against that type's peak (BF16: measured sustained; TF32:
-        # x 1.1/2.25, the nominal ratio; TF32x3: three TF32 passes), i.e. the
+        # x 1.1/2.25, the nominal ratio; TF32x3 / BF16x3: three passes), i.e. the
         # time the flops need at peak over the time they took.  HBM view:
         # algorithmic bytes (enlarged operators once, Y^T written and read
         # once, psi and sigma) over the same time.  The larger fraction binds.
         tc = res["tc"]
         pb = pk["bf16_tflops_sustained"]
-        tpk = [pb, pb * 1.1 / 2.25, pb * 1.1 / 2.25 / 3]
+        tpk = [pb, pb * 1.1 / 2.25, pb * 1.1 / 2.25 / 3, pb / 3]   # BF16, TF32, TF32x3, BF16x3
         gms = tc["tc_gemm_ms"]
         at_peak = sum(f / (p * 1e12) for f, p in zip(tc["tc_flops_by_type"], tpk))
         tfrac = at_peak / (gms / 1000) if gms > 0 else 0.0
@@ -427,7 +467,8 @@ def main():
     line = {"metric": "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u22641e-6 Ha", "value": flops / tmax / 1e12,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic", "config": config,
+            "vs_baseline": None, "data": "synthetic", "config": config,
+            "dtype": DTYPE["fp64"] if args.precision == "fp64" else f"{args.precision}+{args.tier2}/f32-acc",
             "sweep_time_s": tmax / args.steps, "sweep_energies": res["energies"],
             "sigma_kernel_tflops": kern_tflops, "final_energy": res["e_final"],
             "per_sweep": res["breakdown"], "roofline": roof,

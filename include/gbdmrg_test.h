@@ -42,10 +42,13 @@ typedef struct {
   int64_t autotune_trials;      /* tensor-core plans built and timed by the tile-shape autotuner */
   double tc_gemm_ms;            /* device time of the tc_gemm_kernel launches alone (CUDA events) */
   double tc_bytes;              /* algorithmic HBM bytes of the tensor-core sigma builds */
-  double tc_flops_by_type[3];   /* algorithmic flops of those builds with BF16, TF32, TF32x3 operands */
-  double tc_gemm_ms_by_type[3]; /* tc_gemm_kernel device time of those builds */
+  double tc_flops_by_type[4];   /* algorithmic flops of those builds with BF16, TF32, TF32x3, BF16x3 operands */
+  double tc_gemm_ms_by_type[4]; /* tc_gemm_kernel device time of those builds */
   double tc_build_ms;           /* host wall time building tensor-core plans, autotuning included */
   double tc_build_phase_ms[5];  /* of which: layouts and groups, panels, tile lists, upload, tensor maps */
+  double enlarge_host_ms;       /* host part of enlarge_ms (sub-block lists, before the device axpy) */
+  double diag_ms;               /* H_eff diagonal (wall) */
+  double truncate_rho_ms, truncate_eig_ms;   /* decimation: density matrices to the host; eigensolves */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or
@@ -60,6 +63,10 @@ int gbd_set_tc_tile(gbd_ctx *ctx, int32_t ncap);
 /* Preconditioner of the following Davidson solves (GBD_PRECOND_DIAG or
  * GBD_PRECOND_LEARNED; the latter needs weights in the context). */
 int gbd_set_preconditioner(gbd_ctx *ctx, int32_t preconditioner);
+
+/* Operands of the accurate Davidson tier of reduced-precision schedules:
+ * 3 = TF32x3 (default), 4 = BF16x3 (the codes of gbd_apply_heff_prec). */
+int gbd_set_accurate_tier(gbd_ctx *ctx, int32_t prec);
 
 /* One Davidson solve at the current centre k (environments k and k+2
  * valid, as after gbd_init_state for k = 0 or after steps up to k-1) in
@@ -95,7 +102,7 @@ int gbd_two_site_size(gbd_ctx *ctx, int32_t k, int64_t *size);
 /* out = H_eff in (two-site format); diag (may be NULL) = diagonal of H_eff. */
 int gbd_apply_heff(gbd_ctx *ctx, int32_t k, const double *in, double *out, double *diag);
 /* out = H_eff in through the tensor-core sigma: prec 1 TF32, 2 BF16,
- * 3 TF32x3 (0 = the FP64 path, same as gbd_apply_heff). */
+ * 3 TF32x3, 4 BF16x3 (0 = the FP64 path, same as gbd_apply_heff). */
 int gbd_apply_heff_prec(gbd_ctx *ctx, int32_t k, int32_t prec, const double *in, double *out);
 /* One two-site step at (k, k+1): Davidson from the current two-site state,
  * decimation to at most M states and the environment update.  dir 0 = left
@@ -169,6 +176,9 @@ int gbd_davidson_counts(gbd_ctx *ctx, int64_t *iterations, int64_t *fallbacks, i
 int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);
 
 /* ---- host-only pieces of the planner (no GPU needed) ---- */
+/* The decimation's host eigensolver (Householder + implicit QL): A [n*n]
+ * symmetric row-major; w [n] ascending; Z [n*n] with column j = eigenvector j. */
+int gbd_host_sym_eig(int32_t n, const double *A, double *w, double *Z);
 /* Initial bond dimensions of the seeded MPS for n orbitals, (N_alpha,
  * N_beta) electrons and bond dimension M; n_sectors [n+1], triples [3 cap]. */
 int gbd_host_initial_dims(int32_t n, int32_t n_alpha, int32_t n_beta, int32_t M, int32_t *n_sectors,

@@ -15,6 +15,7 @@
 #include "../../include/gbdmrg.h"
 #include "../../include/gbdmrg_test.h"
 #include "engine.h"
+#include "linalg_host.h"
 
 namespace gbd {
 double mps_init_value(uint64_t seed, int site, int na, int nb, int s, int row, int col);
@@ -297,6 +298,15 @@ int gbd_set_preconditioner(gbd_ctx* ctx, int32_t preconditioner) {
   });
 }
 
+int gbd_set_accurate_tier(gbd_ctx* ctx, int32_t prec) {
+  return guarded(ctx, [&]() {
+    if (prec != 3 && prec != 4) return fail(ctx, GBD_ERR_ARG, "accurate tier must be 3 (TF32x3) or 4 (BF16x3)");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tier2 = prec == 3 ? 2 : 3;   // TcPrec kTF32x3 / kBF16x3
+    return GBD_OK;
+  });
+}
+
 int gbd_probe_step(gbd_ctx* ctx, int32_t k, int32_t precision, int32_t fp64_refine, double tol, double* theta,
                    double* e64, double* r64) {
   return guarded(ctx, [&]() {
@@ -399,7 +409,7 @@ int gbd_apply_heff_prec(gbd_ctx* ctx, int32_t k, int32_t prec, const double* in,
   return guarded(ctx, [&]() {
     if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
     if (k < 0 || k > ctx->eng->n - 2) return fail(ctx, GBD_ERR_ARG, "k out of range");
-    if (prec < 0 || prec > 3) return fail(ctx, GBD_ERR_ARG, "prec must be 0..3");
+    if (prec < 0 || prec > 4) return fail(ctx, GBD_ERR_ARG, "prec must be 0..4");
     if (!in || !out) return fail(ctx, GBD_ERR_ARG, "NULL vector");
     ctx->eng->apply_heff(k, in, out, nullptr, prec);
     return GBD_OK;
@@ -587,8 +597,12 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->tc_gemm_ms = t.tc_gemm_ms;
   s->tc_bytes = t.tc_bytes;
   s->tc_build_ms = t.tc_build_ms;
+  s->enlarge_host_ms = t.enl_host_ms;
+  s->diag_ms = t.diag_ms;
+  s->truncate_rho_ms = t.trunc_rho_ms;
+  s->truncate_eig_ms = t.trunc_eig_ms;
   for (int i = 0; i < 5; ++i) s->tc_build_phase_ms[i] = t.tcb_ms[i];
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     s->tc_flops_by_type[i] = t.tc_flops_p[i];
     s->tc_gemm_ms_by_type[i] = t.tc_gemm_ms_p[i];
   }
@@ -605,6 +619,15 @@ int gbd_get_batch_stats(const gbd_ctx* ctx, gbd_stats* s) {
   if (!ctx || !s) return GBD_ERR_ARG;
   copy_stats(ctx->batch_stats, s);
   return GBD_OK;
+}
+
+int gbd_host_sym_eig(int32_t n, const double* A, double* w, double* Z) {
+  if (n < 0 || (n > 0 && (!A || !w || !Z))) return GBD_ERR_ARG;
+  try {
+    return gbd::sym_eig(n, A, w, Z) == 0 ? GBD_OK : GBD_ERR_NOCONV;
+  } catch (...) {
+    return GBD_ERR_OOM;
+  }
 }
 
 int gbd_host_initial_dims(int32_t n, int32_t n_alpha, int32_t n_beta, int32_t M, int32_t* n_sectors,

@@ -83,9 +83,11 @@ struct Stats {
   double max_final_residual = 0, sum_final_residual = 0;   // over Davidson solves
   int64_t graph_launches = 0, autotune_trials = 0;
   double tc_gemm_ms = 0, tc_bytes = 0;   // tc_gemm_kernel launches only; algorithmic bytes of the TC sigma builds
-  double tc_flops_p[3] = {0, 0, 0}, tc_gemm_ms_p[3] = {0, 0, 0};   // by operand type (BF16, TF32, TF32x3)
+  double tc_flops_p[4] = {0, 0, 0, 0}, tc_gemm_ms_p[4] = {0, 0, 0, 0};   // by operand type (BF16, TF32, TF32x3, BF16x3)
   int last_tc_prec = 0;
   double tc_build_ms = 0;   // host wall time building tensor-core plans (incl. autotuning)
+  double enl_host_ms = 0, diag_ms = 0;   // host part of the enlarged operators; the H_eff diagonal
+  double trunc_rho_ms = 0, trunc_eig_ms = 0;   // decimation: density matrices to the host; host eigensolves
   double tcb_ms[5] = {0, 0, 0, 0, 0};   // plan-build phases: layout/groups, panels, tiles, upload, maps
   void add(const Stats& o) {   // sum of the additive counters (batched solves)
     sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
@@ -97,9 +99,10 @@ struct Stats {
     max_final_residual = std::max(max_final_residual, o.max_final_residual);
     sum_final_residual += o.sum_final_residual;
     graph_launches += o.graph_launches; autotune_trials += o.autotune_trials;
-    tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms;
+    tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms; enl_host_ms += o.enl_host_ms; diag_ms += o.diag_ms;
+    trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms;
     for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
-    for (int i = 0; i < 3; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
+    for (int i = 0; i < 4; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
     max_discarded = std::max(max_discarded, o.max_discarded);
   }   // Davidson iterations: low-precision tier, TF32x3 tier, FP64
   double max_discarded = 0;
@@ -162,6 +165,7 @@ class Engine {
   bool use_graphs = true;     // replay the sigma launch sequences as CUDA graphs
   bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
+  int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
   // tier-1 (BF16/TF32) Davidson iterations and steps of the current and the
   // previous sweep: a warm sweep whose predecessor averaged < 2 tier-1
   // iterations per step skips tier 1 (its plan would cost more than it saves)
@@ -240,9 +244,9 @@ class Engine {
   void plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg);
   void sigma(Sigma& sg, const double* x, double* y);
   void compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag);
-  // stag_floor > 0: stop on stagnation (reduced-precision operators); see the definition
+  // stag_rel > 0: stop on stagnation (reduced-precision operators); see the definition
   double davidson(const std::function<void(const double*, double*)>& op, const double* diag, double tol,
-                  int max_iter, int max_space, double stag_floor);
+                  int max_iter, int max_space, double stag_rel);
   // the Davidson solve of one step in schedule precision `precision` with at
   // most `refine` FP64 iterations; the Ritz vector is left in psi
   double solve_tiers(Sigma& sg, const double* diag, double tol, int precision, int refine, bool& planned);

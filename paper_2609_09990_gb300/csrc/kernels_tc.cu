@@ -10,8 +10,8 @@
 //   warps 2-5 epilogue: tcgen05.ld of the accumulator rows they may access
 //            (TMEM lane quarter = warp id % 4), conversion, global stores.
 // Two accumulators let the epilogue of tile i overlap the MMAs of tile i+1.
-// TF32x3 (accurate tier) splits every operand into TF32 hi + lo and issues
-// hi*hi + hi*lo + lo*hi into the same accumulator.
+// TF32x3 and BF16x3 (accurate tiers) split every operand into hi + lo of
+// that type and issue hi*hi + hi*lo + lo*hi into the same accumulator.
 // Every mbarrier wait is bounded: on timeout the kernel raises *err, all
 // roles stop issuing, and TMEM is released before the CTA exits.
 #include <mutex>
@@ -125,8 +125,8 @@ __device__ __forceinline__ float to_tf32(float x) {
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcMaps maps,
                                                              const TcLaunch L) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  const bool x3 = L.prec == kTF32x3;
-  const bool bf = L.prec == kBF16;
+  const bool x3 = L.prec == kTF32x3 || L.prec == kBF16x3;
+  const bool bf = L.prec == kBF16 || L.prec == kBF16x3;
   // B boxes of this launch are at most L.ncap rows; the ring holds as many
   // stages as fit (tc_stages)
   const int bstage = L.ncap * 128;
@@ -239,6 +239,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint64_t ad = smem_desc(sa + kk * 32), bd = smem_desc(sb + kk * 32);
             if (bf) {
               mma_bf16(dt, ad, bd, idesc, first ? 0u : 1u);
+              if (x3) {
+                const uint32_t sa2 = sb + bstage, sb2 = sa2 + kStageA;
+                mma_bf16(dt, ad, smem_desc(sb2 + kk * 32), idesc, 1u);                 // hi * lo
+                mma_bf16(dt, smem_desc(sa2 + kk * 32), bd, idesc, 1u);                 // lo * hi
+              }
             } else {
               mma_tf32(dt, ad, bd, idesc, first ? 0u : 1u);
               if (x3) {
@@ -292,15 +297,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           // 16 contiguous, 16-element aligned output columns
           const int64_t idx = prow + c0;
           if (bf) {
-            uint32_t w[8];
+            uint32_t w[8], wl[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
               w[i] = *reinterpret_cast<uint32_t*>(&p2);
+              __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * i] - __low2float(p2), v[2 * i + 1] - __high2float(p2));
+              wl[i] = *reinterpret_cast<uint32_t*>(&l2);
             }
             uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(L.yt_hi) + idx);
             d[0] = make_uint4(w[0], w[1], w[2], w[3]);
             d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            if (x3) {
+              uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(L.yt_lo) + idx);
+              dl[0] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+              dl[1] = make_uint4(wl[4], wl[5], wl[6], wl[7]);
+            }
           } else {
             float h[16], l[16];
 #pragma unroll
@@ -332,7 +344,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           } else {
             const int64_t idx = (T.out + j) * (int64_t)T.ld + pcol;
             if (bf) {
-              reinterpret_cast<__nv_bfloat16*>(L.yt_hi)[idx] = __float2bfloat16_rn(v[i]);
+              const __nv_bfloat16 hb = __float2bfloat16_rn(v[i]);
+              reinterpret_cast<__nv_bfloat16*>(L.yt_hi)[idx] = hb;
+              if (x3) reinterpret_cast<__nv_bfloat16*>(L.yt_lo)[idx] = __float2bfloat16_rn(v[i] - __bfloat162float(hb));
             } else {
               const float hi = to_tf32(v[i]);
               reinterpret_cast<float*>(L.yt_hi)[idx] = hi;
@@ -382,8 +396,10 @@ __global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, in
 
 // ---------------------------------------------------------------- conversions
 __device__ __forceinline__ void store_conv(double x, int prec, void* hi, void* lo, int64_t idx) {
-  if (prec == kBF16) {
-    reinterpret_cast<__nv_bfloat16*>(hi)[idx] = __double2bfloat16(x);
+  if (prec == kBF16 || prec == kBF16x3) {
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    reinterpret_cast<__nv_bfloat16*>(hi)[idx] = h;
+    if (prec == kBF16x3) reinterpret_cast<__nv_bfloat16*>(lo)[idx] = __double2bfloat16(x - (double)__bfloat162float(h));
   } else {
     const float h = to_tf32((float)x);
     reinterpret_cast<float*>(hi)[idx] = h;
@@ -435,14 +451,14 @@ void launch_tc_reduce(const TcRed* tasks, int ntasks, int64_t total, const float
 }
 
 int tc_stages(int prec, int ncap) {
-  const int stage_bytes = (kStageA + ncap * 128) * (prec == kTF32x3 ? 2 : 1);
+  const int stage_bytes = (kStageA + ncap * 128) * (prec == kTF32x3 || prec == kBF16x3 ? 2 : 1);
   int s = (kSmemBudget - 1024 - 256) / stage_bytes;
   return s < kMaxStages ? s : kMaxStages;
 }
 
 int tc_smem_bytes(int prec, int ncap) {
   const int stages = tc_stages(prec, ncap);
-  const int stage_bytes = (kStageA + ncap * 128) * (prec == kTF32x3 ? 2 : 1);
+  const int stage_bytes = (kStageA + ncap * 128) * (prec == kTF32x3 || prec == kBF16x3 ? 2 : 1);
   return 1024 + stages * stage_bytes + (2 * stages + 4) * 8 + 16;
 }
 

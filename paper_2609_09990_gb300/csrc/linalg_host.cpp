@@ -81,10 +81,15 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
       for (int j = 0; j < n; ++j) row[j] -= f * t[j];
     }
   }
-  // ---- implicit QL on (d, e), rotating the columns of z.  An off-diagonal
+  // ---- implicit QL on (d, e), rotating the columns of z, kept transposed
+  // (zt row j = column j of z) so that a rotation touches two contiguous
+  // rows.  An off-diagonal
   // element is negligible when it is below eps relative to its neighbours or
   // below eps * ||T|| (backward-stable absolute deflation; density matrices
   // have many eigenvalues near zero where a purely relative test stalls).
+  std::vector<double> zt((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) zt[(size_t)j * n + i] = z[(size_t)i * n + j];
   const double eps = 2.220446049250313e-16;
   double anorm = 0.0;
   for (int i = 0; i < n; ++i) anorm = std::max(anorm, std::fabs(d[i]) + std::fabs(e[i]) + (i ? std::fabs(e[i - 1]) : 0.0));
@@ -121,10 +126,12 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
         p = s * r;
         d[i + 1] = g + p;
         g = c * r - b;
+        double* zi = &zt[(size_t)i * n];
+        double* zi1 = zi + n;
         for (int k = 0; k < n; ++k) {
-          double zf = z[(size_t)k * n + i + 1];
-          z[(size_t)k * n + i + 1] = s * z[(size_t)k * n + i] + c * zf;
-          z[(size_t)k * n + i] = c * z[(size_t)k * n + i] - s * zf;
+          const double zf = zi1[k];
+          zi1[k] = s * zi[k] + c * zf;
+          zi[k] = c * zi[k] - s * zf;
         }
       }
       if (early) continue;
@@ -139,7 +146,8 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return d[x] < d[y]; });
   for (int j = 0; j < n; ++j) {
     w[j] = d[ord[j]];
-    for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = z[(size_t)i * n + ord[j]];
+    const double* src = &zt[(size_t)ord[j] * n];
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + j] = src[i];
   }
   return 0;
 }

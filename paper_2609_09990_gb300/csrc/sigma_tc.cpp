@@ -63,8 +63,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   TcPlan* P = new TcPlan();
   P->prec = prec;
   P->tune = tune;
-  P->eb = prec == kBF16 ? 2 : 4;
-  const int nh = prec == kTF32x3 ? 2 : 1;
+  P->eb = prec == kBF16 || prec == kBF16x3 ? 2 : 4;
+  const int nh = prec == kTF32x3 || prec == kBF16x3 ? 2 : 1;
   const int nq = EL.n();
   double tph = now_ms();
   auto phase = [&](int i) {
@@ -301,9 +301,13 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         tiles.push_back(T);
       }
   }
+  // keys < 0: most expensive tiles first; else by the given keys (tiles
+  // that read the same A boxes adjacent, so that they run at the same time
+  // on neighbouring SMs and share the boxes through L2)
+  std::vector<std::array<int, 5>> bkey;
   auto upload_tiles = [&](int which) {
     P->ntiles[which] = (int)tiles.size();
-    // most expensive first: the persistent CTAs stride over the list
+    // the persistent CTAs stride over the list, so consecutive tiles run together
     std::vector<double> cost(tiles.size());
     std::vector<int> order(tiles.size());
     for (size_t i = 0; i < tiles.size(); ++i) {
@@ -312,7 +316,10 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       cost[i] = c * tiles[i].n_mma + 4096.0;   // + per-tile fixed cost (epilogue)
       order[i] = (int)i;
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    if (which == 1 && bkey.size() == tiles.size())
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bkey[a] < bkey[b]; });
+    else
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     {
       std::vector<TcTile> sorted(tiles.size());
       for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
@@ -370,6 +377,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           T.out = psi_off[q] + (int64_t)(EL.soff[q][so] + n0) * ER.dim[q];
           P->flops_exec += 2.0 * 128 * T.n_mma * (double)ksum;
           tiles.push_back(T);
+          bkey.push_back({q, m0, 0, so, n0});   // chunk index filled by the split
         }
     }
   // ---- split K: a stage-B tile whose summed K exceeds kc becomes chunks of
@@ -385,16 +393,19 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       for (int t = T.t0; t < T.t1; ++t) work += (int64_t)terms[t].k * T.n_valid;
     int64_t kc = work / ((int64_t)4 * num_sms * 256);
     kc = (kc + 63) / 64 * 64;
-    kc = std::max<int64_t>(256, std::min<int64_t>(prec == kTF32x3 ? 512 : 2048, kc));
+    kc = std::max<int64_t>(256, std::min<int64_t>(nh == 2 ? 512 : 2048, kc));
     P->kc = kc;
     std::vector<TcTile> split;
+    std::vector<std::array<int, 5>> skey;
     std::vector<TcRed> red;
     int64_t slot = 0, red_total = 0;
-    for (const TcTile& T : tiles) {
+    for (size_t ti = 0; ti < tiles.size(); ++ti) {
+      const TcTile& T = tiles[ti];
       int64_t ktot = 0;
       for (int t = T.t0; t < T.t1; ++t) ktot += terms[t].k;
       if (ktot <= kc) {
         split.push_back(T);
+        skey.push_back(bkey[ti]);
         continue;
       }
       TcRed R{T.out, slot, red_total, T.ld, T.m0, T.m_valid, T.n_valid, T.n_mma, 0};
@@ -410,12 +421,16 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         Cc.out = slot;
         Cc.ld = 128;
         slot += (int64_t)128 * T.n_mma;
+        std::array<int, 5> kk = bkey[ti];
+        kk[2] = R.nslot;
+        skey.push_back(kk);
         R.nslot++;
         split.push_back(Cc);
       }
       red.push_back(R);
     }
     tiles.swap(split);
+    bkey.swap(skey);
     P->nred = (int)red.size();
     P->red_total = red_total;
     if (!red.empty()) {

@@ -32,7 +32,7 @@
 
 namespace gbd {
 
-enum TcPrec { kBF16 = 0, kTF32 = 1, kTF32x3 = 2 };
+enum TcPrec { kBF16 = 0, kTF32 = 1, kTF32x3 = 2, kBF16x3 = 3 };
 enum TcMode { kTcYT = 0, kTcSigma = 1, kTcPart = 2, kTcYTmap = 3 };
 
 struct TcTerm {

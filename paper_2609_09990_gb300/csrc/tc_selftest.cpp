@@ -27,13 +27,14 @@ float bf16_to_float(uint16_t v) {
 extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t nterms,
                                uint64_t seed, double* max_err, double* max_ref) {
   using namespace gbd;
-  if (prec < 0 || prec > 2 || M < 1 || N < 1 || N > 4096 || K < 1 || nterms < 1 || !max_err || !max_ref)
+  if (prec < 0 || prec > 3 || M < 1 || N < 1 || N > 4096 || K < 1 || nterms < 1 || !max_err || !max_ref)
     return GBD_ERR_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return GBD_ERR_CUDA;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  const int eb = prec == kBF16 ? 2 : 4;
-  const int kstep = prec == kBF16 ? 16 : 8;
+  const bool bfp = prec == kBF16 || prec == kBF16x3, split = prec == kTF32x3 || prec == kBF16x3;
+  const int eb = bfp ? 2 : 4;
+  const int kstep = bfp ? 16 : 8;
   const int Kp = (K + kstep - 1) / kstep * kstep;
   const int64_t pitchA = ((int64_t)Kp * nterms + 63) / 64 * 64 + 64;
   const int64_t pitchB = (Kp + 63) / 64 * 64;
@@ -61,7 +62,7 @@ extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t 
   ck(cudaMalloc(&dA, A.size() * 8));
   ck(cudaMalloc(&dB, B.size() * 8));
   ck(cudaMalloc(&dC, (size_t)M * N * 8));
-  for (int h = 0; h < (prec == kTF32x3 ? 2 : 1); ++h) {
+  for (int h = 0; h < (split ? 2 : 1); ++h) {
     ck(cudaMalloc(&pa[h], rowsA * pitchA * eb));
     ck(cudaMalloc(&pb[h], rowsB * pitchB * eb));
     ck(cudaMemset(pa[h], 0, rowsA * pitchA * eb));
@@ -118,7 +119,7 @@ extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t 
     ck(cudaMemcpy(dterms, terms.data(), terms.size() * sizeof(TcTerm), cudaMemcpyHostToDevice));
     TcMaps maps;
     std::memset(&maps, 0, sizeof(maps));
-    for (int h = 0; h < (prec == kTF32x3 ? 2 : 1); ++h) {
+    for (int h = 0; h < (split ? 2 : 1); ++h) {
       if (!tc_encode_panel(&maps.a[h], eb, pa[h], pitchA, rowsA, 128)) rc = GBD_ERR_CUDA;
       for (int s = 0; s < 5; ++s)
         if (!tc_encode_panel(&maps.b[h][s], eb, pb[h], pitchB, rowsB, 16u << s)) rc = GBD_ERR_CUDA;
@@ -137,7 +138,7 @@ extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t 
     ck(cudaMemcpy(Ct.data(), dC, Ct.size() * 8, cudaMemcpyDeviceToHost));
     // decoded operands
     std::vector<double> Ad(A.size()), Bd(B.size());
-    if (prec == kTF32x3) {
+    if (split) {
       Ad = A;
       Bd = B;
     } else {

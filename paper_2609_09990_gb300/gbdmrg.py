@@ -52,9 +52,10 @@ class gbd_stats(C.Structure):
                 ("n_sigma_tc", C.c_int64), ("tier_iterations", C.c_int64 * 3),
                 ("max_final_residual", C.c_double), ("sum_final_residual", C.c_double),
                 ("graph_launches", C.c_int64), ("autotune_trials", C.c_int64), ("tc_gemm_ms", C.c_double),
-                ("tc_bytes", C.c_double), ("tc_flops_by_type", C.c_double * 3),
-                ("tc_gemm_ms_by_type", C.c_double * 3), ("tc_build_ms", C.c_double),
-                ("tc_build_phase_ms", C.c_double * 5)]
+                ("tc_bytes", C.c_double), ("tc_flops_by_type", C.c_double * 4),
+                ("tc_gemm_ms_by_type", C.c_double * 4), ("tc_build_ms", C.c_double),
+                ("tc_build_phase_ms", C.c_double * 5), ("enlarge_host_ms", C.c_double), ("diag_ms", C.c_double),
+                ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,6 +86,7 @@ def lib():
                                         C.POINTER(gbd_result)]),
         "gbd_set_batch_workers": (C.c_int, [vp, C.c_int32]),
         "gbd_set_graphs": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
         "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
         "gbd_probe_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
@@ -121,6 +123,7 @@ def lib():
                                         C.c_int64, C.POINTER(C.c_float), C.c_double, _dp, _dp]),
         "gbd_mlp_precond": (C.c_int, [vp, _dp, _dp, C.c_double, C.c_double, C.c_int64, _dp]),
         "gbd_davidson_counts": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "gbd_host_sym_eig": (C.c_int, [C.c_int32, _dp, _dp, _dp]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
         "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
                                       _dp]),
@@ -276,7 +279,7 @@ class Context:
         return (y, d) if want_diag else y
 
     def apply_heff_prec(self, k, x, prec):
-        """H_eff x through the tensor-core sigma (prec 1 TF32, 2 BF16, 3 TF32x3)."""
+        """H_eff x through the tensor-core sigma (prec 1 TF32, 2 BF16, 3 TF32x3, 4 BF16x3)."""
         x = np.ascontiguousarray(x, dtype=np.float64)
         y = np.zeros_like(x)
         self._check(self.L.gbd_apply_heff_prec(self.ptr, k, prec, _d(x), _d(y)), "gbd_apply_heff_prec")
@@ -287,6 +290,10 @@ class Context:
 
     def set_preconditioner(self, preconditioner):
         self._check(self.L.gbd_set_preconditioner(self.ptr, preconditioner), "gbd_set_preconditioner")
+
+    def set_accurate_tier(self, prec):
+        """3 = TF32x3 (default), 4 = BF16x3."""
+        self._check(self.L.gbd_set_accurate_tier(self.ptr, prec), "gbd_set_accurate_tier")
 
     def set_graphs(self, enable):
         self._check(self.L.gbd_set_graphs(self.ptr, 1 if enable else 0), "gbd_set_graphs")
@@ -395,6 +402,18 @@ class Context:
 
 
 # ---- host-only planner pieces
+def host_sym_eig(A):
+    """Host eigensolver of the decimation: (w ascending, Z columns = eigenvectors)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    Z = np.zeros((n, n))
+    rc = lib().gbd_host_sym_eig(n, _d(A), _d(w), _d(Z))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_sym_eig: {ERRORS.get(rc, rc)}")
+    return w, Z
+
+
 def host_initial_dims(n, n_alpha, n_beta, M):
     L = lib()
     ns = np.zeros(n + 1, dtype=np.int32)

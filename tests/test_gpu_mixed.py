@@ -14,8 +14,9 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 # relative bounds of ||sigma_tc - sigma_oracle|| / ||sigma_oracle||: BF16 inputs
-# 2^-9 rounding, TF32 2^-12, TF32x3 ~2^-21 plus FP32 accumulation
-BOUNDS = {1: 3e-3, 2: 2e-2, 3: 2e-5}
+# 2^-9 rounding, TF32 2^-12, TF32x3 ~2^-21 and BF16x3 ~2^-16 split errors
+# plus FP32 accumulation
+BOUNDS = {1: 3e-3, 2: 2e-2, 3: 2e-5, 4: 5e-5}
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +74,7 @@ def test_tile_shape_does_not_change_sigma(G):
     for k in range(3):
         ctx.run_step(k, 0, 64, 1e-6)
     x = np.random.default_rng(5).standard_normal(ctx.two_site_size(3))
-    for prec in (2, 3):
+    for prec in (2, 3, 4):
         ys = []
         for cap in (256, 128, 64):
             ctx.set_tc_tile(cap)

@@ -103,3 +103,28 @@ def test_selection_rule_matches_oracle(G):
         idx, tot = G.host_select(lam, key, jj, M)
         assert [w[i] for i in idx] == kept
         assert abs((tot - sum(w[i][0] for i in idx)) - tau) < 1e-14
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 7, 60, 150])
+def test_host_eigensolver_against_lapack(G, n):
+    # density-matrix-like inputs: PSD, rank deficient, eigenvalues spanning
+    # many decades, plus an exactly degenerate pair
+    rng = np.random.default_rng(n + 3)
+    if n == 0:
+        w, Z = G.host_sym_eig(np.zeros((0, 0)))
+        assert w.size == 0
+        return
+    X = rng.standard_normal((n, max(n // 2, 1))) * np.exp(-np.arange(max(n // 2, 1)) / 4.0)
+    A = X @ X.T
+    if n >= 7:
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = np.sort(np.concatenate([[2.0, 2.0], np.exp(-np.arange(n - 2) / 3.0)]))
+        A = (Q * lam) @ Q.T + A * 1e-3
+    A = 0.5 * (A + A.T)
+    w, Z = G.host_sym_eig(A)
+    ref = np.linalg.eigvalsh(A)
+    scale = max(np.abs(ref).max(), 1e-300)
+    assert np.all(np.diff(w) >= -1e-15 * scale)
+    assert np.abs(w - ref).max() <= 1e-13 * scale
+    assert np.abs(A @ Z - Z * w).max() <= 1e-13 * scale
+    assert np.abs(Z.T @ Z - np.eye(n)).max() <= 1e-12
