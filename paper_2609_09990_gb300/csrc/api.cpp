@@ -227,6 +227,7 @@ int gbd_solve_batched(gbd_ctx* ctx, int32_t n, const gbd_problem* problems, cons
       }
     };
     auto worker = [&]() {
+      gbd::set_host_threads(std::max(1, hw / nw));   // the workers share the host cores
       std::unique_ptr<gbd::Engine> eng;
       try {
         eng.reset(new gbd::Engine(ctx->device));
@@ -262,6 +263,7 @@ int gbd_solve_batched(gbd_ctx* ctx, int32_t n, const gbd_problem* problems, cons
       // fewer threads than asked for: the started ones and this one share the queue
     }
     worker();
+    gbd::set_host_threads(0);   // this thread ran a worker too
     for (auto& t : pool) t.join();
     if (first_bad < n) return fail(ctx, results[first_bad].status, first_msg);
     return GBD_OK;

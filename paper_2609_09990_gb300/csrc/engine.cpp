@@ -72,8 +72,11 @@ double binom(int n, int k) {
   return std::round(r);
 }
 
+thread_local int t_host_threads = 0;   // 0: min(hardware threads, 16)
+
 void parallel_for(int n, const std::function<void(int)>& f) {
   int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+  if (t_host_threads > 0) nt = std::min(nt, t_host_threads);
   if (n < 2 || nt < 2) {
     for (int i = 0; i < n; ++i) f(i);
     return;
@@ -88,6 +91,8 @@ void parallel_for(int n, const std::function<void(int)>& f) {
 }
 
 }  // namespace
+
+void set_host_threads(int n) { t_host_threads = n; }
 
 // counter-based initial-MPS value (same published definition as the input
 // generator: splitmix64 finalizer on a derived seed and an element key)
@@ -490,6 +495,36 @@ struct Buckets {
 };
 }  // namespace
 
+namespace {
+// The share of one channel b of an enlarged operator, built by one host
+// thread: sub-blocks with owned offsets and axpy outputs relative to the
+// share; merge_parts concatenates the shares in b order (the serial layout).
+struct EnlPart {
+  std::vector<EnlSub> subs;
+  std::vector<AxpyTerm> terms;
+  std::vector<AxpyOut> outs;
+  int64_t own = 0;
+};
+void merge_parts(std::vector<EnlPart>& parts, EnlOp& op, AxpyPlan& ax) {
+  for (EnlPart& P : parts) {
+    const int64_t ob = op.own_size;
+    const int tb = (int)ax.terms.size();
+    for (EnlSub s : P.subs) {
+      if (s.own_off >= 0) s.own_off += ob;
+      op.subs.push_back(s);
+    }
+    for (AxpyOut o : P.outs) {
+      o.dst = (double*)((intptr_t)o.dst + ob);   // element offsets until finish_enl
+      o.t0 += tb;
+      o.t1 += tb;
+      ax.outs.push_back(o);
+    }
+    ax.terms.insert(ax.terms.end(), P.terms.begin(), P.terms.end());
+    op.own_size += P.own;
+  }
+}
+}  // namespace
+
 // Lenl[b] over E_L(Q) (Q in el), from L_k and W_k.  Sub-block (b, Qin, sin,
 // sout) maps rows (q_l, sin) of E_L(Qin) to rows (q_l', sout) of E_L(Qout):
 //   sum_a W_k[a,b](sout, sin) L_k[a](q_l' <- q_l).
@@ -503,15 +538,23 @@ void Engine::build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPl
   op.subs.clear();
   op.own_size = 0;
   const int ns = bk.nsec();
-  std::vector<int64_t> combo(16 * (size_t)ns);
-  size_t e0 = 0;
-  while (e0 < W.size()) {
-    const int b = W[e0].b;
+  // runs of W_k entries with the same right channel b
+  std::vector<std::pair<size_t, size_t>> runs;
+  for (size_t e0 = 0; e0 < W.size();) {
     size_t e1 = e0;
+    while (e1 < W.size() && W[e1].b == W[e0].b) ++e1;
+    runs.push_back({e0, e1});
+    e0 = e1;
+  }
+  std::vector<EnlPart> parts(runs.size());
+  parallel_for((int)runs.size(), [&](int u) {
+    EnlPart& P = parts[u];
+    const size_t e0 = runs[u].first, e1 = runs[u].second;
+    const int b = W[e0].b;
     Buckets B;
-    for (; e1 < W.size() && W[e1].b == b; ++e1) B.lst[W[e1].sout * 4 + W[e1].sin].push_back({W[e1].a, W[e1].v});
+    for (size_t e = e0; e < e1; ++e) B.lst[W[e].sout * 4 + W[e].sin].push_back({W[e].a, W[e].v});
     B.classify();
-    std::fill(combo.begin(), combo.end(), -1);
+    std::vector<int64_t> combo(16 * (size_t)ns, -1);
     for (int p = 0; p < 16; ++p) {
       const auto& lst = B.lst[p];
       if (lst.empty()) continue;
@@ -535,21 +578,21 @@ void Engine::build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPl
           int64_t& off = combo[(size_t)r * ns + il];
           if (off < 0) {
             const int64_t len = (int64_t)sub.rows * sub.cols;
-            off = op.own_size;
-            AxpyOut o{(double*)(intptr_t)off, len, (int)ax.terms.size(), 0};
-            for (auto& t : B.lst[r]) ax.terms.push_back({Lk.d + Lk.at(t.first, il), t.second});
-            o.t1 = (int)ax.terms.size();
-            ax.outs.push_back(o);
-            op.own_size += len;
+            off = P.own;
+            AxpyOut o{(double*)(intptr_t)off, len, (int)P.terms.size(), 0};
+            for (auto& t : B.lst[r]) P.terms.push_back({Lk.d + Lk.at(t.first, il), t.second});
+            o.t1 = (int)P.terms.size();
+            P.outs.push_back(o);
+            P.own += len;
           }
           sub.own_off = off;
           sub.sign = B.ratio[p];
         }
-        op.subs.push_back(sub);
+        P.subs.push_back(sub);
       }
     }
-    e0 = e1;
-  }
+  });
+  merge_parts(parts, op, ax);
 }
 
 // Renl[b] over E_R(Q) (Q in er), from R_{i+1} and W_i (i = site).  Sub-block
@@ -564,13 +607,17 @@ void Engine::build_renl(int i, const Env& R, const Space& er, EnlOp& op, AxpyPla
   // entries of W_i grouped by their left channel (called b here)
   std::vector<std::vector<const MpoEntry*>> bya(mpo.labels[i].size());
   for (const auto& e : W) bya[e.a].push_back(&e);
-  std::vector<int64_t> combo(16 * (size_t)ns);
-  for (int b = 0; b < (int)bya.size(); ++b) {
-    if (bya[b].empty()) continue;
+  std::vector<int> units;
+  for (int b = 0; b < (int)bya.size(); ++b)
+    if (!bya[b].empty()) units.push_back(b);
+  std::vector<EnlPart> parts(units.size());
+  parallel_for((int)units.size(), [&](int u) {
+    EnlPart& P = parts[u];
+    const int b = units[u];
     Buckets B;
     for (const MpoEntry* e : bya[b]) B.lst[e->sout * 4 + e->sin].push_back({e->b, e->v});
     B.classify();
-    std::fill(combo.begin(), combo.end(), -1);
+    std::vector<int64_t> combo(16 * (size_t)ns, -1);
     for (int p = 0; p < 16; ++p) {
       const auto& lst = B.lst[p];
       if (lst.empty()) continue;
@@ -594,20 +641,21 @@ void Engine::build_renl(int i, const Env& R, const Space& er, EnlOp& op, AxpyPla
           int64_t& off = combo[(size_t)r * ns + ir];
           if (off < 0) {
             const int64_t len = (int64_t)sub.rows * sub.cols;
-            off = op.own_size;
-            AxpyOut o{(double*)(intptr_t)off, len, (int)ax.terms.size(), 0};
-            for (auto& t : B.lst[r]) ax.terms.push_back({R.d + R.at(t.first, ir), t.second});
-            o.t1 = (int)ax.terms.size();
-            ax.outs.push_back(o);
-            op.own_size += len;
+            off = P.own;
+            AxpyOut o{(double*)(intptr_t)off, len, (int)P.terms.size(), 0};
+            for (auto& t : B.lst[r]) P.terms.push_back({R.d + R.at(t.first, ir), t.second});
+            o.t1 = (int)P.terms.size();
+            P.outs.push_back(o);
+            P.own += len;
           }
           sub.own_off = off;
           sub.sign = B.ratio[p];
         }
-        op.subs.push_back(sub);
+        P.subs.push_back(sub);
       }
     }
-  }
+  });
+  merge_parts(parts, op, ax);
 }
 
 void Engine::finish_enl(EnlOp& op, AxpyPlan& ax) {

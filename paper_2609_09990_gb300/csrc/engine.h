@@ -118,6 +118,8 @@ struct Schedule {
 
 struct TcPlan;
 double now_ms();   // steady-clock wall time
+// host threads of the engine's parallel loops on the calling thread (0 = default)
+void set_host_threads(int n);
 
 struct TcTune {     // numerics-neutral tile shape of the tensor-core sigma
   int ncap[2] = {256, 256};   // largest N tile of stage A and of stage B (64, 128, 256)
