@@ -138,6 +138,7 @@ def run_ours(args, rank, world):
     breakdown = {k: (st1[k] - st0[k]) / args.steps for k in keys}
     breakdown["sigma_builds"] = (st1["n_sigma"] - st0["n_sigma"]) / args.steps
     breakdown["tc_sigma_builds"] = (st1["n_sigma_tc"] - st0["n_sigma_tc"]) / args.steps
+    breakdown["env_gflop"] = (st1["env_flops"] - st0["env_flops"]) / args.steps / 1e9
     breakdown["tc_build_phase_ms"] = {
         nm: (st1["tc_build_phase_ms"][i] - st0["tc_build_phase_ms"][i]) / args.steps
         for i, nm in enumerate(["layout_groups", "panels", "tiles", "upload", "maps"])}

@@ -23,6 +23,10 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <mutex>
+#include <memory>
+#include <deque>
+#include <condition_variable>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -74,6 +78,88 @@ double binom(int n, int k) {
 
 thread_local int t_host_threads = 0;   // 0: min(hardware threads, 16)
 
+// Persistent host worker pool shared by every engine in the process: a
+// parallel_for call posts one job (a loop body and an index counter); the
+// workers and the calling thread take indices until none is left, and the
+// caller returns when every taken index has finished.  Several callers
+// (batched engines) may post jobs at the same time.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool;
+    return pool;
+  }
+  int size() const { return (int)workers_.size(); }
+  void run(int n, int width, const std::function<void(int)>& f) {
+    auto job = std::make_shared<Job>();
+    job->f = &f;
+    job->n = n;
+    job->slots = width - 1;   // workers that may join besides the caller
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      jobs_.push_back(job);
+    }
+    cv_.notify_all();
+    work(*job);
+    std::unique_lock<std::mutex> g(job->mu);
+    job->cv.wait(g, [&]() { return job->done == job->n; });
+  }
+
+ private:
+  struct Job {
+    const std::function<void(int)>* f = nullptr;
+    int n = 0;
+    std::atomic<int> next{0}, slots{0};
+    int done = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+  };
+  HostPool() {
+    const int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u) - 1;
+    for (int t = 0; t < nt; ++t)
+      workers_.emplace_back([this]() {
+        for (;;) {
+          std::shared_ptr<Job> job;
+          {
+            std::unique_lock<std::mutex> g(mu_);
+            cv_.wait(g, [&]() { return stop_ || !jobs_.empty(); });
+            if (stop_) return;
+            job = jobs_.front();
+            // a job leaves the queue once all its indices are taken or it
+            // has no worker slots left
+            if (job->next.load() >= job->n || --job->slots <= 0) jobs_.pop_front();
+          }
+          work(*job);
+        }
+      });
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& w : workers_) w.join();
+  }
+  static void work(Job& job) {
+    int finished = 0;
+    for (int i = job.next++; i < job.n; i = job.next++) {
+      (*job.f)(i);
+      ++finished;
+    }
+    if (finished) {
+      std::lock_guard<std::mutex> g(job.mu);
+      job.done += finished;
+      if (job.done == job.n) job.cv.notify_all();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::deque<std::shared_ptr<Job>> jobs_;
+  std::mutex mu_;
+  std::condition_variable cv_;
+  bool stop_ = false;
+};
+
 void parallel_for(int n, const std::function<void(int)>& f) {
   int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
   if (t_host_threads > 0) nt = std::min(nt, t_host_threads);
@@ -81,13 +167,7 @@ void parallel_for(int n, const std::function<void(int)>& f) {
     for (int i = 0; i < n; ++i) f(i);
     return;
   }
-  std::atomic<int> next(0);
-  std::vector<std::thread> th;
-  for (int t = 0; t < std::min(nt, n); ++t)
-    th.emplace_back([&]() {
-      for (int i = next++; i < n; i = next++) f(i);
-    });
-  for (auto& x : th) x.join();
+  HostPool::get().run(n, std::min(nt, n), f);
 }
 
 }  // namespace

@@ -377,6 +377,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           T.out = psi_off[q] + (int64_t)(EL.soff[q][so] + n0) * ER.dim[q];
           P->flops_exec += 2.0 * 128 * T.n_mma * (double)ksum;
           tiles.push_back(T);
+          // order: (q, m0, chunk, so, n0): the s_out blocks and n-tiles of
+          // one (q, m0, chunk) read the same Y^T boxes and run together
           bkey.push_back({q, m0, 0, so, n0});   // chunk index filled by the split
         }
     }
