@@ -37,6 +37,13 @@ sys.path.insert(0, ROOT)
 from gbd_synth import WORKLOADS, make_integrals  # noqa: E402
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+# DRAM bytes (read + write, ncu) per algorithmic byte of tc_gemm_kernel, from
+# one --set full capture of `bench.py --sigma-probe 3` (TF32x3 sigma at the
+# central bond of cas16_m512: stage A 443 + 301 MB, stage B 1154 + 21 MB, for
+# 731 MB of algorithmic bytes).  The launches of a sweep move the same kinds
+# of panels, so traffic is reported as this ratio times their algorithmic
+# bytes per launch.
+TC_DRAM_PER_ALG_BYTE = (443.268e6 + 301.2224e6 + 1154.182e6 + 20.782336e6) / 730948448.0
 DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
 
 
@@ -134,7 +141,7 @@ def run_ours(args, rank, world):
     st1 = ctx.stats()
     dt = t1 - t0
     keys = ["sigma_ms", "tc_ms", "tc_gemm_ms", "tc_build_ms", "env_ms", "enlarge_ms", "enlarge_host_ms", "diag_ms",
-            "davidson_ms", "truncate_ms", "truncate_rho_ms", "truncate_eig_ms", "step_ms"]
+            "davidson_ms", "truncate_ms", "truncate_rho_ms", "truncate_eig_ms", "env_wall_ms", "step_ms"]
     breakdown = {k: (st1[k] - st0[k]) / args.steps for k in keys}
     breakdown["sigma_builds"] = (st1["n_sigma"] - st0["n_sigma"]) / args.steps
     breakdown["tc_sigma_builds"] = (st1["n_sigma_tc"] - st0["n_sigma_tc"]) / args.steps
@@ -462,6 +469,11 @@ def main():
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak if peak else 0.0,
             "traffic": None, "kernel": kname, "peak_kind": kind}
     if args.precision != "fp64":
+        nl = res["breakdown"]["tc_sigma_builds"] * 2 * args.steps   # two tc_gemm_kernel launches per sigma
+        if args.tier2 == "tf32x3" and nl > 0:
+            roof["traffic"] = TC_DRAM_PER_ALG_BYTE * res["tc"]["tc_bytes"] / nl
+            roof["traffic_note"] = ("bytes per launch: ncu DRAM/algorithmic ratio %.2f measured at the central bond, "
+                                    "times the timed launches' algorithmic bytes" % TC_DRAM_PER_ALG_BYTE)
         roof["other_view"] = alt_v
         roof["tc_gemm_ms_per_sweep"] = res["tc"]["tc_gemm_ms"] / args.steps
         roof["launches_per_sweep"] = res["breakdown"]["tc_sigma_builds"] * 2

@@ -49,6 +49,7 @@ typedef struct {
   double enlarge_host_ms;       /* host part of enlarge_ms (sub-block lists, before the device axpy) */
   double diag_ms;               /* H_eff diagonal (wall) */
   double truncate_rho_ms, truncate_eig_ms;   /* decimation: density matrices to the host; eigensolves */
+  double env_wall_ms;           /* environment updates, wall time incl. plan upload (env_ms: kernels only) */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or

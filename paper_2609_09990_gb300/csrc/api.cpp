@@ -603,6 +603,7 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->diag_ms = t.diag_ms;
   s->truncate_rho_ms = t.trunc_rho_ms;
   s->truncate_eig_ms = t.trunc_eig_ms;
+  s->env_wall_ms = t.env_wall_ms;
   for (int i = 0; i < 5; ++i) s->tc_build_phase_ms[i] = t.tcb_ms[i];
   for (int i = 0; i < 4; ++i) {
     s->tc_flops_by_type[i] = t.tc_flops_p[i];

@@ -320,6 +320,7 @@ Engine::~Engine() {
 void Engine::dfree(void* p) {
   if (!p) return;
   allocs.erase((uintptr_t)p);
+  if ((uintptr_t)p == chk_base) chk_size = 0;   // the cached allocation is gone
   CK(cudaFreeAsync(p, stream));
 }
 
@@ -330,11 +331,15 @@ void Engine::check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, 
   if (rows > 1 && ld < cols) throw Error(-6, std::string("plan check: leading dimension too small for ") + what);
   uintptr_t a = (uintptr_t)p;
   uintptr_t end = a + (uintptr_t)(((rows - 1) * ld + cols) * (int64_t)sizeof(double));
+  // consecutive checks mostly fall in the same allocation
+  if (chk_size && a >= chk_base && end <= chk_base + chk_size) return;
   auto it = allocs.upper_bound(a);
   if (it == allocs.begin()) throw Error(-6, std::string("plan check: pointer outside allocations: ") + what);
   --it;
   if (a < it->first || end > it->first + it->second)
     throw Error(-6, std::string("plan check: block exceeds its allocation: ") + what);
+  chk_base = it->first;
+  chk_size = it->second;
 }
 
 void Engine::check(const GemmPlan& p) const {
@@ -816,9 +821,10 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
     p2.add_out(out.d + eo, nin, nout, nin, 0);
     p2.add_term(A.d + A.off[tb.nout], nout, T + tb.off, nin, el.dim[tb.qout], 1, 1.0);
   }
-  CK(cudaEventRecord(ev0, stream));
+  const double th0 = now_ms();
   upload(p1);
   upload(p2);
+  CK(cudaEventRecord(ev0, stream));
   run(p1);
   run(p2);
   CK(cudaEventRecord(ev1, stream));
@@ -826,6 +832,7 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, ev0, ev1));
   stats.env_ms += ms;
+  stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
   release(p1);
   release(p2);
@@ -871,9 +878,10 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
     p2.add_out(out.d + eo, nin, nout, nin, 0);
     p2.add_term(B.d + B.off[tb.nout], er.dim[tb.qout], T + tb.off, nin, er.dim[tb.qout], 0, 1.0);
   }
-  CK(cudaEventRecord(ev0, stream));
+  const double th0 = now_ms();
   upload(p1);
   upload(p2);
+  CK(cudaEventRecord(ev0, stream));
   run(p1);
   run(p2);
   CK(cudaEventRecord(ev1, stream));
@@ -881,6 +889,7 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, ev0, ev1));
   stats.env_ms += ms;
+  stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
   release(p1);
   release(p2);

@@ -88,6 +88,7 @@ struct Stats {
   double tc_build_ms = 0;   // host wall time building tensor-core plans (incl. autotuning)
   double enl_host_ms = 0, diag_ms = 0;   // host part of the enlarged operators; the H_eff diagonal
   double trunc_rho_ms = 0, trunc_eig_ms = 0;   // decimation: density matrices to the host; host eigensolves
+  double env_wall_ms = 0;   // environment update: upload (plan checks) + kernels, wall
   double tcb_ms[5] = {0, 0, 0, 0, 0};   // plan-build phases: layout/groups, panels, tiles, upload, maps
   void add(const Stats& o) {   // sum of the additive counters (batched solves)
     sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
@@ -100,7 +101,7 @@ struct Stats {
     sum_final_residual += o.sum_final_residual;
     graph_launches += o.graph_launches; autotune_trials += o.autotune_trials;
     tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms; enl_host_ms += o.enl_host_ms; diag_ms += o.diag_ms;
-    trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms;
+    trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms; env_wall_ms += o.env_wall_ms;
     for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
     for (int i = 0; i < 4; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
     max_discarded = std::max(max_discarded, o.max_discarded);
@@ -202,6 +203,8 @@ class Engine {
   double* psi = nullptr;
 
   std::map<uintptr_t, size_t> allocs;   // live device allocations (base -> bytes)
+  mutable uintptr_t chk_base = 0;       // last allocation a range check matched
+  mutable size_t chk_size = 0;
   int num_sms = 152;
   template <class T>
   T* dalloc(size_t n) {

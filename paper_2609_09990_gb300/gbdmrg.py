@@ -55,7 +55,7 @@ class gbd_stats(C.Structure):
                 ("tc_bytes", C.c_double), ("tc_flops_by_type", C.c_double * 4),
                 ("tc_gemm_ms_by_type", C.c_double * 4), ("tc_build_ms", C.c_double),
                 ("tc_build_phase_ms", C.c_double * 5), ("enlarge_host_ms", C.c_double), ("diag_ms", C.c_double),
-                ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double)]
+                ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double), ("env_wall_ms", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
