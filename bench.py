@@ -39,11 +39,11 @@ from gbd_synth import WORKLOADS, make_integrals  # noqa: E402
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 # DRAM bytes (read + write, ncu) per algorithmic byte of tc_gemm_kernel, from
 # one --set full capture of `bench.py --sigma-probe 3` (TF32x3 sigma at the
-# central bond of cas16_m512: stage A 443 + 301 MB, stage B 1154 + 21 MB, for
+# central bond of cas16_m512: stage A 518 + 300 MB, stage B 1149 + 21 MB, for
 # 731 MB of algorithmic bytes).  The launches of a sweep move the same kinds
 # of panels, so traffic is reported as this ratio times their algorithmic
 # bytes per launch.
-TC_DRAM_PER_ALG_BYTE = (443.268e6 + 301.2224e6 + 1154.182e6 + 20.782336e6) / 730948448.0
+TC_DRAM_PER_ALG_BYTE = (518.48e6 + 300.25472e6 + 1148.62e6 + 20.875264e6) / 730948448.0
 DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
 
 

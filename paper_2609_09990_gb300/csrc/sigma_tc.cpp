@@ -148,27 +148,39 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   //      and the same set of input local states si, stacked over b (rows
   //      m(so) per b), one 16-aligned column section per si.  Every stacked
   //      row is one row of Y^T, so a 128-row A box covers many channels b.
+  //      The B operand (psi rows of qin) and the column sections depend on
+  //      (qin, set of si) only, so members with different (qout, so) share
+  //      a group; the row map sends each stacked row to its own Y^T row.
   struct AGroup {
-    int qin, qout, so, mask;
-    std::vector<std::array<int, 4>> mem;   // per b: sub index for each si (-1: none)
-    std::vector<int> b;
-    int64_t row0 = 0;
+    int qin, mask;
+    std::vector<std::array<int, 4>> mem;   // per member: sub index for each si (-1: none)
+    std::vector<int> b, qout, so;
+    std::vector<int64_t> roff;             // first stacked row of each member (from row0)
+    int64_t rows = 0, row0 = 0;
     std::array<int, 4> col{};
   };
   std::vector<AGroup> groups;
   std::vector<int64_t> rowmap;
   int64_t rs_rows = 0, rs_width = 0;
   {
-    // (b, qin, so) -> subs per si
-    std::vector<std::array<int, 4>> bso((size_t)nb * nq * 4, std::array<int, 4>{-1, -1, -1, -1});
+    // (b, qin) with a Y block -> compact index; (that index, so) -> subs per si
+    std::vector<int> bq_of((size_t)nb * nq, -1);
+    int nbq = 0;
+    for (size_t bq = 0; bq < ybase.size(); ++bq)
+      if (ybase[bq] >= 0) bq_of[bq] = nbq++;
+    std::vector<std::array<int, 4>> bso((size_t)nbq * 4, std::array<int, 4>{-1, -1, -1, -1});
+    std::vector<int> bq_key((size_t)nbq);
+    for (size_t bq = 0; bq < ybase.size(); ++bq)
+      if (bq_of[bq] >= 0) bq_key[bq_of[bq]] = (int)bq;
     for (size_t i = 0; i < renl.subs.size(); ++i) {
       const EnlSub& s = renl.subs[i];
-      if (ybase[(size_t)s.b * nq + s.qin] < 0) continue;
-      int& slot = bso[((size_t)s.b * nq + s.qin) * 4 + s.sout][s.sin];
+      const int c = bq_of[(size_t)s.b * nq + s.qin];
+      if (c < 0) continue;
+      int& slot = bso[(size_t)c * 4 + s.sout][s.sin];
       if (slot >= 0) throw Error(-3, "duplicate enlarged-operator sub-block");
       slot = (int)i;
     }
-    std::vector<int> gidx((size_t)nq * nq * 4 * 16, -1);   // (qin, qout, so, mask) -> group
+    std::vector<int> gidx((size_t)nq * 16, -1);   // (qin, mask) -> group
     for (size_t key = 0; key < bso.size(); ++key) {
       const std::array<int, 4>& m = bso[key];
       int mask = 0, any = -1;
@@ -178,18 +190,26 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           any = m[si];
         }
       if (!mask) continue;
-      const int so = (int)(key % 4), qin = (int)((key / 4) % nq), b = (int)(key / 4 / nq);
+      const int so = (int)(key % 4), bq = bq_key[key / 4];
+      const int qin = bq % nq, b = bq / nq;
       const int qout = renl.subs[any].qout;
-      int& g = gidx[(((size_t)qin * nq + qout) * 4 + so) * 16 + mask];
+      int& g = gidx[(size_t)qin * 16 + mask];
       if (g < 0) {
         g = (int)groups.size();
-        groups.push_back(AGroup{qin, qout, so, mask, {}, {}, 0, {}});
+        AGroup ng;
+        ng.qin = qin;
+        ng.mask = mask;
+        groups.push_back(ng);
       }
-      groups[g].mem.push_back(m);
-      groups[g].b.push_back(b);
+      AGroup& G = groups[g];
+      G.mem.push_back(m);
+      G.b.push_back(b);
+      G.qout.push_back(qout);
+      G.so.push_back(so);
+      G.roff.push_back(G.rows);
+      G.rows += ER.sdim[qout][so];
     }
     for (AGroup& g : groups) {
-      const int mso = ER.sdim[g.qout][g.so];
       g.row0 = rs_rows;
       int64_t w = 0;
       for (int si = 0; si < 4; ++si) {
@@ -198,10 +218,11 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       }
       rs_width = std::max(rs_width, w);
       for (size_t bi = 0; bi < g.b.size(); ++bi) {
-        const int64_t y0 = ybase[(size_t)g.b[bi] * nq + g.qin] + ER.soff[g.qout][g.so];
+        const int mso = ER.sdim[g.qout[bi]][g.so[bi]];
+        const int64_t y0 = ybase[(size_t)g.b[bi] * nq + g.qin] + ER.soff[g.qout[bi]][g.so[bi]];
         for (int r = 0; r < mso; ++r) rowmap.push_back(y0 + r);
       }
-      rs_rows += (int64_t)g.b.size() * mso;
+      rs_rows += g.rows;
     }
   }
   P->rs_pitch = up64(rs_width);
@@ -239,16 +260,14 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   };
   {
     std::vector<int64_t> r0(renl.subs.size(), -1), c0(renl.subs.size(), 0);
-    for (const AGroup& g : groups) {
-      const int mso = ER.sdim[g.qout][g.so];
+    for (const AGroup& g : groups)
       for (size_t bi = 0; bi < g.b.size(); ++bi)
         for (int si = 0; si < 4; ++si) {
           const int i = g.mem[bi][si];
           if (i < 0) continue;
-          r0[i] = g.row0 + (int64_t)bi * mso;
+          r0[i] = g.row0 + g.roff[bi];
           c0[i] = g.col[si];
         }
-    }
     convert(renl, r0, c0, P->rs, P->rs_pitch);
   }
   convert(lenl, ls_row, std::vector<int64_t>(lenl.subs.size(), 0), P->ls, P->ls_pitch);
@@ -265,14 +284,15 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   std::vector<TcTile> tiles;
   std::vector<TcTerm> terms;
   for (const AGroup& g : groups) {
-    const int mso = ER.sdim[g.qout][g.so];
-    const int64_t grows = (int64_t)g.b.size() * mso;
-    for (size_t bi = 0; bi < g.b.size(); ++bi)
+    const int64_t grows = g.rows;
+    for (size_t bi = 0; bi < g.b.size(); ++bi) {
+      const int mso = ER.sdim[g.qout[bi]][g.so[bi]];
       for (int si = 0; si < 4; ++si)
         if (g.mem[bi][si] >= 0) {
           P->flops_alg += 2.0 * EL.dim[g.qin] * mso * ER.sdim[g.qin][si];
           P->bytes_alg += (double)P->eb * nh * mso * ER.sdim[g.qin][si];           // Renl sub-block
         }
+    }
     P->bytes_alg += 2.0 * P->eb * nh * grows * EL.dim[g.qin];                     // Y^T write + read
     // one term list per group, shared by its tiles
     const int gt0 = (int)terms.size();
