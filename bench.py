@@ -4,20 +4,29 @@ Workload: CAS(16e,16o), S_z = 0, synthetic integrals (gbd_synth, seed 3,
 48 Cholesky vectors), bond dimension M = 512.  One "step" is one full
 two-site sweep (left-to-right and back, 30 two-site steps: H_eff diagonal,
 Davidson with sigma builds, decimation, environment updates), with the state
-resident on the device when the timed region starts.
+resident on the device when the timed region starts.  Default precision:
+the reduced-precision tiers (BF16 tier 1, skipped in warm sweeps; TF32x3
+tier 2 with split-K FP64 sums; FP64 everywhere else); --precision fp64 runs
+the plain FP64 path.
 
-value  = algorithmic sigma-build flops of the timed sweeps / wall time of
-         the timed sweeps (TFLOP/s, whole job: everything in the sweep counts
-         in the denominator).
-e2e    = the same metric through gbd_solve (host integrals in, energies out;
-         initial state, sweeps and final energy inside the timed call).
-roofline = the grouped block-GEMM of the sigma build: algorithmic flops over
-         its CUDA-event device time.
+value    = algorithmic sigma-build flops of the timed sweeps / wall time of
+           the timed sweeps (TFLOP/s, whole job: everything in the sweep
+           counts in the denominator); sweep_time_s = wall time per sweep.
+fp64_gpu_sweep_s = one further sweep of the FP64 path from the same state.
+per_step_energy_error_vs_fp64 = the same two-site problems solved by FP64
+           Davidson and by the mixed tiers (FP64 Rayleigh quotients).
+e2e      = the same metric through gbd_solve (host integrals in, energies
+           out; initial state, sweeps and final energy inside the timed call).
+roofline = tc_gemm_kernel (FP64 path: gemm_f64_kernel), CUDA events around
+           its launches on the engine stream; tensor and HBM views.
 cpu_baseline = the CPU oracle on a bounded sample: one sigma build at the
-         central bond pair (7,8) of the same problem (initial MPS at M=512).
+           central bond pair (7,8) of the same problem (initial MPS at M=512).
 
 Multi-GPU: independent replicas (one problem per rank, seed 3 + rank), no
 collective on the data path; value sums the ranks' flops over the max time.
+Other modes: --workload batched64 (64 independent active spaces through
+gbd_solve_batched), --sigma-probe P (profiling driver, no bench line),
+--impl reference (the oracle, timed on the host cores).
 """
 import argparse
 import json
