@@ -69,6 +69,11 @@ int gbd_set_preconditioner(gbd_ctx *ctx, int32_t preconditioner);
  * 3 = TF32x3 (default), 4 = BF16x3 (the codes of gbd_apply_heff_prec). */
 int gbd_set_accurate_tier(gbd_ctx *ctx, int32_t prec);
 
+/* Reduced-precision schedules solve steps whose two-site state has fewer
+ * than n elements (chain ends) in FP64: there the tensor-core plan costs
+ * more than it saves.  Default 4096; 0 = always the tensor-core tiers. */
+int gbd_set_tc_min_two_site(gbd_ctx *ctx, int64_t n);
+
 /* One Davidson solve at the current centre k (environments k and k+2
  * valid, as after gbd_init_state for k = 0 or after steps up to k-1) in
  * schedule precision `precision` (GBD_FP64/TF32/BF16) with at most

@@ -309,6 +309,15 @@ int gbd_set_accurate_tier(gbd_ctx* ctx, int32_t prec) {
   });
 }
 
+int gbd_set_tc_min_two_site(gbd_ctx* ctx, int64_t n) {
+  return guarded(ctx, [&]() {
+    if (n < 0) return fail(ctx, GBD_ERR_ARG, "n < 0");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tc_min_two_site = n;
+    return GBD_OK;
+  });
+}
+
 int gbd_probe_step(gbd_ctx* ctx, int32_t k, int32_t precision, int32_t fp64_refine, double tol, double* theta,
                    double* e64, double* r64) {
   return guarded(ctx, [&]() {

@@ -369,10 +369,21 @@ void Engine::upload(GemmPlan& p) {
   check(p);
   p.d_terms = dalloc<GemmTerm>(p.terms.size());
   p.d_outs = dalloc<GemmOut>(p.outs.size());
-  // tiles: 32 x 32 outputs
+  // tiles: 32 x 32 outputs, or, where 32 x 32 tiles would leave more than
+  // a quarter of their elements idle (sector blocks of a few tens), flat
+  // items of 256 elements with one thread per element.  GB300's FP64 pipe
+  // is slow enough that the unblocked loop keeps it busy, and both kernels
+  // run the same FMA sequence per element.
   p.tiles.clear();
+  p.flat.clear();
   for (int o = 0; o < (int)p.outs.size(); ++o) {
     const GemmOut& g = p.outs[o];
+    const int64_t elems = (int64_t)g.M * g.N;
+    const int64_t padded = (int64_t)((g.M + 31) / 32 * 32) * ((g.N + 31) / 32 * 32);
+    if (elems > 0 && 4 * elems < 3 * padded) {
+      for (int64_t e0 = 0; e0 < elems; e0 += 256) p.flat.push_back({o, -1, (int32_t)e0, 0});
+      continue;
+    }
     for (int tm = 0; tm * 32 < g.M; ++tm)
       for (int tn = 0; tn * 32 < g.N; ++tn) p.tiles.push_back({o, tm, tn, 0});
   }
@@ -382,7 +393,15 @@ void Engine::upload(GemmPlan& p) {
     const GemmOut& y = p.outs[b.out];
     return (x.t1 - x.t0) > (y.t1 - y.t0);
   });
-  p.d_tiles = dalloc<GemmTile>(p.tiles.size());
+  std::stable_sort(p.flat.begin(), p.flat.end(), [&](const GemmTile& a, const GemmTile& b) {
+    const GemmOut& x = p.outs[a.out];
+    const GemmOut& y = p.outs[b.out];
+    return (x.t1 - x.t0) > (y.t1 - y.t0);
+  });
+  p.d_tiles = dalloc<GemmTile>(std::max<size_t>(p.tiles.size(), 1));
+  p.d_flat = dalloc<GemmTile>(std::max<size_t>(p.flat.size(), 1));
+  if (!p.flat.empty())
+    CK(cudaMemcpyAsync(p.d_flat, p.flat.data(), p.flat.size() * sizeof(GemmTile), cudaMemcpyHostToDevice, stream));
   if (!p.terms.empty())
     CK(cudaMemcpyAsync(p.d_terms, p.terms.data(), p.terms.size() * sizeof(GemmTerm), cudaMemcpyHostToDevice, stream));
   if (!p.outs.empty())
@@ -396,9 +415,11 @@ void Engine::release(GemmPlan& p) {
   dfree(p.d_terms);
   dfree(p.d_outs);
   dfree(p.d_tiles);
+  dfree(p.d_flat);
   p.d_terms = nullptr;
   p.d_outs = nullptr;
   p.d_tiles = nullptr;
+  p.d_flat = nullptr;
 }
 
 void Engine::upload(AxpyPlan& p) {
@@ -420,9 +441,9 @@ void Engine::release(AxpyPlan& p) {
 }
 
 void Engine::run(GemmPlan& p) {
-  if (p.tiles.empty()) return;
+  if (p.tiles.empty() && p.flat.empty()) return;
   launch_gemm_f64(p, stream);
-  stats.launches++;
+  stats.launches += (!p.tiles.empty()) + (!p.flat.empty());
   CK(cudaGetLastError());
 }
 
@@ -1350,7 +1371,12 @@ void Engine::truncate(int k, int dir, int M, double* tau_out, std::vector<double
   stats.trunc_rho_ms += tt1 - tt0;
   std::vector<std::vector<double>> ew(nq), ev(nq);
   std::atomic<int> fail(0);
-  parallel_for(nq, [&](int q) {
+  // largest sectors first, so that the longest eigensolve never starts last
+  std::vector<int> byq(nq);
+  std::iota(byq.begin(), byq.end(), 0);
+  std::stable_sort(byq.begin(), byq.end(), [&](int a, int b) { return md[a] > md[b]; });
+  parallel_for(nq, [&](int qi) {
+    const int q = byq[qi];
     int m = md[q];
     ew[q].resize(m);
     ev[q].resize((size_t)m * m);
@@ -1450,7 +1476,9 @@ double Engine::solve_tiers(Sigma& sg, const double* diag, double tol, int precis
     stats.tier_iters[t] += stats.davidson_iters - it0;
     it0 = stats.davidson_iters;
   };
-  if (precision == 0) {
+  // a small two-site state (chain ends) costs more to plan and convert for
+  // the tensor cores than its FP64 sigma takes: such steps stay FP64
+  if (precision == 0 || psi_size < tc_min_two_site) {
     theta = davidson(fp64op, diag, tol, sched.max_iter, sched.max_space, 0.0);
     tier_done(2);
   } else {

@@ -169,6 +169,7 @@ class Engine {
   bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
+  int64_t tc_min_two_site = 4096;   // smaller two-site states: reduced-precision schedules use FP64
   // tier-1 (BF16/TF32) Davidson iterations and steps of the current and the
   // previous sweep: a warm sweep whose predecessor averaged < 2 tier-1
   // iterations per step skips tier 1 (its plan would cost more than it saves)

@@ -101,12 +101,14 @@ struct GemmTile {
 struct GemmPlan {       // host side lists plus their device copies
   std::vector<GemmTerm> terms;
   std::vector<GemmOut> outs;
-  std::vector<GemmTile> tiles;
+  std::vector<GemmTile> tiles;   // 32 x 32 register-blocked tiles
+  std::vector<GemmTile> flat;    // {out, -1, first element, 0}: 256 elements, one per thread
   GemmTerm* d_terms = nullptr;
   GemmOut* d_outs = nullptr;
   GemmTile* d_tiles = nullptr;
+  GemmTile* d_flat = nullptr;
   double flops = 0.0;       // 2 m n k summed over terms
-  void clear() { terms.clear(); outs.clear(); tiles.clear(); flops = 0.0; }
+  void clear() { terms.clear(); outs.clear(); tiles.clear(); flat.clear(); flops = 0.0; }
   int add_out(double* C, int ldc, int M, int N, int beta) {
     GemmOut o{C, ldc, M, N, (int)terms.size(), (int)terms.size(), beta, 0};
     outs.push_back(o);

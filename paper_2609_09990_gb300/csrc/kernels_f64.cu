@@ -92,6 +92,32 @@ gemm_f64_kernel(const GemmTerm* __restrict__ terms, const GemmOut* __restrict__ 
   }
 }
 
+// one output element per thread, 256 consecutive elements (row-major) of
+// one output per item; per element the same FMA sequence as gemm_f64_kernel
+// (terms in order, k ascending, A scaled by alpha first)
+__global__ void __launch_bounds__(256)
+gemm_f64_flat_kernel(const GemmTerm* __restrict__ terms, const GemmOut* __restrict__ outs,
+                     const GemmTile* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const GemmTile w = items[it];
+    const GemmOut o = outs[w.out];
+    const int64_t e = (int64_t)w.tn + threadIdx.x;
+    if (e >= (int64_t)o.M * o.N) continue;
+    const int i = (int)(e / o.N), j = (int)(e - (int64_t)i * o.N);
+    double acc = 0.0;
+    for (int t = o.t0; t < o.t1; ++t) {
+      const GemmTerm T = terms[t];
+      const bool ta = T.flags & 1, tb = T.flags & 2;
+      const double* a = ta ? T.A + i : T.A + (int64_t)i * T.lda;
+      const double* b = tb ? T.B + (int64_t)j * T.ldb : T.B + j;
+      const int64_t sa = ta ? T.lda : 1, sb = tb ? 1 : T.ldb;
+      for (int k = 0; k < T.K; ++k) acc = fma(a[k * sa] * T.alpha, b[k * sb], acc);
+    }
+    double* c = o.C + (int64_t)i * o.ldc + j;
+    *c = o.beta ? (*c + acc) : acc;
+  }
+}
+
 __global__ void axpy_kernel(const AxpyTerm* __restrict__ terms, const AxpyOut* __restrict__ outs, int nouts) {
   for (int oi = blockIdx.x; oi < nouts; oi += gridDim.x) {
     const AxpyOut o = outs[oi];
@@ -199,10 +225,10 @@ int reduction_blocks(int64_t n) {
 }
 
 void launch_gemm_f64(const GemmPlan& p, cudaStream_t s) {
-  int nt = (int)p.tiles.size();
-  if (nt == 0) return;
-  int grid = nt < 152 * 24 ? nt : 152 * 24;
-  gemm_f64_kernel<<<grid, GEMM_THREADS, 0, s>>>(p.d_terms, p.d_outs, p.d_tiles, nt);
+  const int nt = (int)p.tiles.size();
+  if (nt > 0) gemm_f64_kernel<<<nt < 152 * 24 ? nt : 152 * 24, GEMM_THREADS, 0, s>>>(p.d_terms, p.d_outs, p.d_tiles, nt);
+  const int nf = (int)p.flat.size();
+  if (nf > 0) gemm_f64_flat_kernel<<<nf < 152 * 8 ? nf : 152 * 8, 256, 0, s>>>(p.d_terms, p.d_outs, p.d_flat, nf);
 }
 
 void launch_axpy(const AxpyPlan& p, cudaStream_t s) {

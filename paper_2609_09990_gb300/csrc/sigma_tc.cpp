@@ -501,9 +501,19 @@ TcPlan* Engine::tc_plan_impl(const EnlOp& lenl, const EnlOp& renl, int prec) {
   if (tc_fixed_cap) return tc_build(lenl, renl, prec, TcTune{{tc_fixed_cap, tc_fixed_cap}});
   if (!autotune) return tc_build(lenl, renl, prec, TcTune());
   auto lg = [](double x) { return (int64_t)std::lround(2.0 * std::log2(std::max(x, 1.0))); };
-  const int64_t key = ((int64_t)prec << 40) | (lg((double)psi_size) << 20) | lg((double)renl.subs.size());
+  const int64_t ka = lg((double)psi_size), kb = lg((double)renl.subs.size());
+  const int64_t key = ((int64_t)prec << 40) | (ka << 20) | kb;
   auto it = tuned.find(key);
   if (it != tuned.end()) return tc_build(lenl, renl, prec, it->second);
+  // a class within two half-octave buckets of a tuned one takes its shape
+  // (sizes drift from sweep to sweep; tuning again would cost more than it gains)
+  for (const auto& kv : tuned) {
+    const int64_t p2 = kv.first >> 40, a2 = (kv.first >> 20) & 0xFFFFF, b2 = kv.first & 0xFFFFF;
+    if (p2 == prec && std::llabs(a2 - ka) <= 2 && std::llabs(b2 - kb) <= 2) {
+      tuned[key] = kv.second;
+      return tc_build(lenl, renl, prec, kv.second);
+    }
+  }
   cudaEvent_t e[4];
   for (auto& x : e) CK(cudaEventCreate(&x));
   double* y = dalloc<double>(psi_size);

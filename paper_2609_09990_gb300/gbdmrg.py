@@ -86,6 +86,7 @@ def lib():
                                         C.POINTER(gbd_result)]),
         "gbd_set_batch_workers": (C.c_int, [vp, C.c_int32]),
         "gbd_set_graphs": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_tc_min_two_site": (C.c_int, [vp, C.c_int64]),
         "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
         "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
@@ -294,6 +295,9 @@ class Context:
     def set_accurate_tier(self, prec):
         """3 = TF32x3 (default), 4 = BF16x3."""
         self._check(self.L.gbd_set_accurate_tier(self.ptr, prec), "gbd_set_accurate_tier")
+
+    def set_tc_min_two_site(self, n):
+        self._check(self.L.gbd_set_tc_min_two_site(self.ptr, n), "gbd_set_tc_min_two_site")
 
     def set_graphs(self, enable):
         self._check(self.L.gbd_set_graphs(self.ptr, 1 if enable else 0), "gbd_set_graphs")

@@ -56,6 +56,7 @@ def test_mixed_solve_cas6_reaches_fci(G, precision):
         g = json.load(f)
     h, chol = make_integrals(6, 18, 1)
     ctx = G.Context(0)
+    ctx.set_tc_min_two_site(0)   # small problem: force the tensor-core tiers
     r = ctx.solve(h, chol, 6, 0, [64] * 4, [1e-9] * 4, seed=1, precision=precision, fp64_refine=4, rdms=True)
     assert abs(r["energy"] - g["E0"]) < 1e-9
     assert np.abs(r["rdm1"] - np.array(g["rdm1"])).max() < 1e-6
@@ -88,6 +89,7 @@ def test_graphs_and_autotune_do_not_change_the_solve(G):
     out = []
     for graphs, cap in ((True, 0), (False, 64)):
         ctx = G.Context(0)
+        ctx.set_tc_min_two_site(0)   # small problem: force the tensor-core tiers
         ctx.set_graphs(graphs)
         ctx.set_tc_tile(cap)
         r = ctx.solve(h, chol, 8, 0, [48] * 3, [1e-7] * 3, seed=22, precision=2, fp64_refine=0)
@@ -105,6 +107,7 @@ def test_probe_step_isolates_matvec_precision(G):
     # the same Rayleigh quotient; the mixed solve alone stays within its floor
     h, chol = make_integrals(10, 12, 23)
     ctx = G.Context(0)
+    ctx.set_tc_min_two_site(0)   # small problem: force the tensor-core tiers
     ctx.setup(h, chol, 10, 0, [96], [1e-8], seed=23)
     ctx.init_state()
     for k in range(4):
