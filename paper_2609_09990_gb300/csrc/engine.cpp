@@ -173,6 +173,7 @@ void parallel_for(int n, const std::function<void(int)>& f) {
 }  // namespace
 
 void set_host_threads(int n) { t_host_threads = n; }
+void host_parallel_for(int n, const std::function<void(int)>& f) { parallel_for(n, f); }
 
 // counter-based initial-MPS value (same published definition as the input
 // generator: splitmix64 finalizer on a derived seed and an element key)

@@ -6,6 +6,7 @@
 // by the implicit-shift QL iteration (Wilkinson & Reinsch, Handbook for
 // Automatic Computation II, 1971), written from the algorithm's description.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -14,9 +15,30 @@
 
 namespace gbd {
 
+namespace {
+// [0, count) in nblk contiguous blocks, on the host pool when par; every
+// element is handled by exactly one block in the serial order
+template <class F>
+void blocks(bool par, int count, F&& f) {
+  if (!par || count < 64) {
+    f(0, count);
+    return;
+  }
+  // block edges on multiples of 8 doubles (64-byte lines): no two threads
+  // write the same cache line of a row
+  const int nblk = std::min(16, count / 32);
+  auto edge = [&](int b) { return b == nblk ? count : (int)((int64_t)count * b / nblk) / 8 * 8; };
+  host_parallel_for(nblk, [&](int b) { f(edge(b), edge(b + 1)); });
+}
+constexpr int kParallelEig = 160;   // matrices at least this large split their O(n^2) loops
+}  // namespace
+
 // A: n x n symmetric, row-major.  On return w ascending, Z column j = eigvec j.
+// Large matrices run the row / column loops of each phase in parallel
+// blocks; every element sees the same operations in the same order.
 int sym_eig(int n, const double* A, double* w, double* Z) {
   if (n <= 0) return 0;
+  const bool par = n >= kParallelEig;
   std::vector<double> a(A, A + (size_t)n * n);
   std::vector<double> d(n), e(n, 0.0);
   // ---- Householder tridiagonalisation, storing the reflectors in a
@@ -40,20 +62,24 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
     double beta = 2.0 / vv;
     // p = beta * A22 v
     std::vector<double> p(m, 0.0);
-    for (int i = 0; i < m; ++i) {
-      const double* row = &a[(size_t)(k + 1 + i) * n + k + 1];
-      double s = 0.0;
-      for (int j = 0; j < m; ++j) s += row[j] * v[j];
-      p[i] = beta * s;
-    }
+    blocks(par && m >= 256, m, [&](int i0, int i1) {
+      for (int i = i0; i < i1; ++i) {
+        const double* row = &a[(size_t)(k + 1 + i) * n + k + 1];
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += row[j] * v[j];
+        p[i] = beta * s;
+      }
+    });
     double K = 0.0;
     for (int i = 0; i < m; ++i) K += v[i] * p[i];
     K *= 0.5 * beta;
     for (int i = 0; i < m; ++i) p[i] -= K * v[i];   // w
-    for (int i = 0; i < m; ++i) {
-      double* row = &a[(size_t)(k + 1 + i) * n + k + 1];
-      for (int j = 0; j < m; ++j) row[j] -= v[i] * p[j] + p[i] * v[j];
-    }
+    blocks(par && m >= 256, m, [&](int i0, int i1) {
+      for (int i = i0; i < i1; ++i) {
+        double* row = &a[(size_t)(k + 1 + i) * n + k + 1];
+        for (int j = 0; j < m; ++j) row[j] -= v[i] * p[j] + p[i] * v[j];
+      }
+    });
     a[(size_t)(k + 1) * n + k] = alpha;
     a[(size_t)k * n + k + 1] = alpha;
     for (int i = 1; i < m; ++i) { a[(size_t)(k + 1 + i) * n + k] = 0.0; a[(size_t)k * n + k + 1 + i] = 0.0; }
@@ -62,25 +88,29 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
   }
   for (int i = 0; i < n; ++i) d[i] = a[(size_t)i * n + i];
   for (int i = 0; i + 1 < n; ++i) e[i] = a[(size_t)(i + 1) * n + i];
-  // ---- Q = H_0 H_1 ... H_{n-3}, built from the right
+  // ---- Q = H_0 H_1 ... H_{n-3}, built from the right; each column block
+  // of z takes every reflector in turn (the columns are independent)
   std::vector<double> z((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) z[(size_t)i * n + i] = 1.0;
-  for (int k = (int)refl.size() - 1; k >= 0; --k) {
-    if (beta_l[k] == 0.0) continue;
-    const std::vector<double>& v = refl[k];
-    int m = (int)v.size(), o = k + 1;
-    // z[o:, :] -= beta v (v^T z[o:, :])
+  blocks(par, n, [&](int j0, int j1) {
     std::vector<double> t(n, 0.0);
-    for (int i = 0; i < m; ++i) {
-      const double* row = &z[(size_t)(o + i) * n];
-      for (int j = 0; j < n; ++j) t[j] += v[i] * row[j];
+    for (int k = (int)refl.size() - 1; k >= 0; --k) {
+      if (beta_l[k] == 0.0) continue;
+      const std::vector<double>& v = refl[k];
+      const int m = (int)v.size(), o = k + 1;
+      // z[o:, cols] -= beta v (v^T z[o:, cols])
+      for (int j = j0; j < j1; ++j) t[j] = 0.0;
+      for (int i = 0; i < m; ++i) {
+        const double* row = &z[(size_t)(o + i) * n];
+        for (int j = j0; j < j1; ++j) t[j] += v[i] * row[j];
+      }
+      for (int i = 0; i < m; ++i) {
+        double* row = &z[(size_t)(o + i) * n];
+        const double f = beta_l[k] * v[i];
+        for (int j = j0; j < j1; ++j) row[j] -= f * t[j];
+      }
     }
-    for (int i = 0; i < m; ++i) {
-      double* row = &z[(size_t)(o + i) * n];
-      double f = beta_l[k] * v[i];
-      for (int j = 0; j < n; ++j) row[j] -= f * t[j];
-    }
-  }
+  });
   // ---- implicit QL on (d, e), rotating the columns of z, kept transposed
   // (zt row j = column j of z) so that a rotation touches two contiguous
   // rows.  An off-diagonal
@@ -91,6 +121,7 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) zt[(size_t)j * n + i] = z[(size_t)i * n + j];
   const double eps = 2.220446049250313e-16;
+  std::vector<std::array<double, 3>> rot;   // (row, s, c) of every QL rotation, in order
   double anorm = 0.0;
   for (int i = 0; i < n; ++i) anorm = std::max(anorm, std::fabs(d[i]) + std::fabs(e[i]) + (i ? std::fabs(e[i - 1]) : 0.0));
   for (int l = 0; l < n; ++l) {
@@ -126,13 +157,7 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
         p = s * r;
         d[i + 1] = g + p;
         g = c * r - b;
-        double* zi = &zt[(size_t)i * n];
-        double* zi1 = zi + n;
-        for (int k = 0; k < n; ++k) {
-          const double zf = zi1[k];
-          zi1[k] = s * zi[k] + c * zf;
-          zi[k] = c * zi[k] - s * zf;
-        }
+        rot.push_back({(double)i, s, c});
       }
       if (early) continue;
       d[l] -= p;
@@ -140,6 +165,20 @@ int sym_eig(int n, const double* A, double* w, double* Z) {
       e[m] = 0.0;
     }
   }
+  // every rotation of the QL iterations, in order, on column blocks of zt
+  // (the recurrences for d and e never read the eigenvectors)
+  blocks(par, n, [&](int k0, int k1) {
+    for (const auto& R : rot) {
+      double* zi = &zt[(size_t)R[0] * n];
+      double* zi1 = zi + n;
+      const double rs = R[1], rc = R[2];
+      for (int k = k0; k < k1; ++k) {
+        const double zf = zi1[k];
+        zi1[k] = rs * zi[k] + rc * zf;
+        zi[k] = rc * zi[k] - rs * zf;
+      }
+    }
+  });
   // ---- sort ascending
   std::vector<int> ord(n);
   std::iota(ord.begin(), ord.end(), 0);
