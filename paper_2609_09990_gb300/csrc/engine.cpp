@@ -371,17 +371,21 @@ void Engine::upload(GemmPlan& p) {
   p.d_terms = dalloc<GemmTerm>(p.terms.size());
   p.d_outs = dalloc<GemmOut>(p.outs.size());
   // tiles: 32 x 32 outputs, or, where 32 x 32 tiles would leave more than
-  // a quarter of their elements idle (sector blocks of a few tens), flat
-  // items of 256 elements with one thread per element.  GB300's FP64 pipe
-  // is slow enough that the unblocked loop keeps it busy, and both kernels
-  // run the same FMA sequence per element.
+  // a quarter of their elements idle (sector blocks of a few tens) and the
+  // summed K is short (environment updates, not the sigma's long term
+  // lists, where register blocking pays), flat items of 256 elements with
+  // one thread per element.  GB300's FP64 pipe is slow enough that the
+  // unblocked loop keeps it busy, and both kernels run the same FMA
+  // sequence per element.
   p.tiles.clear();
   p.flat.clear();
   for (int o = 0; o < (int)p.outs.size(); ++o) {
     const GemmOut& g = p.outs[o];
     const int64_t elems = (int64_t)g.M * g.N;
     const int64_t padded = (int64_t)((g.M + 31) / 32 * 32) * ((g.N + 31) / 32 * 32);
-    if (elems > 0 && 4 * elems < 3 * padded) {
+    int64_t ksum = 0;
+    for (int t = g.t0; t < g.t1; ++t) ksum += p.terms[t].K;
+    if (elems > 0 && 4 * elems < 3 * padded && ksum <= 1024) {
       for (int64_t e0 = 0; e0 < elems; e0 += 256) p.flat.push_back({o, -1, (int32_t)e0, 0});
       continue;
     }
