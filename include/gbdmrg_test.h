@@ -164,6 +164,12 @@ int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32
  * absolute error and the largest |reference| element. */
 int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t nterms, uint64_t seed,
                     double *max_err, double *max_ref);
+/* Failure detection without a fault: one bounded mbarrier wait (the helper
+ * every role of the tensor-core kernel uses).  arrive = 0: nothing completes
+ * the barrier, the wait runs out after its poll limit (milliseconds) and
+ * returns with *err_flag = 1, *waited_ok = 0; arrive = 1: *err_flag = 0,
+ * *waited_ok = 1. */
+int gbd_wait_selftest(int32_t device, int32_t arrive, int32_t *err_flag, int32_t *waited_ok);
 /* Preconditioner network pieces for gradient checks: install FP32 weights
  * (kept FP16 on the device for inference); loss sum w (g-y)^2 / sum w +
  * lam mean(g^2) and its gradient over n feature rows X [n*8] with targets y

@@ -365,6 +365,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------- bounded waits
+// The failure path of every mbarrier wait above, on its own: one thread
+// waits (with the same bounded helper) on a barrier that is completed only
+// when `arrive` is set.  Without the arrival the wait runs out, raises
+// *err and the kernel returns; nothing hangs and no memory is touched
+// outside the barrier and the flag.
+__global__ void bounded_wait_probe_kernel(int arrive, int* err, int* waited_ok) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) mbar_arrive(&bar);
+    *waited_ok = mbar_wait(&bar, 0, err) ? 1 : 0;
+  }
+}
+
 // ---------------------------------------------------------------- split-K sum
 // one thread per output element; the slots are summed in FP64 with four
 // interleaved partial sums combined in a fixed order (deterministic)
@@ -448,6 +467,11 @@ void launch_tc_reduce(const TcRed* tasks, int ntasks, int64_t total, const float
   int64_t b = (total + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
   tc_reduce_kernel<<<(int)b, 256, 0, s>>>(tasks, ntasks, total, part, out);
+}
+
+bool bounded_wait_probe(int arrive, int* err_dev, int* ok_dev, cudaStream_t s) {
+  bounded_wait_probe_kernel<<<1, 32, 0, s>>>(arrive, err_dev, ok_dev);
+  return cudaGetLastError() == cudaSuccess;
 }
 
 int tc_stages(int prec, int ncap) {

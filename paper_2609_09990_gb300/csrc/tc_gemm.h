@@ -76,6 +76,9 @@ struct TcLaunch {
 };
 // shared-memory pipeline depth for B boxes of at most ncap rows
 int tc_stages(int prec, int ncap);
+// one bounded mbarrier wait (the helper every role of tc_gemm_kernel uses);
+// without `arrive` it runs out and raises *err_dev
+bool bounded_wait_probe(int arrive, int* err_dev, int* ok_dev, cudaStream_t s);
 
 // out[j * ld + m0 + i] = sum over the nslot consecutive partial slots
 // starting at float offset slot0 (slot s at slot0 + s * 128 * n_stride)

@@ -191,3 +191,22 @@ out:
   cudaFree(dterms);
   return rc;
 }
+
+// Failure detection of the tensor-core kernels without a fault: a bounded
+// mbarrier wait on a barrier that is never completed returns with the
+// error flag raised; the same wait with an arrival succeeds.
+extern "C" int gbd_wait_selftest(int32_t device, int32_t arrive, int32_t* err_flag, int32_t* waited_ok) {
+  using namespace gbd;
+  if (!err_flag || !waited_ok) return GBD_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return GBD_ERR_CUDA;
+  int* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return GBD_ERR_OOM;
+  int rc = GBD_OK, h[2] = {0, 0};
+  if (cudaMemset(d, 0, 2 * sizeof(int)) != cudaSuccess || !bounded_wait_probe(arrive, d, d + 1, 0) ||
+      cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = GBD_ERR_CUDA;
+  cudaFree(d);
+  *err_flag = h[0];
+  *waited_ok = h[1];
+  return rc;
+}

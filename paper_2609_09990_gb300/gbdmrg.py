@@ -110,6 +110,7 @@ def lib():
         "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32]),
         "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
+        "gbd_wait_selftest": (C.c_int, [C.c_int32, C.c_int32, _ip, _ip]),
         "gbd_tc_selftest": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                       _dp, _dp]),
         "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
@@ -478,6 +479,15 @@ def tc_selftest(prec, M, N, K, nterms, seed=1, device=0):
     if rc != GBD_OK:
         raise GbdError(f"gbd_tc_selftest: {ERRORS.get(rc, rc)}")
     return e.value, r.value
+
+
+def wait_selftest(arrive, device=0):
+    """(error flag, waited_ok) of one bounded mbarrier wait; arrive=False lets it run out."""
+    e, o = C.c_int32(), C.c_int32()
+    rc = lib().gbd_wait_selftest(device, 1 if arrive else 0, C.byref(e), C.byref(o))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_wait_selftest: {ERRORS.get(rc, rc)}")
+    return e.value, o.value
 
 
 def probe_peaks(device=0):
