@@ -159,6 +159,12 @@ def run_ours(args, rank, world):
     breakdown["tc_build_phase_ms"] = {
         nm: (st1["tc_build_phase_ms"][i] - st0["tc_build_phase_ms"][i]) / args.steps
         for i, nm in enumerate(["layout_groups", "panels", "tiles", "upload", "maps"])}
+    breakdown["tc_gemm_ms_by_stage"] = {
+        nm: (st1["tc_gemm_ms_by_stage"][i] - st0["tc_gemm_ms_by_stage"][i]) / args.steps
+        for i, nm in enumerate(["A", "B"])}
+    breakdown["tc_bytes_by_stage_GB"] = {
+        nm: (st1["tc_stage_alg_bytes"][i] - st0["tc_stage_alg_bytes"][i]) / args.steps / 1e9
+        for i, nm in enumerate(["A", "B"])}
     breakdown["davidson_iterations_by_tier"] = {
         t: (st1["tier_iterations"][i] - st0["tier_iterations"][i]) / args.steps
         for i, t in enumerate(["bf16_or_tf32", "tf32x3", "fp64"])}
@@ -260,13 +266,14 @@ def run_batched(args, rank, world):
                 energies=[r["energy"] for r in res], n_problems=len(probs))
 
 
-def sigma_probe(prec):
+def sigma_probe(prec, orders=(0,)):
     """Profiling driver for the tensor-core sigma: CAS(16,16) M=512, initial
     state, FP64 steps up to the central bond (7,8), then three sigma builds
     there with operand type `prec` (1 TF32, 2 BF16, 3 TF32x3).  The first
     one runs the tile-shape autotuner (3 candidate plans x 3 timed runs = 18
     tc_gemm_kernel launches), so `ncu -k regex:tc_gemm_kernel -s 18 -c 2`
-    captures stage A and stage B of the tuned plan."""
+    captures stage A and stage B of the tuned plan.  With several stage-B
+    tile orders, each is timed on three more builds."""
     from paper_2609_09990_gb300 import gbdmrg as G
     wl = WORKLOADS["cas16_m512"]
     n, ne, nq, M, seed = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"]
@@ -278,16 +285,29 @@ def sigma_probe(prec):
     for j in range(k):
         ctx.run_step(j, 0, M, 1e-3)
     x = np.random.default_rng(0).standard_normal(ctx.two_site_size(k))
-    s0 = ctx.stats()
-    for _ in range(3):
-        ctx.apply_heff_prec(k, x, prec)
-    s1 = ctx.stats()
-    nb = s1["n_sigma_tc"] - s0["n_sigma_tc"]
-    print(json.dumps({"sigma_probe": prec, "bond": k, "psi_len": int(x.size), "builds": nb,
-                      "tc_gemm_ms_per_build": (s1["tc_gemm_ms"] - s0["tc_gemm_ms"]) / nb,
-                      "tc_ms_per_build": (s1["tc_ms"] - s0["tc_ms"]) / nb,
-                      "alg_bytes_per_build": (s1["tc_bytes"] - s0["tc_bytes"]) / nb,
-                      "alg_flops_per_build": (s1["tc_flops"] - s0["tc_flops"]) / nb}))
+    ref = None
+    for order in orders:
+        ctx.set_tc_order(order)
+        s0 = ctx.stats()
+        each = []
+        for _ in range(3):
+            sa = ctx.stats()["tc_gemm_ms"]
+            y = ctx.apply_heff_prec(k, x, prec)
+            each.append(ctx.stats()["tc_gemm_ms"] - sa)
+        s1 = ctx.stats()
+        ref = y if ref is None else ref
+        nb = s1["n_sigma_tc"] - s0["n_sigma_tc"]
+        per = lambda key: (s1[key] - s0[key]) / nb
+        perv = lambda key: [(a - b) / nb for a, b in zip(s1[key], s0[key])]
+        print(json.dumps({"sigma_probe": prec, "stage_b_order": order, "bond": k, "psi_len": int(x.size),
+                          "builds": nb, "identical_to_first_order": bool(np.array_equal(y, ref)),
+                          "tc_gemm_ms_per_build": per("tc_gemm_ms"), "tc_gemm_ms_each": each,
+                          "tc_ms_per_build": per("tc_ms"),
+                          "alg_bytes_per_build": per("tc_bytes"), "alg_flops_per_build": per("tc_flops"),
+                          "stage_alg_bytes": perv("tc_stage_alg_bytes"),
+                          "stage_box_bytes": perv("tc_stage_box_bytes"),
+                          "stage_dense_bytes": perv("tc_stage_dense_bytes"),
+                          "stage_ms": perv("tc_gemm_ms_by_stage")}))
     ctx.close()
 
 
@@ -369,9 +389,10 @@ def main():
                     help="operands of the accurate Davidson tier")
     ap.add_argument("--sigma-probe", type=int, default=0, help="profiling driver: central sigma of cas16_m512 "
                     "with operand type 1 TF32, 2 BF16, 3 TF32x3 (no bench line)")
+    ap.add_argument("--probe-orders", default="0", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2")
     args = ap.parse_args()
     if args.sigma_probe:
-        sigma_probe(args.sigma_probe)
+        sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -50,6 +50,10 @@ typedef struct {
   double diag_ms;               /* H_eff diagonal (wall) */
   double truncate_rho_ms, truncate_eig_ms;   /* decimation: density matrices to the host; eigensolves */
   double env_wall_ms;           /* environment updates, wall time incl. plan upload (env_ms: kernels only) */
+  double tc_stage_alg_bytes[2]; /* tc_bytes split by stage: A (Renl, psi, Y^T write), B (Y^T read, Lenl, sigma) */
+  double tc_stage_box_bytes[4]; /* bytes the TMA boxes request from L2: stage A (A box, B box), stage B (A, B) */
+  double tc_stage_dense_bytes[4]; /* the valid rows x K of those boxes, without row, K or box-width padding */
+  double tc_gemm_ms_by_stage[2];  /* tc_gemm_ms split into stage A and stage B */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or
@@ -60,6 +64,15 @@ int gbd_set_graphs(gbd_ctx *ctx, int32_t enable);
  * class; 64, 128 or 256 = that largest N tile for both stages.  The shape
  * never changes the arithmetic (same products, same summation order). */
 int gbd_set_tc_tile(gbd_ctx *ctx, int32_t ncap);
+
+/* Order in which the persistent tensor-core CTAs take the stage-B tiles of
+ * the sigma (output sector q, 128-row block m0 of E_R, split-K chunk,
+ * s_out block so, N tile n0): 0 (default) by (q, m0, chunk, so, n0), 1 by
+ * (q, chunk, m0, so, n0), 2 by (q, so, chunk, n0, m0).  Tiles running at
+ * the same time share operand boxes through L2 in different ways; every
+ * tile computes the same products in the same order, so the result is
+ * identical for all three. */
+int gbd_set_tc_order(gbd_ctx *ctx, int32_t order);
 
 /* Preconditioner of the following Davidson solves (GBD_PRECOND_DIAG or
  * GBD_PRECOND_LEARNED; the latter needs weights in the context). */

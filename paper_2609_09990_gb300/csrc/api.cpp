@@ -288,6 +288,15 @@ int gbd_set_tc_tile(gbd_ctx* ctx, int32_t ncap) {
   });
 }
 
+int gbd_set_tc_order(gbd_ctx* ctx, int32_t order) {
+  return guarded(ctx, [&]() {
+    if (order < 0 || order > 2) return fail(ctx, GBD_ERR_ARG, "order not in {0,1,2}");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tc_order = order;
+    return GBD_OK;
+  });
+}
+
 int gbd_set_preconditioner(gbd_ctx* ctx, int32_t preconditioner) {
   return guarded(ctx, [&]() {
     if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
@@ -614,6 +623,14 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->truncate_eig_ms = t.trunc_eig_ms;
   s->env_wall_ms = t.env_wall_ms;
   for (int i = 0; i < 5; ++i) s->tc_build_phase_ms[i] = t.tcb_ms[i];
+  for (int i = 0; i < 2; ++i) {
+    s->tc_stage_alg_bytes[i] = t.tc_alg_st[i];
+    s->tc_stage_box_bytes[2 * i] = t.tc_box_st[i][0];
+    s->tc_stage_box_bytes[2 * i + 1] = t.tc_box_st[i][1];
+    s->tc_stage_dense_bytes[2 * i] = t.tc_dense_st[i][0];
+    s->tc_stage_dense_bytes[2 * i + 1] = t.tc_dense_st[i][1];
+    s->tc_gemm_ms_by_stage[i] = t.tc_gemm_ms_st[i];
+  }
   for (int i = 0; i < 4; ++i) {
     s->tc_flops_by_type[i] = t.tc_flops_p[i];
     s->tc_gemm_ms_by_type[i] = t.tc_gemm_ms_p[i];

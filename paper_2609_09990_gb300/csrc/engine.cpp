@@ -295,6 +295,7 @@ Engine::Engine(int dev) : device(dev) {
   CK(cudaEventCreate(&ev1));
   CK(cudaEventCreate(&evg0));
   CK(cudaEventCreate(&evg1));
+  CK(cudaEventCreate(&evgm));
   CK(cudaMallocHost(&tc_err_host, sizeof(int)));
   *tc_err_host = 0;
   cudaMemPool_t pool;
@@ -315,6 +316,7 @@ Engine::~Engine() {
   if (ev1) cudaEventDestroy(ev1);
   if (evg0) cudaEventDestroy(evg0);
   if (evg1) cudaEventDestroy(evg1);
+  if (evgm) cudaEventDestroy(evgm);
   if (stream) cudaStreamDestroy(stream);
 }
 
@@ -1336,6 +1338,10 @@ void Engine::settle() {
     stats.tc_ms += ms;
     float g = 0;
     CK(cudaEventElapsedTime(&g, evg0, evg1));
+    float ga = 0;
+    CK(cudaEventElapsedTime(&ga, evg0, evgm));
+    stats.tc_gemm_ms_st[0] += ga;
+    stats.tc_gemm_ms_st[1] += g - ga;
     stats.tc_gemm_ms += g;
     stats.tc_gemm_ms_p[stats.last_tc_prec] += g;
     if (*tc_err_host) throw Error(-5, "tensor-core sigma: a bounded device wait ran out");
@@ -1955,6 +1961,7 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, 
   std::vector<double> hy(psi_size);
   CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
   sync();
+  settle();   // the stats include this build when the call returns
   for (auto& m : maps)
     for (int a = 0; a < m.rows; ++a)
       for (int c = 0; c < m.cols; ++c) out[m.src + (int64_t)a * m.cols + c] = hy[m.dst + (int64_t)a * m.ld + c];

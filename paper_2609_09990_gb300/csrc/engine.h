@@ -82,6 +82,8 @@ struct Stats {
   int64_t tier_iters[3] = {0, 0, 0};
   double max_final_residual = 0, sum_final_residual = 0;   // over Davidson solves
   int64_t graph_launches = 0, autotune_trials = 0;
+  double tc_gemm_ms_st[2] = {0, 0};   // tc_gemm_kernel time by stage (A, B)
+  double tc_alg_st[2] = {0, 0}, tc_box_st[2][2] = {{0, 0}, {0, 0}}, tc_dense_st[2][2] = {{0, 0}, {0, 0}};   // per stage: algorithmic, TMA box bytes (A, B)
   double tc_gemm_ms = 0, tc_bytes = 0;   // tc_gemm_kernel launches only; algorithmic bytes of the TC sigma builds
   double tc_flops_p[4] = {0, 0, 0, 0}, tc_gemm_ms_p[4] = {0, 0, 0, 0};   // by operand type (BF16, TF32, TF32x3, BF16x3)
   int last_tc_prec = 0;
@@ -100,6 +102,14 @@ struct Stats {
     max_final_residual = std::max(max_final_residual, o.max_final_residual);
     sum_final_residual += o.sum_final_residual;
     graph_launches += o.graph_launches; autotune_trials += o.autotune_trials;
+    for (int s = 0; s < 2; ++s) {
+      tc_gemm_ms_st[s] += o.tc_gemm_ms_st[s];
+      tc_alg_st[s] += o.tc_alg_st[s];
+      tc_box_st[s][0] += o.tc_box_st[s][0];
+      tc_box_st[s][1] += o.tc_box_st[s][1];
+      tc_dense_st[s][0] += o.tc_dense_st[s][0];
+      tc_dense_st[s][1] += o.tc_dense_st[s][1];
+    }
     tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms; enl_host_ms += o.enl_host_ms; diag_ms += o.diag_ms;
     trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms; env_wall_ms += o.env_wall_ms;
     for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
@@ -168,6 +178,7 @@ class Engine {
   bool use_graphs = true;     // replay the sigma launch sequences as CUDA graphs
   bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
+  int tc_order = 0;           // stage-B tile order: 0 (q,m0,chunk,so,n0), 1 (q,chunk,m0,so,n0), 2 (q,so,chunk,n0,m0)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
   int64_t tc_min_two_site = 4096;   // smaller two-site states: reduced-precision schedules use FP64
   // tier-1 (BF16/TF32) Davidson iterations and steps of the current and the
@@ -190,6 +201,7 @@ class Engine {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t evg0 = nullptr, evg1 = nullptr;   // around the tensor-core GEMM launches of one sigma
+  cudaEvent_t evgm = nullptr;                    // between its stage A and stage B
   std::vector<double> h, eri;
   Mpo mpo;
   std::vector<Bond> bonds;

@@ -185,13 +185,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (!mbar_wait(&empty[stage], ph ^ 1, L.err)) { ok = false; break; }
           uint8_t* sa = base + stage * stage_bytes;
           uint8_t* sb = sa + kStageA;
+          // K-blocked operands step down by ays / bys rows per box,
+          // the others step right by one box
+          const int kb = k0 / kc;
+          const int xa = tm.ax + (tm.ays ? 0 : k0), ya = tm.ay + T.m0 + kb * tm.ays;
+          const int xb = tm.bx + (tm.bys ? 0 : k0), yb = tm.by + T.n0 + kb * tm.bys;
           mbar_expect_tx(&full[stage], tx);
-          tma_load_2d(sa, &maps.a[0], tm.ax + k0, tm.ay + T.m0, &full[stage]);
-          tma_load_2d(sb, &maps.b[0][T.bsel], tm.bx + k0, tm.by + T.n0, &full[stage]);
+          tma_load_2d(sa, &maps.a[0], xa, ya, &full[stage]);
+          tma_load_2d(sb, &maps.b[0][T.bsel], xb, yb, &full[stage]);
           if (x3) {
             uint8_t* sa2 = sb + bstage;
-            tma_load_2d(sa2, &maps.a[1], tm.ax + k0, tm.ay + T.m0, &full[stage]);
-            tma_load_2d(sa2 + kStageA, &maps.b[1][T.bsel], tm.bx + k0, tm.by + T.n0, &full[stage]);
+            tma_load_2d(sa2, &maps.a[1], xa, ya, &full[stage]);
+            tma_load_2d(sa2 + kStageA, &maps.b[1][T.bsel], xb, yb, &full[stage]);
           }
           if (++stage == stages) { stage = 0; ph ^= 1; }
         }
@@ -271,14 +276,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const bool has = T.t1 > T.t0;
       const bool live = row < T.m_valid;
       int pcol = 0;
-      int64_t prow = 0;
+      TcYRow yr{};
       if (T.mode == kTcYT && live) {
         int r = T.m0 + row, s = 0;
         for (int u = 1; u < 4; ++u)
           if (r >= T.rbreak[u]) s = u;
         pcol = T.rpad[s] + (r - T.rbreak[s]);
-      } else if (T.mode == kTcYTmap && live) {
-        prow = L.rowmap[T.out + row] * (int64_t)T.ld + T.n0;
+      } else if (T.mode == kTcYTblk && live) {
+        const int64_t r = T.out + row;
+        yr = L.yrows[L.ymem[r]];
+        yr.base += (r - yr.first) * (int64_t)kc;
       }
       const int a = acc_i & 1;
       const uint32_t aph = (acc_i >> 1) & 1;
@@ -293,9 +300,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
         if (!live) continue;
-        if (T.mode == kTcYTmap) {
-          // 16 contiguous, 16-element aligned output columns
-          const int64_t idx = prow + c0;
+        if (T.mode == kTcYTblk) {
+          // 16 contiguous output columns: section s, K offset k, block k / kc
+          if (c0 >= T.n_valid) continue;
+          const int c = T.n0 + c0;
+          int s = 0;
+          for (int u = 1; u < 4; ++u)
+            if (c >= T.rbreak[u]) s = u;
+          if (yr.koff[s] < 0) continue;
+          const int k = yr.koff[s] + (c - T.rbreak[s]);
+          const int64_t idx = yr.base + (int64_t)(k / kc) * yr.stride + (k % kc);
           if (bf) {
             uint32_t w[8], wl[8];
 #pragma unroll
@@ -433,7 +447,11 @@ __global__ void tc_convert_kernel(const TcConv* __restrict__ tasks, int ntasks, 
     const int64_t n = (int64_t)c.rows * c.cols;
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
       const int r = (int)(e / c.cols), col = (int)(e % c.cols);
-      store_conv(c.scale * c.src[(int64_t)r * c.ld_src + col], prec, hi, lo, (int64_t)(c.r0 + r) * pitch + c.c0 + col);
+      const int64_t dst = c.kstride > 0
+                              ? ((int64_t)c.r0 + (int64_t)((c.c0 + col) / pitch) * c.kstride + r) * pitch +
+                                    (c.c0 + col) % pitch
+                              : (int64_t)(c.r0 + r) * pitch + c.c0 + col;
+      store_conv(c.scale * c.src[(int64_t)r * c.ld_src + col], prec, hi, lo, dst);
     }
   }
 }

@@ -35,7 +35,8 @@ struct TcPlan {
   int ntiles[2] = {0, 0};
   TcMaps maps[2];
   float* part = nullptr;         // split-K partial slots of stage B
-  int64_t* d_rowmap = nullptr;   // stage A: Y^T row of every stacked Renl row
+  TcYRow* d_yrows = nullptr;      // stage A: where the stacked Renl rows of each member go in Y^T
+  int32_t* d_ymem = nullptr;      // stage A: member of every stacked row
   double *xin = nullptr, *yout = nullptr;   // fixed sigma input/output of the replayed graph
   GraphSeq graph;
   TcRed* d_red = nullptr;
@@ -47,6 +48,12 @@ struct TcPlan {
   // algorithmic HBM bytes of one sigma: the Renl and Lenl sub-blocks once,
   // Y^T written once and read once, psi read and sigma written in FP64
   double bytes_alg = 0;
+  // the same split by stage (A, B), and the bytes the TMA boxes of each
+  // stage request from L2, by operand (A box, B box): whole boxes of 128
+  // B wide and 128 (A) or 16 << bsel (B) rows per K step
+  double alg_st[2] = {0, 0}, box_st[2][2] = {{0, 0}, {0, 0}};
+  // the valid rows x K of those boxes (no padding of rows, K or box width)
+  double dense_st[2][2] = {{0, 0}, {0, 0}};
 };
 
 namespace {
@@ -75,7 +82,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   // ---- psi panel: rows E_L(Q) stacked, columns E_R(Q) with padded sub-ranges
   std::vector<int64_t> psi_row(nq);
   std::vector<std::array<int, 4>> cpadR(nq), cpadL(nq);
-  int64_t rows = 0, wmax = 0, wlmax = 0;
+  int64_t rows = 0, wmax = 0;
   std::vector<TcPsiSector> sec(nq);
   std::vector<int> wlq(nq);   // padded width of E_L(q)
   for (int q = 0; q < nq; ++q) {
@@ -90,7 +97,6 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     wlq[q] = (int)wl;
     rows += wl;   // psi rows in padded E_L positions (zero rows in the padding)
     wmax = std::max(wmax, w);
-    wlmax = std::max(wlmax, wl);
     TcPsiSector& S = sec[q];
     S.src_off = psi_off[q];
     S.rows = EL.dim[q];
@@ -105,45 +111,67 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   }
   P->psi_pitch = up64(wmax);
   const int64_t psi_rows = std::max<int64_t>(rows, 256);   // >= the largest B box
-  // ---- sub-block panels
-  auto sub_panel = [&](const EnlOp& op, std::vector<int64_t>& rowof, int64_t& pitch) {
-    int64_t r = 0, w = 0;
-    rowof.resize(op.subs.size());
-    for (size_t i = 0; i < op.subs.size(); ++i) {
-      rowof[i] = r;
-      r += op.subs[i].rows;
-      w = std::max<int64_t>(w, up16(op.subs[i].cols));
-    }
-    pitch = up64(w);
-    return std::max<int64_t>(r, 1);
-  };
-  std::vector<int64_t> ls_row;
-  const int64_t ls_rows = std::max<int64_t>(sub_panel(lenl, ls_row, P->ls_pitch), 256);
-  // ---- Y blocks (b, Qin) -> rows E_R(Qout) of the Y^T panel.  Keys are
-  //      small dense integers: flat tables indexed by b * nq + qin.
+  // ---- K layout of stage B.  For output sector q the contraction runs
+  //      over the column sections (b, qin, sin) that some Lenl[b] sub-block
+  //      (qin, sin -> q, sout) reads, in the order (b, qin, sin), each
+  //      section up16(cols) wide: K_q in all.  Y^T(q) (rows E_R(q)) and the
+  //      Lenl panel of q (rows E_L(q): every s_out section at its offset,
+  //      zero where Lenl[b] has no sub-block into it) are stored K-blocked:
+  //      block j holds columns [jW, (j+1)W) of every row, one W-element
+  //      panel row each (W = one 128-byte box row).  A stage-B tile then
+  //      streams dense boxes down the blocks, and the rows a 128-row box
+  //      reads beyond E_R(q) are the next block's, which it reads next.
+  //      Only the sections some sub-block reads are written by stage A.
+  const int W = 128 / P->eb;
   int nb = 0;
   for (const EnlSub& s : renl.subs) nb = std::max(nb, s.b + 1);
   for (const EnlSub& s : lenl.subs) nb = std::max(nb, s.b + 1);
   std::vector<int> rfirst((size_t)nb * nq, -1);   // first Renl sub of (b, qin)
-  std::vector<char> lhas((size_t)nb * nq, 0);
-  std::vector<std::vector<int>> lout((size_t)nq * 4);   // Lenl subs by (qout, sout)
   for (size_t i = 0; i < renl.subs.size(); ++i) {
     int& f = rfirst[(size_t)renl.subs[i].b * nq + renl.subs[i].qin];
     if (f < 0) f = (int)i;
   }
-  for (size_t i = 0; i < lenl.subs.size(); ++i) {
-    lhas[(size_t)lenl.subs[i].b * nq + lenl.subs[i].qin] = 1;
-    lout[(size_t)lenl.subs[i].qout * 4 + lenl.subs[i].sout].push_back((int)i);
+  std::vector<int32_t> koff((size_t)nb * nq * 4, -1);   // K offset of section (b, qin, sin) in K_qout
+  std::vector<char> yuse((size_t)nb * nq, 0);            // (b, qin) has a section in use
+  std::vector<int64_t> Kq(nq, 0), yrow0(nq, 0), lrow0(nq, 0);
+  int64_t yrows = 0, ls_rows = 0;
+  {
+    std::vector<std::vector<int32_t>> secs((size_t)nq);
+    for (const EnlSub& s : lenl.subs) {
+      const size_t bq = (size_t)s.b * nq + s.qin, key = bq * 4 + s.sin;
+      if (s.cols != EL.sdim[s.qin][s.sin] || s.rows != EL.sdim[s.qout][s.sout])
+        throw Error(-3, "enlarged-operator sub-block does not match its sections");
+      if (rfirst[bq] < 0 || koff[key] != -1) continue;   // no Y block, or already listed
+      if (renl.subs[rfirst[bq]].qout != s.qout) throw Error(-3, "Lenl and Renl channels disagree on the sector");
+      koff[key] = -2;
+      secs[s.qout].push_back((int32_t)key);
+    }
+    for (int q = 0; q < nq; ++q) {
+      std::sort(secs[q].begin(), secs[q].end());   // (b, qin, sin) order
+      int64_t k = 0;
+      for (int32_t key : secs[q]) {
+        koff[key] = (int32_t)k;
+        yuse[key / 4] = 1;
+        const int qin = (key / 4) % nq, sin = key % 4;
+        k += up16(EL.sdim[qin][sin]);
+        // Y^T(q) section written by stage A and read by stage B
+        const double yb = (double)P->eb * nh * ER.dim[q] * EL.sdim[qin][sin];
+        P->bytes_alg += 2.0 * yb;
+        P->alg_st[0] += yb;
+        P->alg_st[1] += yb;
+      }
+      Kq[q] = k;
+      const int64_t nblk = (k + W - 1) / W;
+      yrow0[q] = yrows;
+      yrows += nblk * ER.dim[q];
+      lrow0[q] = ls_rows;
+      ls_rows += nblk * EL.dim[q];
+    }
   }
-  std::vector<int64_t> ybase((size_t)nb * nq, -1);
-  int64_t yrows = 0;
-  for (size_t bq = 0; bq < ybase.size(); ++bq) {
-    if (rfirst[bq] < 0 || !lhas[bq]) continue;
-    ybase[bq] = yrows;
-    yrows += ER.dim[renl.subs[rfirst[bq]].qout];
-  }
-  P->yt_pitch = up64(wlmax);
+  P->yt_pitch = W;
+  P->ls_pitch = W;
   yrows = std::max<int64_t>(yrows, 128);
+  ls_rows = std::max<int64_t>(ls_rows, 256);
   // ---- stage A operand: the Renl sub-blocks with the same (qin, qout, so)
   //      and the same set of input local states si, stacked over b (rows
   //      m(so) per b), one 16-aligned column section per si.  Every stacked
@@ -160,17 +188,18 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     std::array<int, 4> col{};
   };
   std::vector<AGroup> groups;
-  std::vector<int64_t> rowmap;
+  std::vector<TcYRow> yrowtab;
+  std::vector<int32_t> ymem;
   int64_t rs_rows = 0, rs_width = 0;
   {
-    // (b, qin) with a Y block -> compact index; (that index, so) -> subs per si
+    // (b, qin) with a Y block in use -> compact index; (that index, so) -> subs per si
     std::vector<int> bq_of((size_t)nb * nq, -1);
     int nbq = 0;
-    for (size_t bq = 0; bq < ybase.size(); ++bq)
-      if (ybase[bq] >= 0) bq_of[bq] = nbq++;
+    for (size_t bq = 0; bq < yuse.size(); ++bq)
+      if (yuse[bq]) bq_of[bq] = nbq++;
     std::vector<std::array<int, 4>> bso((size_t)nbq * 4, std::array<int, 4>{-1, -1, -1, -1});
     std::vector<int> bq_key((size_t)nbq);
-    for (size_t bq = 0; bq < ybase.size(); ++bq)
+    for (size_t bq = 0; bq < yuse.size(); ++bq)
       if (bq_of[bq] >= 0) bq_key[bq_of[bq]] = (int)bq;
     for (size_t i = 0; i < renl.subs.size(); ++i) {
       const EnlSub& s = renl.subs[i];
@@ -218,9 +247,14 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       }
       rs_width = std::max(rs_width, w);
       for (size_t bi = 0; bi < g.b.size(); ++bi) {
-        const int mso = ER.sdim[g.qout[bi]][g.so[bi]];
-        const int64_t y0 = ybase[(size_t)g.b[bi] * nq + g.qin] + ER.soff[g.qout[bi]][g.so[bi]];
-        for (int r = 0; r < mso; ++r) rowmap.push_back(y0 + r);
+        const int q = g.qout[bi], mso = ER.sdim[q][g.so[bi]];
+        TcYRow R{};
+        R.base = (yrow0[q] + ER.soff[q][g.so[bi]]) * (int64_t)W;
+        R.stride = (int32_t)(ER.dim[q] * W);
+        for (int s = 0; s < 4; ++s) R.koff[s] = koff[((size_t)g.b[bi] * nq + g.qin) * 4 + s];
+        R.first = (int32_t)(g.row0 + g.roff[bi]);
+        ymem.insert(ymem.end(), (size_t)mso, (int32_t)yrowtab.size());
+        yrowtab.push_back(R);
       }
       rs_rows += g.rows;
     }
@@ -241,13 +275,14 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   }
   // ---- convert the sub-blocks (once per step)
   auto convert = [&](const EnlOp& op, const std::vector<int64_t>& rowof, const std::vector<int64_t>& colof,
-                     void** panel, int64_t pitch) {
+                     const std::vector<int32_t>* kstride, void** panel, int64_t pitch) {
     std::vector<TcConv> tasks;
     for (size_t i = 0; i < op.subs.size(); ++i) {
       const EnlSub& s = op.subs[i];
       if (rowof[i] < 0) continue;   // not used by any product
       check_range(s.ptr, s.rows, s.cols, s.cols, "tc convert source");
-      tasks.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], (int32_t)colof[i]});
+      tasks.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], (int32_t)colof[i],
+                       kstride ? (*kstride)[i] : 0});
     }
     if (tasks.empty()) return;
     TcConv* d = dalloc<TcConv>(tasks.size());
@@ -268,12 +303,28 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           r0[i] = g.row0 + g.roff[bi];
           c0[i] = g.col[si];
         }
-    convert(renl, r0, c0, P->rs, P->rs_pitch);
+    convert(renl, r0, c0, nullptr, P->rs, P->rs_pitch);
   }
-  convert(lenl, ls_row, std::vector<int64_t>(lenl.subs.size(), 0), P->ls, P->ls_pitch);
-  if (!rowmap.empty()) {
-    P->d_rowmap = dalloc<int64_t>(rowmap.size());
-    CK(cudaMemcpyAsync(P->d_rowmap, rowmap.data(), rowmap.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  {
+    // Lenl sub-block (qin, sin -> q, sout): rows at E_L(q) offset of sout in
+    // every K block of q, columns from the K offset of its section
+    std::vector<int64_t> r0(lenl.subs.size(), -1), c0(lenl.subs.size(), 0);
+    std::vector<int32_t> ks(lenl.subs.size(), 0);
+    for (size_t i = 0; i < lenl.subs.size(); ++i) {
+      const EnlSub& s = lenl.subs[i];
+      const int32_t k = koff[((size_t)s.b * nq + s.qin) * 4 + s.sin];
+      if (k < 0) continue;
+      r0[i] = lrow0[s.qout] + EL.soff[s.qout][s.sout];
+      c0[i] = k;
+      ks[i] = EL.dim[s.qout];
+    }
+    convert(lenl, r0, c0, &ks, P->ls, P->ls_pitch);
+  }
+  if (!yrowtab.empty()) {
+    P->d_yrows = dalloc<TcYRow>(yrowtab.size());
+    P->d_ymem = dalloc<int32_t>(ymem.size());
+    CK(cudaMemcpyAsync(P->d_yrows, yrowtab.data(), yrowtab.size() * sizeof(TcYRow), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(P->d_ymem, ymem.data(), ymem.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
   }
   P->nsec = nq;
   P->d_sec = dalloc<TcPsiSector>(std::max(nq, 1));
@@ -283,6 +334,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   //      columns = sum over si  Rsub(b; si -> so) psi(qin)[:, si part]^T
   std::vector<TcTile> tiles;
   std::vector<TcTerm> terms;
+  std::vector<int32_t> term_k;   // unpadded K of every term (byte counts only)
   for (const AGroup& g : groups) {
     const int64_t grows = g.rows;
     for (size_t bi = 0; bi < g.b.size(); ++bi) {
@@ -291,15 +343,17 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         if (g.mem[bi][si] >= 0) {
           P->flops_alg += 2.0 * EL.dim[g.qin] * mso * ER.sdim[g.qin][si];
           P->bytes_alg += (double)P->eb * nh * mso * ER.sdim[g.qin][si];           // Renl sub-block
+          P->alg_st[0] += (double)P->eb * nh * mso * ER.sdim[g.qin][si];
         }
     }
-    P->bytes_alg += 2.0 * P->eb * nh * grows * EL.dim[g.qin];                     // Y^T write + read
     // one term list per group, shared by its tiles
     const int gt0 = (int)terms.size();
     for (int si = 0; si < 4; ++si)
-      if (g.mask >> si & 1)
+      if (g.mask >> si & 1) {
+        term_k.push_back(ER.sdim[g.qin][si]);
         terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)psi_row[g.qin], (int32_t)up16(ER.sdim[g.qin][si]),
                          0, cpadR[g.qin][si]});
+      }
     const int gt1 = (int)terms.size();
     for (int64_t m0 = 0; m0 < grows; m0 += 128)
       for (int n0 = 0; n0 < wlq[g.qin]; n0 += tune.ncap[0]) {
@@ -312,18 +366,20 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         T.n_mma = (int)up16(nv);
         T.n_valid = nv;
         T.bsel = bsel_for(T.n_mma);
-        T.mode = kTcYTmap;
+        T.mode = kTcYTblk;
         T.beta = 0;
         T.ld = (int32_t)P->yt_pitch;
         T.out = g.row0 + m0;
         T.n0 = n0;
+        for (int s = 0; s < 4; ++s) T.rbreak[s] = cpadL[g.qin][s];   // column sections of E_L(qin)
         for (int t = T.t0; t < T.t1; ++t) P->flops_exec += 2.0 * 128 * T.n_mma * terms[t].k;
         tiles.push_back(T);
       }
   }
-  // keys < 0: most expensive tiles first; else by the given keys (tiles
-  // that read the same A boxes adjacent, so that they run at the same time
-  // on neighbouring SMs and share the boxes through L2)
+  // stage A: most expensive tiles first; stage B: by the keys, in the
+  // priority tc_order names (tiles that read the same boxes adjacent, so
+  // that they run at the same time on neighbouring SMs and share the boxes
+  // through L2)
   std::vector<std::array<int, 5>> bkey;
   auto upload_tiles = [&](int which) {
     P->ntiles[which] = (int)tiles.size();
@@ -336,14 +392,32 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       cost[i] = c * tiles[i].n_mma + 4096.0;   // + per-tile fixed cost (epilogue)
       order[i] = (int)i;
     }
-    if (which == 1 && bkey.size() == tiles.size())
-      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bkey[a] < bkey[b]; });
-    else
+    if (which == 1 && bkey.size() == tiles.size()) {
+      // bkey holds (q, m0, chunk, so, n0); the order names the priority
+      static const int perm[3][5] = {{0, 1, 2, 3, 4}, {0, 2, 1, 3, 4}, {0, 3, 2, 4, 1}};
+      const int* pm = perm[tc_order];
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        for (int i = 0; i < 5; ++i)
+          if (bkey[a][pm[i]] != bkey[b][pm[i]]) return bkey[a][pm[i]] < bkey[b][pm[i]];
+        return false;
+      });
+    } else
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     {
       std::vector<TcTile> sorted(tiles.size());
       for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
       tiles.swap(sorted);
+    }
+    {
+      const int kstep = 128 / P->eb;
+      for (const TcTile& T : tiles)
+        for (int t = T.t0; t < T.t1; ++t) {
+          const double steps = (double)((terms[t].k + kstep - 1) / kstep) * nh;
+          P->box_st[which][0] += steps * 128 * 128;
+          P->box_st[which][1] += steps * (16 << T.bsel) * 128;
+          P->dense_st[which][0] += (double)T.m_valid * term_k[t] * P->eb * nh;
+          P->dense_st[which][1] += (double)T.n_valid * term_k[t] * P->eb * nh;
+        }
     }
     P->d_tiles[which] = dalloc<TcTile>(std::max<size_t>(tiles.size(), 1));
     P->d_terms[which] = dalloc<TcTerm>(std::max<size_t>(terms.size(), 1));
@@ -356,67 +430,75 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     sync();
     tiles.clear();
     terms.clear();
+    term_k.clear();
   };
   phase(2);   // host: stage A tiles
   upload_tiles(0);
   phase(3);   // upload
-  // ---- stage B tiles: sigma(Qout)[rows (q_l', so), E_R tile] = sum Y^T Lsub^T
-  for (int q = 0; q < nq; ++q)
-    for (int so = 0; so < 4; ++so) {
-      if (EL.soff[q][so] < 0) continue;
-      const int N = EL.sdim[q][so];
-      const std::vector<int>& lo = lout[(size_t)q * 4 + so];
-      // one term list per output block (q, so), shared by its tiles
-      const int ot0 = (int)terms.size();
-      for (int i : lo) {
-        const EnlSub& s = lenl.subs[i];
-        const int64_t yb = ybase[(size_t)s.b * nq + s.qin];
-        if (yb < 0) continue;
-        terms.push_back({cpadL[s.qin][s.sin], (int32_t)yb, (int32_t)ls_row[i], (int32_t)up16(s.cols), 0, 0});
-        P->flops_alg += 2.0 * ER.dim[q] * N * s.cols;
-        P->bytes_alg += (double)P->eb * nh * N * s.cols;                          // Lenl sub-block
-      }
-      const int ot1 = (int)terms.size();
-      int64_t ksum = 0;
-      for (int t = ot0; t < ot1; ++t) ksum += terms[t].k;
-      for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
-        for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
-          TcTile T{};
-          T.t0 = ot0;
-          T.t1 = ot1;
-          T.n0 = n0;
-          T.m0 = m0;
-          T.m_valid = std::min(128, ER.dim[q] - m0);
-          const int nv = std::min(tune.ncap[1], N - n0);
-          T.n_mma = (int)up16(nv);
-          T.n_valid = nv;
-          T.bsel = bsel_for(T.n_mma);
-          T.mode = kTcSigma;
-          T.beta = 0;
-          T.ld = ER.dim[q];
-          T.out = psi_off[q] + (int64_t)(EL.soff[q][so] + n0) * ER.dim[q];
-          P->flops_exec += 2.0 * 128 * T.n_mma * (double)ksum;
-          tiles.push_back(T);
-          // order: (q, m0, chunk, so, n0): the s_out blocks and n-tiles of
-          // one (q, m0, chunk) read the same Y^T boxes and run together
-          bkey.push_back({q, m0, 0, so, n0});   // chunk index filled by the split
-        }
+  // ---- stage B tiles: sigma(q)[E_L(q) rows, E_R(q) tile] = Lenl panel of q
+  //      x Y^T(q)^T over K_q: one dense product per output sector, its K
+  //      cut into chunks of kc (multiples of W) that are separate terms
+  for (const EnlSub& s : lenl.subs)
+    if (koff[((size_t)s.b * nq + s.qin) * 4 + s.sin] >= 0) {
+      P->flops_alg += 2.0 * ER.dim[s.qout] * s.rows * s.cols;
+      P->bytes_alg += (double)P->eb * nh * s.rows * s.cols;                       // Lenl sub-block
+      P->alg_st[1] += (double)P->eb * nh * s.rows * s.cols;
     }
-  // ---- split K: a stage-B tile whose summed K exceeds kc becomes chunks of
-  //      whole terms (summed K <= kc) writing FP32 partial slots, summed in
-  //      FP64 by tc_reduce.  The chunks fill the SMs when sigma has few
-  //      output tiles, and they bound the length of every FP32 accumulation
-  //      in TMEM (its rounding error grows with that length).
+  // chunk length: the summed K x columns over all output tiles, shared out
+  // over ~4 tiles per SM, within [256, 512] (split types) or [256, 2048].
+  // It depends on the sizes only, never on the tuned tile shape, so the
+  // tile shape never changes the arithmetic.
+  int64_t kc = 0;
   {
-    // summed K x columns, independent of the N tiling (so that the tuned
-    // tile shape never changes the chunking, i.e. the arithmetic)
     int64_t work = 0;
-    for (const TcTile& T : tiles)
-      for (int t = T.t0; t < T.t1; ++t) work += (int64_t)terms[t].k * T.n_valid;
-    int64_t kc = work / ((int64_t)4 * num_sms * 256);
+    for (int q = 0; q < nq; ++q)
+      if (EL.dim[q] > 0 && ER.dim[q] > 0) work += (int64_t)((ER.dim[q] + 127) / 128) * Kq[q] * EL.dim[q];
+    kc = work / ((int64_t)4 * num_sms * 256);
     kc = (kc + 63) / 64 * 64;
     kc = std::max<int64_t>(256, std::min<int64_t>(nh == 2 ? 512 : 2048, kc));
     P->kc = kc;
+  }
+  for (int q = 0; q < nq; ++q) {
+    if (EL.dim[q] <= 0 || ER.dim[q] <= 0) continue;
+    const int N = EL.dim[q];
+    // one term list per output sector, shared by its tiles
+    const int ot0 = (int)terms.size();
+    for (int64_t k0 = 0; k0 < Kq[q]; k0 += kc) {
+      const int64_t blk = k0 / W, k = std::min<int64_t>(kc, Kq[q] - k0);
+      term_k.push_back((int32_t)k);
+      terms.push_back({0, (int32_t)(yrow0[q] + blk * ER.dim[q]), (int32_t)(lrow0[q] + blk * EL.dim[q]), (int32_t)k, 0,
+                       0, ER.dim[q], EL.dim[q]});
+    }
+    const int ot1 = (int)terms.size();
+    for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
+      for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
+        TcTile T{};
+        T.t0 = ot0;
+        T.t1 = ot1;
+        T.n0 = n0;
+        T.m0 = m0;
+        T.m_valid = std::min(128, ER.dim[q] - m0);
+        const int nv = std::min(tune.ncap[1], N - n0);
+        T.n_mma = (int)up16(nv);
+        T.n_valid = nv;
+        T.bsel = bsel_for(T.n_mma);
+        T.mode = kTcSigma;
+        T.beta = 0;
+        T.ld = ER.dim[q];
+        T.out = psi_off[q] + (int64_t)n0 * ER.dim[q];
+        P->flops_exec += 2.0 * 128 * T.n_mma * (double)Kq[q];
+        tiles.push_back(T);
+        // key (q, m0, chunk, -, n0): by default the n tiles of one
+        // (q, m0, chunk) read the same Y^T boxes and run together
+        bkey.push_back({q, m0, 0, 0, n0});   // chunk index filled by the split
+      }
+  }
+  // ---- split K: a stage-B tile with more than one chunk becomes one tile
+  //      per chunk writing an FP32 partial slot, summed in FP64 by
+  //      tc_reduce.  The chunks fill the SMs when sigma has few output
+  //      tiles, and they bound the length of every FP32 accumulation in
+  //      TMEM (its rounding error grows with that length).
+  {
     std::vector<TcTile> split;
     std::vector<std::array<int, 5>> skey;
     std::vector<TcRed> red;
@@ -465,6 +547,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   upload_tiles(1);
   phase(3);
   P->bytes_alg += 2.0 * 8.0 * psi_size;                                          // psi in, sigma out
+  P->alg_st[0] += 8.0 * psi_size;
+  P->alg_st[1] += 8.0 * psi_size;
   // ---- tensor maps
   std::memset(P->maps, 0, sizeof(P->maps));
   for (int h = 0; h < nh; ++h) {
@@ -524,9 +608,9 @@ TcPlan* Engine::tc_plan_impl(const EnlOp& lenl, const EnlOp& renl, int prec) {
     for (int rep = 0; rep < 3; ++rep) {
       launch_tc_convert_psi(psi, P->d_sec, P->nsec, psi_size, P->prec, P->psi[0], P->psi[1], P->psi_pitch, stream);
       TcLaunch A{P->d_tiles[0], P->d_terms[0], P->ntiles[0], P->prec, P->yt[0], P->yt[1], nullptr, P->d_err,
-                 nullptr, P->d_rowmap, c, tc_stages(prec, c)};
+                 nullptr, P->d_yrows, P->d_ymem, c, tc_stages(prec, c)};
       TcLaunch B{P->d_tiles[1], P->d_terms[1], P->ntiles[1], P->prec, nullptr, nullptr, y, P->d_err, P->part,
-                 nullptr, c, tc_stages(prec, c)};
+                 nullptr, nullptr, c, tc_stages(prec, c)};
       CK(cudaEventRecord(e[0], stream));
       bool ok = launch_tc_gemm(P->maps[0], A, num_sms, stream);
       CK(cudaEventRecord(e[1], stream));
@@ -566,7 +650,8 @@ void Engine::tc_free(TcPlan* P) {
   }
   if (P->d_sec) dfree(P->d_sec);
   if (P->part) dfree(P->part);
-  if (P->d_rowmap) dfree(P->d_rowmap);
+  if (P->d_yrows) dfree(P->d_yrows);
+  if (P->d_ymem) dfree(P->d_ymem);
   if (P->xin) dfree(P->xin);
   if (P->yout) dfree(P->yout);
   Engine::drop(P->graph);
@@ -589,11 +674,13 @@ void Engine::tc_apply(TcPlan* P, const double* x, double* y) {
     const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     CK(cudaEventRecordWithFlags(evg0, stream, evf));
     TcLaunch A{P->d_tiles[0], P->d_terms[0], P->ntiles[0], P->prec, P->yt[0], P->yt[1], nullptr, P->d_err,
-               nullptr, P->d_rowmap, P->tune.ncap[0], tc_stages(P->prec, P->tune.ncap[0])};
+               nullptr, P->d_yrows, P->d_ymem, P->tune.ncap[0], tc_stages(P->prec, P->tune.ncap[0])};
     TcLaunch B{P->d_tiles[1], P->d_terms[1], P->ntiles[1], P->prec, nullptr, nullptr, yo, P->d_err, P->part,
-               nullptr, P->tune.ncap[1], tc_stages(P->prec, P->tune.ncap[1])};
-    if (!launch_tc_gemm(P->maps[0], A, num_sms, stream) || !launch_tc_gemm(P->maps[1], B, num_sms, stream))
-      throw Error(-3, "invalid tensor-core launch configuration");
+               nullptr, nullptr, P->tune.ncap[1], tc_stages(P->prec, P->tune.ncap[1])};
+    bool ok = launch_tc_gemm(P->maps[0], A, num_sms, stream);
+    CK(cudaEventRecordWithFlags(evgm, stream, evf));
+    ok = ok && launch_tc_gemm(P->maps[1], B, num_sms, stream);
+    if (!ok) throw Error(-3, "invalid tensor-core launch configuration");
     CK(cudaEventRecordWithFlags(evg1, stream, evf));
     launch_tc_reduce(P->d_red, P->nred, P->red_total, P->part, yo, stream);
   };
@@ -620,6 +707,13 @@ void Engine::tc_apply(TcPlan* P, const double* x, double* y) {
   stats.n_sigma_tc++;
   stats.tc_flops += P->flops_alg;
   stats.tc_bytes += P->bytes_alg;
+  for (int s = 0; s < 2; ++s) {
+    stats.tc_dense_st[s][0] += P->dense_st[s][0];
+    stats.tc_dense_st[s][1] += P->dense_st[s][1];
+    stats.tc_alg_st[s] += P->alg_st[s];
+    stats.tc_box_st[s][0] += P->box_st[s][0];
+    stats.tc_box_st[s][1] += P->box_st[s][1];
+  }
   stats.tc_flops_p[P->prec] += P->flops_alg;
   stats.last_tc_prec = P->prec;
 }

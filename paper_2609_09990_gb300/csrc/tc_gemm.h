@@ -15,10 +15,15 @@
 //   kTcYT    : C^T into a panel (BF16, TF32, or TF32 hi/lo), row j of the
 //              output is panel row out + j, output column = the padded
 //              position of tile row m0 + i (rmap: 4 breaks + 4 pads),
-//   kTcYTmap : C into a panel: row i goes to panel row rowmap[out + i],
-//              columns n0 + j (the B rows are already in padded positions,
-//              so every 16-column chunk is contiguous and 16-aligned:
-//              vector stores),
+//   kTcYTblk : C into a K-blocked panel (pitch = one box row, W elements;
+//              element (m, k) of a block at ((k / W) * rows + m) * W + k % W):
+//              tile row r = out + i belongs to run yrows[ymem[r]] (a run of
+//              consecutive rows: position of its first row in block 0, the
+//              block stride, and for each of the 4 column sections of B the
+//              K offset where that section goes, or -1 to drop it);
+//              sections start at rbreak[s] (tile columns n0 + j).
+//              Every 16-column chunk lies in one section and one block, so
+//              it is stored with vector stores,
 //   kTcSigma : C^T into FP64, out[j * ld + m0 + i] (= or +=),
 //   kTcPart  : C^T into an FP32 partial slot, part[out + j * 128 + i]; the
 //              partial slots of one output tile (split K) are summed in FP64
@@ -33,7 +38,7 @@
 namespace gbd {
 
 enum TcPrec { kBF16 = 0, kTF32 = 1, kTF32x3 = 2, kBF16x3 = 3 };
-enum TcMode { kTcYT = 0, kTcSigma = 1, kTcPart = 2, kTcYTmap = 3 };
+enum TcMode { kTcYT = 0, kTcSigma = 1, kTcPart = 2, kTcYTblk = 4 };
 
 struct TcTerm {
   int32_t ax, ay;   // A box origin: column (K) and row (before adding the tile's m0)
@@ -41,6 +46,17 @@ struct TcTerm {
   int32_t k;        // K, a multiple of the MMA K step (16 BF16, 8 TF32)
   int32_t neg;      // 1: subtract the product
   int32_t bx;       // B box first column (K origin)
+  int32_t ays, bys; // > 0: K-blocked operand, each K box is ays (bys) rows further
+                    // down at the same column; 0: the next K box is the next columns
+};
+
+// a run of consecutive output rows of kTcYTblk tiles (row first + i goes
+// to element base + i * W, W = elements per box row)
+struct TcYRow {
+  int64_t base;      // element offset of (first row, k = 0)
+  int32_t stride;    // elements from one K block to the next
+  int32_t koff[4];   // K offset of column section s, -1: not stored
+  int32_t first;     // tile-row index (out + i) of the run's first row
 };
 
 struct TcTile {
@@ -49,9 +65,9 @@ struct TcTile {
   int32_t n_mma, n_valid;
   int32_t bsel;          // B box height index: 16 << bsel rows
   int32_t mode, beta, ld;
-  int64_t out;           // output element offset (panel row for kTcYT, row-map index for kTcYTmap)
+  int64_t out;           // output element offset (panel row for kTcYT, first yrows entry for kTcYTblk)
   int32_t rbreak[4], rpad[4];
-  int32_t n0;            // offset of the tile's first B row (kTcYTmap: also its first output column)
+  int32_t n0;            // offset of the tile's first B row (kTcYTblk: also its first output column)
   int32_t unused;
 };
 
@@ -70,7 +86,8 @@ struct TcLaunch {
   double* f64;           // kTcSigma output
   int* err;              // device flag: 1 = a bounded wait ran out
   float* part;           // kTcPart output slots
-  const int64_t* rowmap; // kTcYTmap output rows
+  const TcYRow* yrows;   // kTcYTblk output row runs
+  const int32_t* ymem;   // kTcYTblk: run of every output row
   int ncap;              // largest n_mma of the launch's tiles: 64, 128 or 256
   int stages;            // = tc_stages(prec, ncap)
 };
@@ -101,12 +118,15 @@ bool tc_encode_panel(CUtensorMap* m, int prec_elem_bytes, const void* base, uint
 bool launch_tc_gemm(const TcMaps& maps, const TcLaunch& L, int num_sms, cudaStream_t s);
 
 // conversion of FP64 blocks into panels: rows x cols block at src (ld_src)
-// written at panel row r0, column c0 (pitch); lo != nullptr for TF32x3
+// written at panel row r0, column c0 (pitch); lo != nullptr for the split
+// (x3) types.  kstride > 0: K-blocked panel, column c0 + j goes to row
+// r0 + ((c0 + j) / pitch) * kstride, column (c0 + j) % pitch.
 struct TcConv {
   const double* src;
   double scale;          // multiplies every element (the sub-block's coefficient)
   int32_t rows, cols, ld_src;
   int32_t r0, c0;
+  int32_t kstride;
 };
 void launch_tc_convert(const TcConv* tasks, int ntasks, int prec, void* hi, void* lo, int64_t pitch,
                        cudaStream_t s);

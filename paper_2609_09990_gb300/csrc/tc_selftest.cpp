@@ -125,7 +125,7 @@ extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t 
         if (!tc_encode_panel(&maps.b[h][s], eb, pb[h], pitchB, rowsB, 16u << s)) rc = GBD_ERR_CUDA;
     }
     if (rc != GBD_OK) goto out;
-    TcLaunch L{dtiles, dterms, (int)tiles.size(), prec, nullptr, nullptr, dC, derr, nullptr, nullptr, 256,
+    TcLaunch L{dtiles, dterms, (int)tiles.size(), prec, nullptr, nullptr, dC, derr, nullptr, nullptr, nullptr, 256,
                tc_stages(prec, 256)};
     if (!launch_tc_gemm(maps, L, sms, 0)) rc = GBD_ERR_CUDA;
     ck(cudaGetLastError());

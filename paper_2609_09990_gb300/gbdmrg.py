@@ -55,11 +55,15 @@ class gbd_stats(C.Structure):
                 ("tc_bytes", C.c_double), ("tc_flops_by_type", C.c_double * 4),
                 ("tc_gemm_ms_by_type", C.c_double * 4), ("tc_build_ms", C.c_double),
                 ("tc_build_phase_ms", C.c_double * 5), ("enlarge_host_ms", C.c_double), ("diag_ms", C.c_double),
-                ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double), ("env_wall_ms", C.c_double)]
+                ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double), ("env_wall_ms", C.c_double),
+                ("tc_stage_alg_bytes", C.c_double * 2), ("tc_stage_box_bytes", C.c_double * 4),
+                ("tc_stage_dense_bytes", C.c_double * 4), ("tc_gemm_ms_by_stage", C.c_double * 2)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
-        for k in ("tier_iterations", "tc_flops_by_type", "tc_gemm_ms_by_type", "tc_build_phase_ms"):
+        for k in ("tier_iterations", "tc_flops_by_type", "tc_gemm_ms_by_type", "tc_build_phase_ms",
+                  "tc_stage_alg_bytes", "tc_stage_box_bytes", "tc_stage_dense_bytes",
+                  "tc_gemm_ms_by_stage"):
             d[k] = list(d[k])
         return d
 
@@ -90,6 +94,7 @@ def lib():
         "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
         "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_tc_order": (C.c_int, [vp, C.c_int32]),
         "gbd_probe_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
         "gbd_init_state": (C.c_int, [vp]),
         "gbd_set_precision": (C.c_int, [vp, C.c_int32, C.c_int32]),
@@ -289,6 +294,9 @@ class Context:
 
     def set_tc_tile(self, ncap):
         self._check(self.L.gbd_set_tc_tile(self.ptr, ncap), "gbd_set_tc_tile")
+
+    def set_tc_order(self, order):
+        self._check(self.L.gbd_set_tc_order(self.ptr, order), "gbd_set_tc_order")
 
     def set_preconditioner(self, preconditioner):
         self._check(self.L.gbd_set_preconditioner(self.ptr, preconditioner), "gbd_set_preconditioner")

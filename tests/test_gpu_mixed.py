@@ -81,6 +81,15 @@ def test_tile_shape_does_not_change_sigma(G):
             ctx.set_tc_tile(cap)
             ys.append(ctx.apply_heff_prec(3, x, prec))
         assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2]), prec
+    # nor does the order in which the CTAs take the stage-B tiles
+    ctx.set_tc_tile(0)
+    for prec in (1, 3):
+        ys = []
+        for order in (0, 1, 2):
+            ctx.set_tc_order(order)
+            ys.append(ctx.apply_heff_prec(3, x, prec))
+        assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2]), prec
+    ctx.set_tc_order(0)
     ctx.close()
 
 
