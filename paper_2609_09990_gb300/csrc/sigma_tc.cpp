@@ -346,13 +346,23 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           P->alg_st[0] += (double)P->eb * nh * mso * ER.sdim[g.qin][si];
         }
     }
-    // one term list per group, shared by its tiles
+    // one term list per group, shared by its tiles; consecutive si whose
+    // sections are adjacent in both panels form one term (the same MMAs in
+    // the same order, with fewer, fuller boxes)
     const int gt0 = (int)terms.size();
     for (int si = 0; si < 4; ++si)
       if (g.mask >> si & 1) {
+        const int w = (int)up16(ER.sdim[g.qin][si]);
+        if ((int)terms.size() > gt0) {
+          TcTerm& t = terms.back();
+          if (t.ax + t.k == g.col[si] && t.bx + t.k == cpadR[g.qin][si]) {
+            t.k += w;
+            term_k.back() += ER.sdim[g.qin][si];
+            continue;
+          }
+        }
         term_k.push_back(ER.sdim[g.qin][si]);
-        terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)psi_row[g.qin], (int32_t)up16(ER.sdim[g.qin][si]),
-                         0, cpadR[g.qin][si]});
+        terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)psi_row[g.qin], w, 0, cpadR[g.qin][si]});
       }
     const int gt1 = (int)terms.size();
     for (int64_t m0 = 0; m0 < grows; m0 += 128)
