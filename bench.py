@@ -49,11 +49,11 @@ PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 METRIC = "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u22641e-6 Ha"
 # DRAM bytes (read + write, ncu) per algorithmic byte of tc_gemm_kernel, from
 # one --set full capture of `bench.py --sigma-probe 3` (TF32x3 sigma at the
-# central bond of cas16_m512: stage A 518 + 300 MB, stage B 1149 + 21 MB, for
-# 731 MB of algorithmic bytes).  The launches of a sweep move the same kinds
-# of panels, so traffic is reported as this ratio times their algorithmic
-# bytes per launch.
-TC_DRAM_PER_ALG_BYTE = (518.48e6 + 300.25472e6 + 1148.62e6 + 20.875264e6) / 730948448.0
+# central bond of cas16_m512: stage A 494.6 + 240.4 MB, stage B 650.1 + 35.7
+# MB, for 655.0 MB of algorithmic bytes).  The launches of a sweep move the
+# same kinds of panels, so traffic is reported as this ratio times their
+# algorithmic bytes per launch.
+TC_DRAM_PER_ALG_BYTE = (494.5536e6 + 240.401664e6 + 650.058496e6 + 35.650304e6) / 655036096.0
 DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
 
 

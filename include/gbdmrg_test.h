@@ -66,11 +66,11 @@ int gbd_set_graphs(gbd_ctx *ctx, int32_t enable);
 int gbd_set_tc_tile(gbd_ctx *ctx, int32_t ncap);
 
 /* Order in which the persistent tensor-core CTAs take the stage-B tiles of
- * the sigma (output sector q, 128-row block m0 of E_R, split-K chunk,
- * s_out block so, N tile n0): 0 (default) by (q, m0, chunk, so, n0), 1 by
- * (q, chunk, m0, so, n0), 2 by (q, so, chunk, n0, m0).  Tiles running at
- * the same time share operand boxes through L2 in different ways; every
- * tile computes the same products in the same order, so the result is
+ * the sigma (output sector q, 128-row block m0 of E_R(q), split-K chunk,
+ * N tile n0 of E_L(q)): 0 (default) by (q, m0, chunk, n0), 1 by
+ * (q, chunk, m0, n0), 2 by (q, chunk, n0, m0).  Tiles running at the same
+ * time share operand boxes through L2 in different ways; every tile
+ * computes the same products in the same order, so the result is
  * identical for all three. */
 int gbd_set_tc_order(gbd_ctx *ctx, int32_t order);
 

@@ -178,7 +178,7 @@ class Engine {
   bool use_graphs = true;     // replay the sigma launch sequences as CUDA graphs
   bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
-  int tc_order = 0;           // stage-B tile order: 0 (q,m0,chunk,so,n0), 1 (q,chunk,m0,so,n0), 2 (q,so,chunk,n0,m0)
+  int tc_order = 0;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
   int64_t tc_min_two_site = 4096;   // smaller two-site states: reduced-precision schedules use FP64
   // tier-1 (BF16/TF32) Davidson iterations and steps of the current and the

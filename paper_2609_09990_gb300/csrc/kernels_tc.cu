@@ -399,8 +399,10 @@ __global__ void bounded_wait_probe_kernel(int arrive, int* err, int* waited_ok) 
 }
 
 // ---------------------------------------------------------------- split-K sum
-// one thread per output element; the slots are summed in FP64 with four
-// interleaved partial sums combined in a fixed order (deterministic)
+// one thread per output element; the slots are summed in FP64 with eight
+// interleaved partial sums combined in a fixed order (deterministic).  The
+// eight loads of a round are independent, so a long slot list is not a
+// chain of dependent memory latencies.
 __global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, int64_t total,
                                  const float* __restrict__ part, double* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -414,16 +416,17 @@ __global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, in
     const int j = loc / R.m_valid, i = loc - j * R.m_valid;
     const int64_t ss = (int64_t)128 * R.n_stride;
     const float* p = part + R.slot0 + (int64_t)j * 128 + i;
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int s = 0;
-    for (; s + 4 <= R.nslot; s += 4) {
-      a0 += (double)p[s * ss];
-      a1 += (double)p[(s + 1) * ss];
-      a2 += (double)p[(s + 2) * ss];
-      a3 += (double)p[(s + 3) * ss];
+    for (; s + 8 <= R.nslot; s += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = p[(s + u) * ss];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += (double)v[u];
     }
-    for (; s < R.nslot; ++s) a0 += (double)p[s * ss];
-    out[R.out + (int64_t)j * R.ld + R.m0 + i] = (a0 + a1) + (a2 + a3);
+    for (int u = 0; s < R.nslot; ++s, ++u) a[u] += (double)p[s * ss];
+    out[R.out + (int64_t)j * R.ld + R.m0 + i] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
 }
 

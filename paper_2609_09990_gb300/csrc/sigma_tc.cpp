@@ -403,7 +403,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       order[i] = (int)i;
     }
     if (which == 1 && bkey.size() == tiles.size()) {
-      // bkey holds (q, m0, chunk, so, n0); the order names the priority
+      // bkey holds (q, m0, chunk, 0, n0); the order names the priority
       static const int perm[3][5] = {{0, 1, 2, 3, 4}, {0, 2, 1, 3, 4}, {0, 3, 2, 4, 1}};
       const int* pm = perm[tc_order];
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
