@@ -14,6 +14,8 @@ Modules
            for the wavefunction", item (i)) built term by term.
   dmrg  -- symmetry-blocked two-site DMRG with Davidson and SVD decimation
            (Fig. 2 and its section).
+  precond -- Davidson correction vectors: Jacobi, Olsen, shift-and-invert
+           inner PCG (Sec. "Computational details", preconditioner family).
 
 Every function cites the passage it follows.  Parity status of each
 function is stated in its docstring; all are pinned by tests under

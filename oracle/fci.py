@@ -158,10 +158,11 @@ class FCI:
         return g1, g2
 
 
-def davidson(matvec, diag, tol=1e-10, max_iter=200, max_space=24, nroots=1, guess=None):
+def davidson(matvec, diag, tol=1e-10, max_iter=200, max_space=24, nroots=1, guess=None, correction=None):
     """Plain Davidson (Davidson 1975) with the diagonal preconditioner
     t = -r / (diag - theta), two Gram-Schmidt passes and restart from the
-    lowest Ritz vectors."""
+    lowest Ritz vectors.  `correction(x, r, theta)`, when given, replaces
+    the diagonal step (the members of oracle/precond.py)."""
     N = diag.shape[0]
     if guess is None:
         V = []
@@ -192,9 +193,12 @@ def davidson(matvec, diag, tol=1e-10, max_iter=200, max_space=24, nroots=1, gues
         for i in range(nroots):
             if rn[i] < tol:
                 continue
-            den = diag - theta[i]
-            den = np.where(np.abs(den) < 1e-8, np.where(den >= 0, 1e-8, -1e-8), den)
-            t = -R[i] / den
+            if correction is not None:
+                t = np.array(correction(X[i], R[i], theta[i]), dtype=np.float64)
+            else:
+                den = diag - theta[i]
+                den = np.where(np.abs(den) < 1e-8, np.where(den >= 0, 1e-8, -1e-8), den)
+                t = -R[i] / den
             for _ in range(2):
                 for v in V:
                     t -= (v @ t) * v
