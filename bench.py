@@ -46,6 +46,7 @@ sys.path.insert(0, ROOT)
 from gbd_synth import WORKLOADS, make_integrals  # noqa: E402
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+PRECOND = {"diag": 0, "olsen": 2, "pcg": 3}
 METRIC = "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u22641e-6 Ha"
 # DRAM bytes (read + write, ncu) per algorithmic byte of tc_gemm_kernel, from
 # one --set full capture of `bench.py --sigma-probe 3` (TF32x3 sigma at the
@@ -132,6 +133,8 @@ def run_ours(args, rank, world):
     nsw = args.warmup + args.steps
     ctx.setup(h, chol, ne, 0, [M] * (nsw + 1), schedule(nsw + 1, args.tol), seed=seed, precision=prec,
               fp64_refine=args.refine)
+    if args.precond != "diag":
+        ctx.set_preconditioner(PRECOND[args.precond])
     ctx.init_state()
     for s in range(args.warmup):
         ctx.run_sweep(s)
@@ -165,6 +168,7 @@ def run_ours(args, rank, world):
     breakdown["tc_bytes_by_stage_GB"] = {
         nm: (st1["tc_stage_alg_bytes"][i] - st0["tc_stage_alg_bytes"][i]) / args.steps / 1e9
         for i, nm in enumerate(["A", "B"])}
+    breakdown["inner_pcg_matvecs"] = (st1["inner_matvecs"] - st0["inner_matvecs"]) / args.steps
     breakdown["davidson_iterations_by_tier"] = {
         t: (st1["tier_iterations"][i] - st0["tier_iterations"][i]) / args.steps
         for i, t in enumerate(["bf16_or_tf32", "tf32x3", "fp64"])}
@@ -385,6 +389,8 @@ def main():
     ap.add_argument("--batch-sweeps", type=int, default=2, help="sweeps per problem (batched64)")
     ap.add_argument("--workers", type=int, default=0, help="host worker threads (batched64; 0 = auto)")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--precond", default="diag", choices=sorted(PRECOND),
+                    help="Davidson correction of the timed sweeps (diag = Jacobi)")
     ap.add_argument("--tier2", default="tf32x3", choices=["tf32x3", "bf16x3"],
                     help="operands of the accurate Davidson tier")
     ap.add_argument("--sigma-probe", type=int, default=0, help="profiling driver: central sigma of cas16_m512 "
@@ -436,6 +442,8 @@ def main():
               "n_orb": wl["n_orb"], "bond_dim": wl["M"], "davidson_tol": args.tol,
               "l2": "inputs larger than L2 (environments of all bonds, > 1 GB)",
               "parallelism": f"replicas x{world}"}
+    if args.precond != "diag":
+        config["davidson_correction"] = args.precond
     if args.impl == "reference":
         if rank != 0:
             return

@@ -46,8 +46,25 @@ extern "C" {
 #define GBD_TF32 1
 #define GBD_BF16 2
 
+/* Davidson correction t from the Ritz pair (theta, x) and residual r, with
+ * den = d - theta kept at least 1e-8 from zero (d: H_eff diagonal).  The
+ * paper names a run-time-selectable family: Jacobi, deflation-aware
+ * diagonal, Olsen, and shift-and-invert inner PCG with an indefiniteness
+ * guard (Sec. "Computational details").  None changes the converged energy.
+ *   GBD_PRECOND_DIAG    Jacobi: t = -r / den
+ *   GBD_PRECOND_LEARNED diagonal step scaled by a trained network (below)
+ *   GBD_PRECOND_OLSEN   t = -(r - eps x) / den, eps = (x.r/den)/(x.x/den): x.t = 0
+ *   GBD_PRECOND_PCG     t from at most 4 preconditioned CG steps on
+ *                       (1 - xx^T)(H_eff - theta)(1 - xx^T) t = -r, t orthogonal to x
+ *                       (preconditioner: the Olsen-projected den), stopping at
+ *                       |residual| < 0.1 |r| or at a direction of non-positive
+ *                       curvature; each step costs one extra sigma build.
+ * The deflation-aware diagonal serves deflated excited-state targets, which
+ * this library does not solve for. */
 #define GBD_PRECOND_DIAG 0
 #define GBD_PRECOND_LEARNED 1
+#define GBD_PRECOND_OLSEN 2
+#define GBD_PRECOND_PCG 3
 
 typedef struct gbd_ctx gbd_ctx;
 
@@ -79,7 +96,7 @@ typedef struct {
   int32_t davidson_max_iter;      /* per two-site step (0 -> 100) */
   int32_t davidson_max_subspace;  /* restart size limit (0 -> 24) */
   int32_t precision;              /* GBD_FP64 | GBD_TF32 | GBD_BF16 */
-  int32_t preconditioner;         /* GBD_PRECOND_DIAG | GBD_PRECOND_LEARNED */
+  int32_t preconditioner;         /* GBD_PRECOND_DIAG | _LEARNED | _OLSEN | _PCG */
   uint64_t seed;
   double svd_cutoff;
   int32_t fp64_refine;            /* GBD_TF32/GBD_BF16: at most this many FP64

@@ -54,6 +54,8 @@ typedef struct {
   double tc_stage_box_bytes[4]; /* bytes the TMA boxes request from L2: stage A (A box, B box), stage B (A, B) */
   double tc_stage_dense_bytes[4]; /* the valid rows x K of those boxes, without row, K or box-width padding */
   double tc_gemm_ms_by_stage[2];  /* tc_gemm_ms split into stage A and stage B */
+  int64_t davidson_iterations;    /* outer Davidson iterations (all tiers) */
+  int64_t inner_matvecs;          /* sigma builds inside inner-PCG corrections (in n_sigma too) */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or
@@ -177,9 +179,17 @@ int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32
  * absolute error and the largest |reference| element. */
 int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t nterms, uint64_t seed,
                     double *max_err, double *max_ref);
+/* One Davidson correction on the device, as the solver computes it: from
+ * the Ritz vector x (|x| = 1), sx = H x and theta, r = sx - theta x and
+ * t = the correction of kind GBD_PRECOND_DIAG (Jacobi) or GBD_PRECOND_OLSEN
+ * (see gbdmrg.h).  Host arrays of length n >= 1; returns |r|^2.
+ * GBD_ERR_ARG for NULL pointers, n < 1 or another kind. */
+int gbd_correction_selftest(int32_t device, int32_t kind, int64_t n, const double *x, const double *sx,
+                            const double *diag, double theta, double *r_out, double *t_out, double *rr);
 /* Failure detection without a fault: one bounded mbarrier wait (the helper
  * every role of the tensor-core kernel uses).  arrive = 0: nothing completes
- * the barrier, the wait runs out after its poll limit (milliseconds) and
+ * the barrier, the wait runs out after its poll limit (2^22 polls, a few
+ * seconds) and
  * returns with *err_flag = 1, *waited_ok = 0; arrive = 1: *err_flag = 0,
  * *waited_ok = 1. */
 int gbd_wait_selftest(int32_t device, int32_t arrive, int32_t *err_flag, int32_t *waited_ok);

@@ -88,7 +88,7 @@ int validate(gbd_ctx* c, const gbd_problem* p, const gbd_schedule* s) {
   if (s->precision != GBD_FP64 && s->precision != GBD_TF32 && s->precision != GBD_BF16)
     return fail(c, GBD_ERR_ARG, "unknown precision");
   if (s->fp64_refine < 0) return fail(c, GBD_ERR_ARG, "fp64_refine < 0");
-  if (s->preconditioner != GBD_PRECOND_DIAG && s->preconditioner != GBD_PRECOND_LEARNED)
+  if (s->preconditioner < GBD_PRECOND_DIAG || s->preconditioner > GBD_PRECOND_PCG)
     return fail(c, GBD_ERR_ARG, "unknown preconditioner");
   if (s->svd_cutoff < 0 || !std::isfinite(s->svd_cutoff)) return fail(c, GBD_ERR_ARG, "svd_cutoff invalid");
   return GBD_OK;
@@ -300,7 +300,7 @@ int gbd_set_tc_order(gbd_ctx* ctx, int32_t order) {
 int gbd_set_preconditioner(gbd_ctx* ctx, int32_t preconditioner) {
   return guarded(ctx, [&]() {
     if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
-    if (preconditioner != GBD_PRECOND_DIAG && preconditioner != GBD_PRECOND_LEARNED)
+    if (preconditioner < GBD_PRECOND_DIAG || preconditioner > GBD_PRECOND_PCG)
       return fail(ctx, GBD_ERR_ARG, "unknown preconditioner");
     if (preconditioner == GBD_PRECOND_LEARNED && !ctx->eng->mlp_loaded)
       return fail(ctx, GBD_ERR_STATE, "no preconditioner weights loaded");
@@ -623,6 +623,8 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->truncate_eig_ms = t.trunc_eig_ms;
   s->env_wall_ms = t.env_wall_ms;
   for (int i = 0; i < 5; ++i) s->tc_build_phase_ms[i] = t.tcb_ms[i];
+  s->davidson_iterations = t.davidson_iters;
+  s->inner_matvecs = t.inner_matvecs;
   for (int i = 0; i < 2; ++i) {
     s->tc_stage_alg_bytes[i] = t.tc_alg_st[i];
     s->tc_stage_box_bytes[2 * i] = t.tc_box_st[i][0];
@@ -743,3 +745,34 @@ double gbd_mps_init_value(uint64_t seed, int32_t site, int32_t na, int32_t nb, i
 }
 
 }  // extern "C"
+
+int gbd_correction_selftest(int32_t device, int32_t kind, int64_t n, const double* x, const double* sx,
+                            const double* diag, double theta, double* r_out, double* t_out, double* rr) {
+  using namespace gbd;
+  if (!x || !sx || !diag || !r_out || !t_out || !rr || n < 1) return GBD_ERR_ARG;
+  if (kind != GBD_PRECOND_DIAG && kind != GBD_PRECOND_OLSEN) return GBD_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return GBD_ERR_CUDA;
+  const int nblk = reduction_blocks(n);
+  const size_t vb = (size_t)n * sizeof(double);
+  double* d = nullptr;
+  const size_t total = 5 * (size_t)n + 2 * (size_t)nblk + 4;
+  if (cudaMalloc(&d, total * sizeof(double)) != cudaSuccess) return GBD_ERR_OOM;
+  double *dx = d, *dsx = d + n, *dd = d + 2 * n, *dr = d + 3 * n, *dt = d + 4 * n, *part = d + 5 * n,
+         *sums = part + 2 * nblk;
+  int rc = GBD_OK;
+  if (cudaMemcpy(dx, x, vb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dsx, sx, vb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dd, diag, vb, cudaMemcpyHostToDevice) != cudaSuccess) {
+    rc = GBD_ERR_CUDA;
+  } else {
+    launch_residual_precond(dx, dsx, dd, theta, n, dr, dt, part, nblk, sums + 2, 0);
+    if (kind == GBD_PRECOND_OLSEN) launch_projected_precond(dr, dx, dd, theta, -1.0, n, dt, part, nblk, sums, 0);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(r_out, dr, vb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(t_out, dt, vb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(rr, sums + 2, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = GBD_ERR_CUDA;
+  }
+  cudaFree(d);
+  return rc;
+}

@@ -1178,6 +1178,10 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
   double* dorth = dalloc<double>(max_space);        // Gram-Schmidt overlaps
   double* drow = dalloc<double>(max_space + 2);     // [V^T s_k, |t|^2]
   double* coef = dalloc<double>((size_t)max_space * keep + max_space);
+  // Olsen / inner PCG: two sums, and the PCG vectors (residual, z, p, A p)
+  const int pk = sched.precond;
+  double* dsums = (pk == 2 || pk == 3) ? dalloc<double>(4) : nullptr;
+  double* cg = pk == 3 ? dalloc<double>((size_t)4 * n) : nullptr;
   std::vector<double> Hs((size_t)max_space * max_space, 0.0), hd(max_space + 2);
   auto d2h = [&](double* host, const double* dev, int cnt) {
     CK(cudaMemcpyAsync(host, dev, cnt * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -1192,6 +1196,53 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
   auto dots = [&](const double* base, int k, const double* vec, double* out_dev) {
     launch_multi_dot(base, n, k, vec, n, out_dev, partial, nblk, stream);
     stats.launches += 2;
+  };
+  auto dot_host = [&](const double* a, const double* b) {
+    dots(a, 1, b, dsums + 2);
+    double v;
+    d2h(&v, dsums + 2, 1);
+    return v;
+  };
+  // shift-and-invert inner PCG on the projected correction equation
+  // (I - x x^T)(H - theta)(I - x x^T) t = -r, t orthogonal to x, from t = 0
+  // with the projected diagonal preconditioner; a direction of non-positive
+  // curvature ends it (on the first direction the result is the
+  // preconditioned residual, i.e. the Olsen correction)
+  auto inner_pcg = [&](const double* xr, const double* rr_vec, double th, double* tout) {
+    double *res = cg, *z = cg + n, *p = cg + 2 * n, *ap = cg + 3 * n;
+    launch_axpby(res, -1.0, rr_vec, 0.0, n, stream);
+    const double xr0 = dot_host(xr, res);
+    launch_axpby(res, -xr0, xr, 1.0, n, stream);
+    CK(cudaMemsetAsync(tout, 0, n * sizeof(double), stream));
+    launch_projected_precond(res, xr, diag, th, 1.0, n, z, partial, nblk, dsums, stream);
+    CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    stats.launches += 6;
+    double rz = dot_host(res, z);
+    const double nrhs = std::sqrt(std::max(dot_host(res, res), 0.0));
+    for (int j = 0; j < pcg_steps; ++j) {
+      op(p, ap);
+      stats.inner_matvecs++;
+      launch_axpby(ap, -th, p, 1.0, n, stream);
+      const double xa = dot_host(xr, ap);
+      launch_axpby(ap, -xa, xr, 1.0, n, stream);
+      stats.launches += 2;
+      const double pap = dot_host(p, ap);
+      if (!(pap > 0.0)) {
+        if (j == 0) CK(cudaMemcpyAsync(tout, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+        break;
+      }
+      const double alpha = rz / pap;
+      launch_axpby(tout, alpha, p, 1.0, n, stream);
+      launch_axpby(res, -alpha, ap, 1.0, n, stream);
+      stats.launches += 2;
+      if (std::sqrt(std::max(dot_host(res, res), 0.0)) < pcg_rel_tol * nrhs) break;
+      launch_projected_precond(res, xr, diag, th, 1.0, n, z, partial, nblk, dsums, stream);
+      const double rz1 = dot_host(res, z);
+      launch_axpby(p, 1.0, z, rz1 / rz, n, stream);
+      stats.launches += 4;
+      rz = rz1;
+    }
+    if (pcg_steps == 0) CK(cudaMemcpyAsync(tout, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   };
   // v0 = psi / |psi|, s0 = H v0
   dots(psi, 1, psi, drow + max_space + 1);
@@ -1265,6 +1316,11 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
         launch_mlp_precond(r, diag, scalars(theta, rn, it), n, mlp_w16, t, dbad, stream);
         stats.launches++;
       }
+    } else if (pk == 2) {
+      launch_projected_precond(r, x, diag, theta, -1.0, n, t, partial, nblk, dsums, stream);   // Olsen
+      stats.launches += 3;
+    } else if (pk == 3) {
+      inner_pcg(x, r, theta, t);
     }
     if (k == max_space) {
       int kk = std::min(keep, k);
@@ -1323,6 +1379,8 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
   for (void* p : {(void*)V, (void*)S, (void*)Vt, (void*)St, (void*)x, (void*)sx, (void*)r, (void*)t, (void*)partial,
                   (void*)dres, (void*)dorth, (void*)drow, (void*)coef})
     dfree(p);
+  if (dsums) dfree(dsums);
+  if (cg) dfree(cg);
   return theta;
 }
 

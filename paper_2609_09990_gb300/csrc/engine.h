@@ -79,6 +79,7 @@ struct Stats {
   int64_t n_sigma_tc = 0;
   int64_t n_sigma = 0, n_steps = 0, launches = 0, h2d = 0, d2h = 0;
   int64_t davidson_iters = 0, precond_fallbacks = 0;
+  int64_t inner_matvecs = 0;   // sigma builds inside the inner PCG corrections
   int64_t tier_iters[3] = {0, 0, 0};
   double max_final_residual = 0, sum_final_residual = 0;   // over Davidson solves
   int64_t graph_launches = 0, autotune_trials = 0;
@@ -98,6 +99,7 @@ struct Stats {
     sigma_flops_exec += o.sigma_flops_exec; tc_ms += o.tc_ms; tc_flops += o.tc_flops;
     n_sigma_tc += o.n_sigma_tc; n_sigma += o.n_sigma; n_steps += o.n_steps; launches += o.launches;
     h2d += o.h2d; d2h += o.d2h; davidson_iters += o.davidson_iters; precond_fallbacks += o.precond_fallbacks;
+    inner_matvecs += o.inner_matvecs;
     for (int i = 0; i < 3; ++i) tier_iters[i] += o.tier_iters[i];
     max_final_residual = std::max(max_final_residual, o.max_final_residual);
     sum_final_residual += o.sum_final_residual;
@@ -178,6 +180,8 @@ class Engine {
   bool use_graphs = true;     // replay the sigma launch sequences as CUDA graphs
   bool autotune = true;       // pick the tensor-core tile shape per shape class by timing
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
+  int pcg_steps = 4;          // inner PCG (preconditioner 3): at most this many matvecs per correction
+  double pcg_rel_tol = 0.1;   // ... stopping when |residual| < pcg_rel_tol |r|
   int tc_order = 0;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
   int64_t tc_min_two_site = 4096;   // smaller two-site states: reduced-precision schedules use FP64

@@ -149,6 +149,14 @@ void launch_absmax(const double* x, int64_t n, double* out, cudaStream_t s);
 void launch_residual_precond(const double* x, const double* sx, const double* diag, double theta, int64_t n,
                              double* r, double* t, double* partial, int nblk, double* out_dev, cudaStream_t s);
 void launch_scale(double* x, double a, int64_t n, cudaStream_t s);
+// out = K^-1 (scale v) - (x . K^-1 scale v)/(x . K^-1 x) K^-1 x with K = the
+// guarded d - theta (x . out = 0): the Olsen correction for v = r, scale -1,
+// and the preconditioner of the inner PCG.  Three launches, no host sync;
+// partial holds 2 * nblk doubles, sums_dev 2.
+void launch_projected_precond(const double* v, const double* x, const double* diag, double theta, double scale,
+                              int64_t n, double* out, double* partial, int nblk, double* sums_dev, cudaStream_t s);
+// y = a x + b y
+void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t s);
 int reduction_blocks(int64_t n);
 
 }  // namespace gbd

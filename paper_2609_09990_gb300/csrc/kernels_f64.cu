@@ -188,6 +188,13 @@ __global__ void normalize_kernel(const double* __restrict__ t, const double* __r
     out[i] = t[i] * s;
 }
 
+// diag - theta, kept at least 1e-8 away from zero (sign kept, + for 0)
+__device__ __forceinline__ double guarded_den(double d, double theta) {
+  double den = d - theta;
+  if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
+  return den;
+}
+
 // r = sx - theta x ; t = -r / clamp(diag - theta) ; partial sums of r^2
 __global__ void residual_precond_kernel(const double* __restrict__ x, const double* __restrict__ sx,
                                         const double* __restrict__ diag, double theta, int64_t n,
@@ -196,13 +203,47 @@ __global__ void residual_precond_kernel(const double* __restrict__ x, const doub
   for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
     double ri = sx[i] - theta * x[i];
     r[i] = ri;
-    double den = diag[i] - theta;
-    if (fabs(den) < 1e-8) den = den >= 0.0 ? 1e-8 : -1e-8;
-    t[i] = -ri / den;
+    t[i] = -ri / guarded_den(diag[i], theta);
     s = fma(ri, ri, s);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// projected diagonal preconditioner, pass 1: out = scale v / den; partial
+// sums of x . out (row 0) and x . x / den (row 1)
+__global__ void kdiv_kernel(const double* __restrict__ v, const double* __restrict__ x,
+                            const double* __restrict__ diag, double theta, double scale, int64_t n, double* out,
+                            double* partial) {
+  const int nblk = gridDim.x;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)RED_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RED_THREADS) {
+    const double den = guarded_den(diag[i], theta);
+    const double o = scale * v[i] / den;
+    out[i] = o;
+    s1 = fma(x[i], o, s1);
+    s2 = fma(x[i], x[i] / den, s2);
+  }
+  s1 = block_sum(s1);
+  s2 = block_sum(s2);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s1;
+    partial[nblk + blockIdx.x] = s2;
+  }
+}
+
+// pass 2: out -= (sums[0] / sums[1]) x / den, so that x . out = 0
+__global__ void kproj_kernel(const double* __restrict__ x, const double* __restrict__ diag, double theta,
+                             const double* __restrict__ sums, int64_t n, double* out) {
+  const double eps = sums[1] != 0.0 ? sums[0] / sums[1] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] -= eps * x[i] / guarded_den(diag[i], theta);
+}
+
+// y = a x + b y
+__global__ void axpby_kernel(double* y, double a, const double* __restrict__ x, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], b * y[i]);
 }
 
 __global__ void scale_kernel(double* x, double a, int64_t n) {
@@ -263,6 +304,17 @@ void launch_residual_precond(const double* x, const double* sx, const double* di
                              double* r, double* t, double* partial, int nblk, double* out_dev, cudaStream_t s) {
   residual_precond_kernel<<<nblk, RED_THREADS, 0, s>>>(x, sx, diag, theta, n, r, t, partial);
   finish_sums<<<1, RED_THREADS, 0, s>>>(partial, nblk, 1, out_dev);
+}
+
+void launch_projected_precond(const double* v, const double* x, const double* diag, double theta, double scale,
+                              int64_t n, double* out, double* partial, int nblk, double* sums_dev, cudaStream_t s) {
+  kdiv_kernel<<<nblk, RED_THREADS, 0, s>>>(v, x, diag, theta, scale, n, out, partial);
+  finish_sums<<<2, RED_THREADS, 0, s>>>(partial, nblk, 2, sums_dev);
+  kproj_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, diag, theta, sums_dev, n, out);
+}
+
+void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t s) {
+  axpby_kernel<<<grid_for(n, 256), 256, 0, s>>>(y, a, x, b, n);
 }
 
 void launch_scale(double* x, double a, int64_t n, cudaStream_t s) {

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgbdmrg.so")
 GBD_OK = 0
 GBD_ERR_ARG, GBD_ERR_OOM, GBD_ERR_CUDA, GBD_ERR_NOCONV, GBD_ERR_TIMEOUT, GBD_ERR_STATE = -1, -2, -3, -4, -5, -6
 GBD_FP64, GBD_TF32, GBD_BF16 = 0, 1, 2
-GBD_PRECOND_DIAG, GBD_PRECOND_LEARNED = 0, 1
+GBD_PRECOND_DIAG, GBD_PRECOND_LEARNED, GBD_PRECOND_OLSEN, GBD_PRECOND_PCG = 0, 1, 2, 3
 ERRORS = {-1: "GBD_ERR_ARG", -2: "GBD_ERR_OOM", -3: "GBD_ERR_CUDA", -4: "GBD_ERR_NOCONV",
           -5: "GBD_ERR_TIMEOUT", -6: "GBD_ERR_STATE"}
 
@@ -57,7 +57,8 @@ class gbd_stats(C.Structure):
                 ("tc_build_phase_ms", C.c_double * 5), ("enlarge_host_ms", C.c_double), ("diag_ms", C.c_double),
                 ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double), ("env_wall_ms", C.c_double),
                 ("tc_stage_alg_bytes", C.c_double * 2), ("tc_stage_box_bytes", C.c_double * 4),
-                ("tc_stage_dense_bytes", C.c_double * 4), ("tc_gemm_ms_by_stage", C.c_double * 2)]
+                ("tc_stage_dense_bytes", C.c_double * 4), ("tc_gemm_ms_by_stage", C.c_double * 2),
+                ("davidson_iterations", C.c_int64), ("inner_matvecs", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -116,6 +117,8 @@ def lib():
                                             C.c_int32, C.c_int32]),
         "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
         "gbd_wait_selftest": (C.c_int, [C.c_int32, C.c_int32, _ip, _ip]),
+        "gbd_correction_selftest": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _dp, _dp, _dp, C.c_double, _dp, _dp,
+                                               _dp]),
         "gbd_tc_selftest": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                       _dp, _dp]),
         "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
@@ -487,6 +490,18 @@ def tc_selftest(prec, M, N, K, nterms, seed=1, device=0):
     if rc != GBD_OK:
         raise GbdError(f"gbd_tc_selftest: {ERRORS.get(rc, rc)}")
     return e.value, r.value
+
+
+def correction_selftest(kind, x, sx, diag, theta, device=0):
+    """(r, t, |r|^2) of one Davidson correction on the device (kind: GBD_PRECOND_DIAG or _OLSEN)."""
+    x, sx, diag = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, sx, diag))
+    n = x.size
+    r, t, rr = np.empty(n), np.empty(n), C.c_double()
+    rc = lib().gbd_correction_selftest(device, kind, n, _d(x), _d(sx), _d(diag), float(theta), _d(r), _d(t),
+                                       C.byref(rr))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_correction_selftest: {ERRORS.get(rc, rc)}")
+    return r, t, rr.value
 
 
 def wait_selftest(arrive, device=0):

@@ -1,0 +1,81 @@
+"""The Davidson correction family on the GPU: Jacobi and Olsen corrections
+element by element against the oracle, and converged energies that do not
+depend on the correction (Jacobi, Olsen, inner PCG)."""
+import numpy as np
+import pytest
+
+from gbd_synth import make_integrals
+from oracle import fci, fock, precond
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2609_09990_gb300 import build, gbdmrg
+    build.build()
+    return gbdmrg
+
+
+def ritz_like(n, seed):
+    # unit x, sx with theta = x . sx (so r is orthogonal to x), a diagonal
+    # with a few entries within the 1e-8 guard of theta
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=n)
+    x /= np.linalg.norm(x)
+    sx = rng.normal(size=n) + 3.0 * x
+    theta = float(x @ sx)
+    d = theta + rng.normal(size=n) * 2.0
+    if n > 8:
+        d[[1, 3, 5]] = theta + np.array([0.0, 4e-9, -7e-9])
+    return x, sx, d, theta
+
+
+@pytest.mark.parametrize("n", [1, 7, 1000, 100003])
+@pytest.mark.parametrize("kind", ["diag", "olsen"])
+def test_correction_matches_oracle(G, kind, n):
+    x, sx, d, theta = ritz_like(n, n + 17)
+    code = G.GBD_PRECOND_DIAG if kind == "diag" else G.GBD_PRECOND_OLSEN
+    r, t, rr = G.correction_selftest(code, x, sx, d, theta)
+    r_ref = sx - theta * x
+    t_ref = precond.jacobi_correction(r_ref, d, theta) if kind == "diag" else \
+        precond.olsen_correction(x, r_ref, d, theta)
+    # r = sx - theta x may be evaluated with a fused multiply-add
+    assert np.abs(r - r_ref).max() <= 1e-15 * (np.abs(sx).max() + abs(theta))
+    assert abs(rr - r_ref @ r_ref) <= 1e-12 * (r_ref @ r_ref)
+    assert np.abs(t - t_ref).max() <= 1e-12 * np.abs(t_ref).max()
+    if kind == "olsen" and n > 1:
+        assert abs(x @ t) <= 1e-12 * np.linalg.norm(t)
+
+
+def test_converged_energy_does_not_depend_on_the_correction(G):
+    # CAS(6,6) at M = 64 is exact: every correction reaches the FCI energy
+    h, chol = make_integrals(6, 8, 5)
+    e_fci = np.linalg.eigvalsh(fci.FCI(h, fock.eri_from_chol(chol), 3, 3).dense_h())[0]
+    out = {}
+    for kind in (G.GBD_PRECOND_DIAG, G.GBD_PRECOND_OLSEN, G.GBD_PRECOND_PCG):
+        ctx = G.Context(0)
+        r = ctx.solve(h, chol, 6, 0, [64] * 4, [1e-9] * 4, seed=5, preconditioner=kind)
+        st = ctx.stats()
+        assert (st["inner_matvecs"] > 0) == (kind == G.GBD_PRECOND_PCG)
+        out[kind] = (r["energy"], st["davidson_iterations"])
+        ctx.close()
+    for kind, (e, _) in out.items():
+        assert abs(e - e_fci) < 1e-9, (kind, e - e_fci)
+
+
+def test_reduced_precision_solve_with_each_correction(G):
+    # the mixed tiers with Olsen and inner-PCG corrections converge to the
+    # same sweep energies as with Jacobi, to the tiers' accuracy
+    h, chol = make_integrals(10, 12, 9)
+    res = {}
+    for kind in (G.GBD_PRECOND_DIAG, G.GBD_PRECOND_OLSEN, G.GBD_PRECOND_PCG):
+        ctx = G.Context(0)
+        ctx.set_tc_min_two_site(0)
+        r = ctx.solve(h, chol, 10, 0, [96] * 4, [1e-6] * 4, seed=9, precision=G.GBD_TF32,
+                      preconditioner=kind)
+        res[kind] = r["sweep_energies"]
+        ctx.close()
+    ref = res[G.GBD_PRECOND_DIAG]
+    for kind, se in res.items():
+        assert abs(se[-1] - ref[-1]) < 2e-6, (kind, se[-1] - ref[-1])
