@@ -14,6 +14,9 @@ Modules
            for the wavefunction", item (i)) built term by term.
   dmrg  -- symmetry-blocked two-site DMRG with Davidson and SVD decimation
            (Fig. 2 and its section).
+  states -- excited states of the sector: the eigenpairs that deflated
+           sweeps converge to, with <S^2> from the 2-RDM (Sec. "Excited
+           states: dual-penalty deflation and NACMEs").
   precond -- Davidson correction vectors: Jacobi, Olsen, shift-and-invert
            inner PCG (Sec. "Computational details", preconditioner family).
 

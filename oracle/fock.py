@@ -130,6 +130,22 @@ def rdms(vec: np.ndarray, states: np.ndarray, n_orb: int):
     return g1, g2
 
 
+def spin_square(n_orb: int) -> sp.csr_matrix:
+    """S^2 = S_z^2 + (S_+ S_- + S_- S_+)/2 with S_+ = sum_p a+_pa a_pb,
+    S_- = sum_p a+_pb a_pa, S_z = 1/2 sum_p (n_pa - n_pb), from the operator
+    strings (the textbook definition)."""
+    dim = 1 << (2 * n_orb)
+    Sp = sp.csr_matrix((dim, dim))
+    Sm = sp.csr_matrix((dim, dim))
+    Sz = sp.csr_matrix((dim, dim))
+    for p in range(n_orb):
+        a, b = 2 * p, 2 * p + 1
+        Sp = Sp + apply_string([(a, True), (b, False)], dim)
+        Sm = Sm + apply_string([(b, True), (a, False)], dim)
+        Sz = Sz + 0.5 * (apply_string([(a, True), (a, False)], dim) - apply_string([(b, True), (b, False)], dim))
+    return (Sz @ Sz + 0.5 * (Sp @ Sm + Sm @ Sp)).tocsr()
+
+
 def eri_from_chol(chol: np.ndarray) -> np.ndarray:
     """(pq|rs) = sum_Q L^Q_pq L^Q_rs (Sec. "The DMRG-QD-NEVPT2 energy",
     Cholesky-factorised two-electron tensor)."""
