@@ -131,6 +131,32 @@ const char *gbd_last_error(const gbd_ctx *ctx);
 int gbd_solve(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule,
               gbd_result *result);
 
+/* Excited states by penalty deflation (Sec. "Excited states: dual-penalty
+ * deflation and NACMEs").  Roots are solved one after another, each from
+ * its own seeded initial MPS (seed + attempt), with every earlier root kept
+ * on the device and added to H_eff of every two-site step as
+ * penalty * |phi_j><phi_j|.  Here phi_j is that root projected onto the
+ * current two-site basis through overlap environments, and the Davidson
+ * diagonal gains penalty * phi_j^2 (the deflation-aware diagonal).
+ * penalty (Ha, > 0) must exceed the gap between the wanted roots and the
+ * ones below them.
+ *
+ * Root selection by <S^2>: each converged root gets
+ * <S^2> = -1/2 sum_pq rdm2[p,q,q,p] - N^2/4 + N from its 2-RDM.  When
+ * target_s2 >= 0, a root with |<S^2> - target_s2| >= 0.1 is not reported
+ * but stays deflated (an M_s = 0 triplet, say, when singlets are wanted).
+ * At most n_states + max_extra roots are solved.  The dual penalty of the
+ * paper (lambda S_z^2 + mu (N - N_el)^2) is zero in the (N_alpha, N_beta)
+ * sector this solver is blocked by, so it is not applied.
+ *
+ * results[0 .. *n_found-1] are filled as by gbd_solve: energy = <H> of the
+ * root without the penalty; sweep energies are the Ritz values with it.
+ * s2[i] is the root's <S^2>.  Returns GBD_OK when n_states roots were
+ * found, else GBD_ERR_NOCONV with the roots found so far in place. */
+int gbd_solve_states(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule, int32_t n_states,
+                     double penalty, double target_s2, int32_t max_extra, gbd_result *results, double *s2,
+                     int32_t *n_found);
+
 /* Many independent active spaces in one call (the paper solves one active
  * space per call; batching is this library's addition).  problems[i] is
  * solved with schedules[i] into results[i] (caller-owned, as for

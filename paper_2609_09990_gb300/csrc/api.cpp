@@ -175,6 +175,59 @@ int gbd_solve(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, gbd_res
   });
 }
 
+int gbd_solve_states(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, int32_t n_states, double penalty,
+                     double target_s2, int32_t max_extra, gbd_result* results, double* s2, int32_t* n_found) {
+  return guarded(ctx, [&]() {
+    if (!results || !s2 || !n_found) return fail(ctx, GBD_ERR_ARG, "results, s2 or n_found is NULL");
+    if (n_states < 1 || max_extra < 0) return fail(ctx, GBD_ERR_ARG, "n_states < 1 or max_extra < 0");
+    if (!(penalty > 0) || !std::isfinite(penalty) || !std::isfinite(target_s2))
+      return fail(ctx, GBD_ERR_ARG, "penalty must be positive and finite");
+    *n_found = 0;
+    int rc = setup(ctx, p, s);
+    if (rc != GBD_OK) return rc;
+    gbd::Engine& e = *ctx->eng;
+    if (s->preconditioner == GBD_PRECOND_LEARNED && !e.mlp_loaded)
+      return fail(ctx, GBD_ERR_STATE, "learned preconditioner requested but no weights are loaded");
+    const int n = p->n_orb;
+    const uint64_t seed0 = e.sched.seed;
+    e.defl_w = penalty;
+    std::vector<double> g1((size_t)n * n), g2((size_t)n * n * n * n), se((size_t)s->n_sweeps);
+    int found = 0;
+    for (int a = 0; a < n_states + max_extra && found < n_states; ++a) {
+      e.sched.seed = seed0 + (uint64_t)a;
+      e.init_state();
+      e.ov_init();
+      for (int i = 0; i < s->n_sweeps; ++i) se[i] = e.sweep(i) + p->e_core;
+      const double energy = e.final_energy() + p->e_core;
+      e.rdms(g1.data(), g2.data());
+      // <S^2> = -1/2 sum_pq Gamma_pqqp - N^2/4 + N
+      double t = 0;
+      for (int pp = 0; pp < n; ++pp)
+        for (int q = 0; q < n; ++q) t += g2[(((size_t)pp * n + q) * n + q) * n + pp];
+      const double N = p->n_elec;
+      const double v = -0.5 * t - N * N / 4.0 + N;
+      if (target_s2 < 0 || std::fabs(v - target_s2) < 0.1) {
+        gbd_result& r = results[found];
+        r.energy = energy;
+        if (r.sweep_energies) std::copy(se.begin(), se.end(), r.sweep_energies);
+        if (r.rdm1) std::copy(g1.begin(), g1.end(), r.rdm1);
+        if (r.rdm2) std::copy(g2.begin(), g2.end(), r.rdm2);
+        r.max_discarded_weight = e.stats.max_discarded;
+        r.n_matvec = e.stats.n_sigma;
+        r.status = GBD_OK;
+        s2[found] = v;
+        ++found;
+        *n_found = found;
+      }
+      if (found < n_states) e.store_state();
+    }
+    e.clear_states();
+    e.sched.seed = seed0;
+    if (found < n_states) return fail(ctx, GBD_ERR_NOCONV, "fewer roots of the target <S^2> than requested");
+    return GBD_OK;
+  });
+}
+
 int gbd_set_batch_workers(gbd_ctx* ctx, int32_t workers) {
   if (!ctx || workers < 0) return GBD_ERR_ARG;
   ctx->batch_workers = workers;

@@ -310,6 +310,7 @@ Engine::~Engine() {
   for (auto& e : Lenv) free_env(e);
   for (auto& e : Renv) free_env(e);
   for (auto& s : sites) free_site(s);
+  clear_states();
   if (psi) dfree(psi);
   cudaStreamSynchronize(stream);
   if (ev0) cudaEventDestroy(ev0);
@@ -1197,6 +1198,17 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     launch_multi_dot(base, n, k, vec, n, out_dev, partial, nblk, stream);
     stats.launches += 2;
   };
+  // H_eff plus the deflation penalty w sum_j phi_j (phi_j . x)
+  const int nphi = defl_phi ? (int)defl.size() : 0;
+  double* dpen = nphi ? dalloc<double>(nphi) : nullptr;
+  auto opp = [&](const double* a, double* b) {
+    op(a, b);
+    if (nphi) {
+      dots(defl_phi, nphi, a, dpen);
+      launch_lincomb(b, defl_phi, n, dpen, nphi, n, 1, stream, defl_w);
+      stats.launches++;
+    }
+  };
   auto dot_host = [&](const double* a, const double* b) {
     dots(a, 1, b, dsums + 2);
     double v;
@@ -1220,7 +1232,7 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     double rz = dot_host(res, z);
     const double nrhs = std::sqrt(std::max(dot_host(res, res), 0.0));
     for (int j = 0; j < pcg_steps; ++j) {
-      op(p, ap);
+      opp(p, ap);
       stats.inner_matvecs++;
       launch_axpby(ap, -th, p, 1.0, n, stream);
       const double xa = dot_host(xr, ap);
@@ -1248,7 +1260,7 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
   dots(psi, 1, psi, drow + max_space + 1);
   launch_normalize(psi, drow + max_space + 1, n, V, stream);
   stats.launches++;
-  op(V, S);
+  opp(V, S);
   dots(V, 1, S, drow);
   CK(cudaMemcpyAsync(hd.data(), drow, (max_space + 2) * sizeof(double), cudaMemcpyDeviceToHost, stream));
   sync();
@@ -1348,7 +1360,7 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     dots(t, 1, t, drow + max_space + 1);
     launch_normalize(t, drow + max_space + 1, n, V + (size_t)k * n, stream);
     stats.launches++;
-    op(V + (size_t)k * n, S + (size_t)k * n);
+    opp(V + (size_t)k * n, S + (size_t)k * n);
     dots(V, k + 1, S + (size_t)k * n, drow);
     CK(cudaMemcpyAsync(hd.data(), drow, (max_space + 2) * sizeof(double), cudaMemcpyDeviceToHost, stream));
     int hbad = 0;
@@ -1381,6 +1393,7 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     dfree(p);
   if (dsums) dfree(dsums);
   if (cg) dfree(cg);
+  if (dpen) dfree(dpen);
   return theta;
 }
 
@@ -1661,6 +1674,12 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
   double tdg = now_ms();
   double* diag = dalloc<double>(psi_size);
   compute_diag(sg.lenl, sg.renl, diag);
+  if (!defl.empty()) {
+    // deflated states: their projections, and the diagonal of the penalty
+    defl_phi = dalloc<double>((size_t)defl.size() * psi_size);
+    deflation_vectors(k, defl_phi);
+    launch_add_sq(diag, defl_phi, (int)defl.size(), psi_size, defl_w, stream);
+  }
   stats.diag_ms += now_ms() - tdg;
   double td = now_ms();
   double theta = 0;
@@ -1668,6 +1687,10 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
   theta = solve_tiers(sg, diag, tol, sched.precision, sched.refine, planned);
   stats.davidson_ms += now_ms() - td;
   dfree(diag);
+  if (defl_phi) {
+    dfree(defl_phi);
+    defl_phi = nullptr;
+  }
   free_sigma(sg, planned);
   double tt = now_ms();
   truncate(k, dir, M, tau, kept);
@@ -1677,9 +1700,11 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
     Space el2 = EL;
     env_update_left(sg.lenl, el2, sites[k], bonds[k + 1], Lenv[k + 1]);
     Renv[k + 1].valid = false;
+    for (int j = 0; j < (int)defl.size(); ++j) ov_update_left(j, k);
   } else {
     env_update_right(sg.renl, ER, sites[k + 1], bonds[k + 1], Renv[k + 1]);
     Lenv[k + 1].valid = false;
+    for (int j = 0; j < (int)defl.size(); ++j) ov_update_right(j, k + 1);
   }
   free_enl(sg.lenl);
   free_enl(sg.renl);
@@ -1829,6 +1854,7 @@ void Engine::prepare(int n_, int n_elec, int two_sz, int n_chol, const double* h
     }
   }
   build_mpo(n, h.data(), eri.data(), n / 2, mpo);
+  clear_states();   // deflated states belong to the previous problem
   stats = Stats();
   sweep_E.clear();
   prepared = false;

@@ -153,6 +153,16 @@ class Engine {
   double sweep(int s);     // returns the Ritz value of the last step
   double final_energy();
   void rdms(double* rdm1, double* rdm2);
+  // excited states by penalty deflation: the converged lower states stay
+  // resident (both site layouts) and enter every two-site step through
+  // overlap environments; sigma gains w sum_j phi_j (phi_j . x) and the
+  // diagonal w sum_j phi_j^2, phi_j = the stored state j projected onto the
+  // current two-site basis
+  void store_state();        // keep the current MPS as a deflated state
+  void clear_states();
+  void ov_init();            // after init_state: overlap environments of every stored state
+  double defl_w = 0.0;       // penalty weight w (Ha)
+  int n_stored() const { return (int)defl.size(); }
   // debug / test hooks
   void set_mps(const int* nsec, const int* sectors, const double* data, int center);
   int64_t two_site_size(int k);
@@ -211,6 +221,26 @@ class Engine {
   std::vector<Bond> bonds;
   std::vector<Site> sites;
   std::vector<Env> Lenv, Renv;
+
+  // ---- deflated states and their overlap environments
+  struct Ov {                       // <current basis | stored basis> on one bond, per current sector
+    std::vector<int64_t> off;       // -1: the stored state has no such sector
+    std::vector<int> rows, cols;
+    double* d = nullptr;
+    int64_t size = 0;
+  };
+  struct Stored {
+    std::vector<Bond> bonds;
+    std::vector<Site> fl, fr;       // every site fused-left and fused-right
+  };
+  std::vector<Stored> defl;
+  std::vector<std::vector<Ov>> OLv, ORv;   // [state][bond]
+  double* defl_phi = nullptr;       // n_stored x psi_size at the current step
+  void free_ov(Ov& o);
+  void ov_make(int j, int bond, Ov& o);
+  void ov_update_left(int j, int k);    // OLv[j][k+1] from OLv[j][k] and sites[k] (fused-left)
+  void ov_update_right(int j, int b);   // ORv[j][b] from ORv[j][b+1] and sites[b] (fused-right)
+  void deflation_vectors(int k, double* phi);
 
   // ---- current two-site step state
   int cur_k = -1;

@@ -157,6 +157,8 @@ void launch_projected_precond(const double* v, const double* x, const double* di
                               int64_t n, double* out, double* partial, int nblk, double* sums_dev, cudaStream_t s);
 // y = a x + b y
 void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t s);
+// d[i] += w sum_j phi[j * n + i]^2 (j < k)
+void launch_add_sq(double* d, const double* phi, int k, int64_t n, double w, cudaStream_t s);
 int reduction_blocks(int64_t n);
 
 }  // namespace gbd

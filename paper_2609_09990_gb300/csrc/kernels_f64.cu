@@ -246,6 +246,14 @@ __global__ void axpby_kernel(double* y, double a, const double* __restrict__ x, 
     y[i] = fma(a, x[i], b * y[i]);
 }
 
+__global__ void add_sq_kernel(double* d, const double* __restrict__ phi, int k, int64_t n, double w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s = fma(phi[(int64_t)j * n + i], phi[(int64_t)j * n + i], s);
+    d[i] = fma(w, s, d[i]);
+  }
+}
+
 __global__ void scale_kernel(double* x, double a, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] *= a;
@@ -315,6 +323,10 @@ void launch_projected_precond(const double* v, const double* x, const double* di
 
 void launch_axpby(double* y, double a, const double* x, double b, int64_t n, cudaStream_t s) {
   axpby_kernel<<<grid_for(n, 256), 256, 0, s>>>(y, a, x, b, n);
+}
+
+void launch_add_sq(double* d, const double* phi, int k, int64_t n, double w, cudaStream_t s) {
+  if (k > 0) add_sq_kernel<<<grid_for(n, 256), 256, 0, s>>>(d, phi, k, n, w);
 }
 
 void launch_scale(double* x, double a, int64_t n, cudaStream_t s) {

@@ -87,6 +87,8 @@ def lib():
         "gbd_last_error": (C.c_char_p, [vp]),
         "gbd_solve": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), C.POINTER(gbd_result)]),
         "gbd_setup": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule)]),
+        "gbd_solve_states": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), C.c_int32, C.c_double,
+                                        C.c_double, C.c_int32, C.POINTER(gbd_result), _dp, _ip]),
         "gbd_solve_batched": (C.c_int, [vp, C.c_int32, C.POINTER(gbd_problem), C.POINTER(gbd_schedule),
                                         C.POINTER(gbd_result)]),
         "gbd_set_batch_workers": (C.c_int, [vp, C.c_int32]),
@@ -241,6 +243,29 @@ class Context:
         res = [dict(energy=rs[i].energy, sweep_energies=outs[i][0], rdm1=outs[i][1], rdm2=outs[i][2],
                     max_discarded_weight=rs[i].max_discarded_weight, n_matvec=rs[i].n_matvec,
                     status=rs[i].status) for i in range(n)]
+        return rc, res
+
+    def solve_states(self, h, chol, n_elec, two_sz, bond_dims, tols, n_states, penalty=5.0, target_s2=0.0,
+                     max_extra=2, rdms=False, check=True, **kw):
+        """gbd_solve_states: (return code, list of result dicts with 's2', one per root found)."""
+        p, s = self._structs(h, chol, n_elec, two_sz, bond_dims, tols, **kw)
+        n = p.n_orb
+        rs = (gbd_result * n_states)()
+        outs = []
+        for i in range(n_states):
+            se = np.zeros(len(bond_dims))
+            r1 = np.zeros((n, n)) if rdms else None
+            r2 = np.zeros((n, n, n, n)) if rdms else None
+            outs.append((se, r1, r2))
+            rs[i] = gbd_result(0.0, _d(se), _d(r1), _d(r2), 0.0, 0, 0)
+        s2 = np.zeros(n_states)
+        nf = C.c_int32(0)
+        rc = self.L.gbd_solve_states(self.ptr, C.byref(p), C.byref(s), n_states, float(penalty), float(target_s2),
+                                     max_extra, rs, _d(s2), C.byref(nf))
+        if check:
+            self._check(rc, "gbd_solve_states")
+        res = [dict(energy=rs[i].energy, sweep_energies=outs[i][0], rdm1=outs[i][1], rdm2=outs[i][2],
+                    s2=float(s2[i]), n_matvec=rs[i].n_matvec) for i in range(nf.value)]
         return rc, res
 
     def setup(self, h, chol, n_elec, two_sz, bond_dims, tols, **kw):
