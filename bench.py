@@ -26,6 +26,7 @@ Multi-GPU: independent replicas (one problem per rank, seed 3 + rank), no
 collective on the data path; value sums the ranks' flops over the max time.
 Other modes: --workload batched64 (64 independent active spaces through
 gbd_solve_batched), --sigma-probe P (profiling driver, no bench line),
+--states K (excited states by penalty deflation, no bench line),
 --impl reference (the oracle, timed on the host cores).
 """
 import argparse
@@ -315,6 +316,30 @@ def sigma_probe(prec, orders=(0,)):
     ctx.close()
 
 
+def states_run(args):
+    """Excited states by penalty deflation on a workload (gbd_solve_states):
+    the lowest `--states` roots of any spin (no <S^2> guard), each from its
+    own seeded initial MPS, n_sweeps of the workload at --tol, mixed-precision
+    tiers; every root's <S^2> is reported.  One JSON line, no bench line."""
+    from paper_2609_09990_gb300 import gbdmrg as G
+    wl = WORKLOADS[args.workload]
+    n, ne, nq, M, seed, nsw = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"], wl["n_sweeps"]
+    h, chol = make_integrals(n, nq, seed)
+    ctx = G.Context(0)
+    t0 = time.perf_counter()
+    rc, res = ctx.solve_states(h, chol, ne, 0, [M] * nsw, [args.tol] * nsw, args.states, penalty=args.penalty,
+                               target_s2=-1.0, max_extra=0, seed=seed, precision=PREC[args.precision],
+                               fp64_refine=args.refine, check=False)
+    dt = time.perf_counter() - t0
+    st = ctx.stats()
+    ctx.close()
+    print(json.dumps({"states": args.states, "workload": args.workload, "rc": int(rc), "found": len(res),
+                      "seconds": dt, "penalty_Ha": args.penalty, "sigma_builds": int(st["n_sigma"]),
+                      "roots": [{"energy": r["energy"], "s2": r["s2"], "last_sweep_ritz": float(r["sweep_energies"][-1])}
+                                for r in res],
+                      "excitation_energies_Ha": [r["energy"] - res[0]["energy"] for r in res]}))
+
+
 def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -395,10 +420,16 @@ def main():
                     help="operands of the accurate Davidson tier")
     ap.add_argument("--sigma-probe", type=int, default=0, help="profiling driver: central sigma of cas16_m512 "
                     "with operand type 1 TF32, 2 BF16, 3 TF32x3 (no bench line)")
+    ap.add_argument("--states", type=int, default=0, help="excited-state driver: this many lowest roots of "
+                    "--workload by penalty deflation, with <S^2> (no bench line)")
+    ap.add_argument("--penalty", type=float, default=2.0, help="deflation penalty (Ha) of --states")
     ap.add_argument("--probe-orders", default="0", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2")
     args = ap.parse_args()
     if args.sigma_probe:
         sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")))
+        return
+    if args.states:
+        states_run(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

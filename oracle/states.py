@@ -38,12 +38,14 @@ def spin_square_from_rdm(g2: np.ndarray, n_elec: int) -> float:
     return float(-0.5 * s - n_elec * n_elec / 4.0 + n_elec)
 
 
-def sector_spectrum(h, eri, n_alpha, n_beta, nroots):
+def sector_spectrum(h, eri, n_alpha, n_beta, nroots, dense_limit=2000):
     """Lowest nroots eigenpairs of H in the (N_alpha, N_beta) sector (dense
-    FCI) with <S^2> of each.  Returns (energies, S^2 values, CI vectors)."""
+    FCI up to dense_limit determinants, block Davidson to |r| < 1e-10 above)
+    with <S^2> of each.  Returns (energies, S^2 values, CI vectors)."""
     F = fci.FCI(h, eri, n_alpha, n_beta)
-    w, v = np.linalg.eigh(F.dense_h())
-    w, v = w[:nroots], v[:, :nroots]
+    w, v = F.ground_state(tol=1e-10, nroots=nroots, max_iter=400, max_space=max(24, 4 * nroots),
+                          dense_limit=dense_limit)
+    w, v = np.asarray(w)[:nroots], np.asarray(v)[:, :nroots]
     s2 = np.array([spin_square_from_rdm(F.rdms(v[:, i])[1], n_alpha + n_beta) for i in range(v.shape[1])])
     return w, s2, v
 

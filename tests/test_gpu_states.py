@@ -71,3 +71,34 @@ def test_too_few_roots_of_the_target_spin(G, cas66):
     assert rc == G.GBD_ERR_NOCONV and len(res) < 3
     for r in res:
         assert abs(r["s2"]) < 1e-6
+
+
+def test_roots_with_the_tensor_core_tiers(G, cas66):
+    # BF16 -> TF32x3 Davidson tiers (forced on this small space): the same
+    # singlet roots to the tiers' accuracy
+    h, chol, w, s2 = cas66
+    sel = states.select_roots(w, s2, 0.0, 3)
+    pen = 2.0 * (w[sel[-1]] - w[0]) + 1.0
+    ctx = G.Context(0)
+    ctx.set_tc_min_two_site(0)
+    rc, res = ctx.solve_states(h, chol, 6, 0, [64] * 8, [1e-7] * 8, 3, penalty=pen, target_s2=0.0,
+                               max_extra=sel[-1] - 2 + 1, seed=5, precision=G.GBD_BF16, fp64_refine=0)
+    st = ctx.stats()
+    ctx.close()
+    assert st["n_sigma_tc"] > 0
+    assert np.allclose([r["energy"] for r in res], w[sel], rtol=0, atol=2e-6)
+    assert all(abs(r["s2"]) < 1e-4 for r in res)
+
+
+def test_truncated_bond_dimension_roots(G):
+    # CAS(8,8) at M = 48 (full: 256): each root within a few mHa above FCI
+    h, chol = make_integrals(8, 10, 6)
+    w, s2, _ = states.sector_spectrum(h, fock.eri_from_chol(chol), 4, 4, 6)
+    sel = states.select_roots(w, s2, 0.0, 2)
+    pen = 2.0 * (w[sel[-1]] - w[0]) + 1.0
+    ctx = G.Context(0)
+    rc, res = ctx.solve_states(h, chol, 8, 0, [48] * 8, [1e-8] * 8, 2, penalty=pen, target_s2=0.0,
+                               max_extra=sel[-1] - 1 + 2, seed=6)
+    ctx.close()
+    E = np.array([r["energy"] for r in res])
+    assert np.all(E > w[sel] - 1e-9) and np.all(E - w[sel] < 5e-3), E - w[sel]
