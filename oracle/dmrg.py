@@ -325,7 +325,7 @@ def heff_dense(L, W1, W2, R, keys, mpo, k, dims_k, dims_k2):
 
 
 # ---------------------------------------------------------------- truncation
-def select_states(weights, M, cutoff=1e-12, tie=1e-10):
+def select_states(weights, M, cutoff=1e-12, tie=1e-10, max_discarded=0.0, m_min=1):
     """Reading of the decimation rule (Fig. 2: keep chi_k states, discard
     tau = sum of the dropped sigma^2).  weights = [(lambda, sector, j)] with
     lambda = sigma^2 of a normalised two-site state.
@@ -335,9 +335,28 @@ def select_states(weights, M, cutoff=1e-12, tie=1e-10):
          <= tie, step back past the whole cluster (never split a
          near-degenerate multiplet at the cut; if every weight is in the
          cluster keep min(M, count)).
+    Per-bond adaptive bond dimension (Sec. "Cholesky decomposition for the
+    wavefunction", ingredient (ii): a dynamically adapted per-bond bond
+    dimension), when max_discarded > 0: before step 3, take the smallest m
+    whose discarded weight (everything not among the first m, the cut-off
+    weights included) is <= max_discarded; extend m past a cluster it
+    would split; raise it to m_min.  If that m is below min(M, count), keep
+    it; otherwise step 3 applies (M caps the bond).
     Returns the kept list and tau."""
     cand = [w for w in weights if w[0] > cutoff]
     cand.sort(key=lambda w: (-w[0], w[1], w[2]))
+    if max_discarded > 0.0:
+        total = sum(w[0] for w in weights)
+        m, kept_sum = 0, 0.0
+        while m < len(cand) and total - kept_sum > max_discarded:
+            kept_sum += cand[m][0]
+            m += 1
+        while 0 < m < len(cand) and cand[m - 1][0] - cand[m][0] <= tie:
+            m += 1
+        m = max(m, min(m_min, len(cand)))
+        if m < min(M, len(cand)):
+            kept = cand[:m]
+            return kept, total - sum(w[0] for w in kept)
     nk = min(M, len(cand))
     if len(cand) > nk:
         j = nk

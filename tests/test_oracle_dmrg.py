@@ -222,3 +222,38 @@ def test_move_center_keeps_state_and_gauge():
     x = dmrg.flatten(psi, keys, d.dims[k], d.dims[k + 2])
     s = dmrg.flatten(dmrg.apply_heff(*d.heff_parts(k), psi, d.mpo, k), keys, d.dims[k], d.dims[k + 2])
     assert abs(x @ s / (x @ x) - E) < 1e-11
+
+
+def test_select_states_adaptive_bond_dimension():
+    # the smallest m whose discarded weight is <= delta, clusters kept whole,
+    # m_min as a floor, M as a cap (brute force over m)
+    rng = np.random.default_rng(17)
+    for trial in range(200):
+        n = int(rng.integers(1, 30))
+        lam = np.sort(rng.exponential(1.0, n) ** 3)[::-1]
+        if trial % 5 == 0 and n > 3:
+            lam[2] = lam[1]                      # a degenerate pair
+        lam /= lam.sum()
+        w = [(float(v), (i % 3, 0), i) for i, v in enumerate(lam)]
+        delta = float(10 ** rng.uniform(-8, -1))
+        M = int(rng.integers(1, n + 3))
+        m_min = int(rng.integers(1, 4))
+        kept, tau = dmrg.select_states(w, M, tie=1e-12, max_discarded=delta, m_min=m_min)
+        order = sorted(w, key=lambda x: (-x[0], x[1], x[2]))
+        disc = lambda m: sum(x[0] for x in order[m:])
+        m_delta = next(m for m in range(n + 1) if disc(m) <= delta)
+        while 0 < m_delta < n and order[m_delta - 1][0] - order[m_delta][0] <= 1e-12:
+            m_delta += 1
+        m_delta = max(m_delta, min(m_min, n))
+        if m_delta < min(M, n):
+            assert kept == order[:m_delta]
+            assert tau <= delta + 1e-15   # extending m only lowers the discarded weight
+        else:
+            assert kept == dmrg.select_states(w, M, tie=1e-12)[0]
+        assert abs(tau - (sum(lam) - sum(x[0] for x in kept))) < 1e-12
+    # max_discarded = 0 is the fixed-M rule
+    w = [(0.5, (0, 0), 0), (0.3, (0, 1), 0), (0.2, (1, 0), 0)]
+    assert dmrg.select_states(w, 2) == dmrg.select_states(w, 2, max_discarded=0.0)
+    # a loose target keeps fewer states than M; a tight one is capped by M
+    assert len(dmrg.select_states(w, 3, max_discarded=0.25)[0]) == 2
+    assert len(dmrg.select_states(w, 2, max_discarded=1e-9)[0]) == 2
