@@ -67,6 +67,15 @@ int gbd_set_graphs(gbd_ctx *ctx, int32_t enable);
  * never changes the arithmetic (same products, same summation order). */
 int gbd_set_tc_tile(gbd_ctx *ctx, int32_t ncap);
 
+/* Per-bond adaptive bond dimension for the following solves on this
+ * context (the paper's dynamically adapted per-bond bond dimension): each
+ * decimation keeps the fewest states whose discarded weight is at most
+ * max_discarded.  It never splits a near-degenerate cluster, keeps at least
+ * m_min, and keeps at most the schedule's bond dimension of that sweep.
+ * max_discarded = 0 (the default) is the fixed bond dimension.  The choice
+ * is made on the host; the device path is that of any smaller bond. */
+int gbd_set_adaptive_bond_dim(gbd_ctx *ctx, double max_discarded, int32_t m_min);
+
 /* Order in which the persistent tensor-core CTAs take the stage-B tiles of
  * the sigma (output sector q, 128-row block m0 of E_R(q), split-K chunk,
  * N tile n0 of E_L(q)): 0 (default) by (q, m0, chunk, n0), 1 by
@@ -220,9 +229,13 @@ int gbd_host_initial_dims(int32_t n, int32_t n_alpha, int32_t n_beta, int32_t M,
                           int32_t *triples, int32_t cap);
 /* Decimation rule on `count` weights lam (= sigma^2) with sector keys
  * (64 N_alpha + N_beta) and in-sector ranks j: indices of the kept weights
- * in kept order, their number, and the total weight. */
+ * in kept order, their number, and the total weight.  max_discarded > 0
+ * turns on the per-bond adaptive bond dimension (see
+ * gbd_set_adaptive_bond_dim); 0 is the fixed-M rule.  GBD_ERR_ARG for
+ * max_discarded < 0 or m_min < 1. */
 int gbd_host_select(int32_t count, const double *lam, const int32_t *key, const int32_t *j, int32_t M,
-                    double cutoff, double tie, int32_t *kept_index, int32_t *nkept, double *total);
+                    double cutoff, double tie, double max_discarded, int32_t m_min, int32_t *kept_index,
+                    int32_t *nkept, double *total);
 /* MPO bond dimensions [n+1]; if dense != NULL (n <= 5) also the full
  * 4^n x 4^n matrix of the contracted MPO in the product basis
  * |s_0 ... s_{n-1}> (site 0 most significant). */

@@ -341,6 +341,17 @@ int gbd_set_tc_tile(gbd_ctx* ctx, int32_t ncap) {
   });
 }
 
+int gbd_set_adaptive_bond_dim(gbd_ctx* ctx, double max_discarded, int32_t m_min) {
+  return guarded(ctx, [&]() {
+    if (!(max_discarded >= 0) || !std::isfinite(max_discarded) || m_min < 1)
+      return fail(ctx, GBD_ERR_ARG, "max_discarded < 0 or m_min < 1");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->adapt_disc = max_discarded;
+    ctx->eng->adapt_mmin = m_min;
+    return GBD_OK;
+  });
+}
+
 int gbd_set_tc_order(gbd_ctx* ctx, int32_t order) {
   return guarded(ctx, [&]() {
     if (order < 0 || order > 2) return fail(ctx, GBD_ERR_ARG, "order not in {0,1,2}");
@@ -740,11 +751,13 @@ int gbd_host_initial_dims(int32_t n, int32_t n_alpha, int32_t n_beta, int32_t M,
 }
 
 int gbd_host_select(int32_t count, const double* lam, const int32_t* key, const int32_t* j, int32_t M,
-                    double cutoff, double tie, int32_t* kept_index, int32_t* nkept, double* total) {
+                    double cutoff, double tie, double max_discarded, int32_t m_min, int32_t* kept_index,
+                    int32_t* nkept, double* total) {
   if (count < 0 || (count > 0 && (!lam || !key || !j)) || M < 1 || !nkept) return GBD_ERR_ARG;
+  if (!(max_discarded >= 0) || !std::isfinite(max_discarded) || m_min < 1) return GBD_ERR_ARG;
   std::vector<gbd::Weight> w;
   for (int i = 0; i < count; ++i) w.push_back({lam[i], key[i], i, j[i]});
-  auto kw = gbd::select_states(w, M, cutoff, tie, total);
+  auto kw = gbd::select_states(w, M, cutoff, tie, total, max_discarded, m_min);
   *nkept = (int)kw.size();
   if (kept_index)
     for (size_t i = 0; i < kw.size(); ++i) kept_index[i] = kw[i].idx;

@@ -263,7 +263,13 @@ std::vector<Bond> initial_bond_dims(int n, int Na, int Nb, int M) {
 // min(M, count); if the last kept and the first dropped differ by <= tie,
 // step back so that a near-degenerate cluster is never split at the cut
 // (unless the cluster reaches the top, then keep min(M, count)).
-std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, double tie, double* total) {
+// Per-bond adaptive bond dimension (a dynamically adapted bond dimension per
+// bond, the paper's compression ingredient (ii)), when max_disc > 0: first
+// the smallest m whose discarded weight (all but the first m, cut-off
+// weights included) is <= max_disc, extended past a cluster it would split
+// and raised to m_min; kept if below min(M, count), else the rule above.
+std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, double tie, double* total,
+                                  double max_disc, int m_min) {
   double tot = 0;
   std::vector<Weight> cand;
   for (auto& x : w) {
@@ -276,6 +282,18 @@ std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, d
     if (a.key != b.key) return a.key < b.key;
     return a.j < b.j;
   });
+  const int cn = (int)cand.size();
+  if (max_disc > 0.0) {
+    int m = 0;
+    double kept = 0.0;
+    while (m < cn && tot - kept > max_disc) kept += cand[m++].lam;
+    while (m > 0 && m < cn && cand[m - 1].lam - cand[m].lam <= tie) ++m;
+    m = std::max(m, std::min(m_min, cn));
+    if (m < std::min(M, cn)) {
+      cand.resize(m);
+      return cand;
+    }
+  }
   int nk = std::min<int>(M, (int)cand.size());
   if ((int)cand.size() > nk) {
     int j = nk;
@@ -1472,7 +1490,7 @@ void Engine::truncate(int k, int dir, int M, double* tau_out, std::vector<double
     for (int j = 0; j < m; ++j) all.push_back({ew[q][m - 1 - j], qkey(EL.qa[q], EL.qb[q]), q, j});
   }
   double total = 0, kept_sum = 0;
-  std::vector<Weight> kw = select_states(all, M, sched.cutoff, sched.tie, &total);
+  std::vector<Weight> kw = select_states(all, M, sched.cutoff, sched.tie, &total, adapt_disc, adapt_mmin);
   std::vector<int> nkeep(nq, 0);
   for (auto& w : kw) {
     nkeep[w.idx]++;

@@ -69,7 +69,8 @@ struct Site {         // device tensor of one site; layout 0 = fused-left, 1 = f
 };
 
 struct Weight { double lam; int key, idx, j; };
-std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, double tie, double* total);
+std::vector<Weight> select_states(std::vector<Weight> w, int M, double cutoff, double tie, double* total,
+                                  double max_disc = 0.0, int m_min = 1);
 std::vector<Bond> initial_bond_dims(int n, int Na, int Nb, int M);
 
 struct Stats {
@@ -162,6 +163,10 @@ class Engine {
   void clear_states();
   void ov_init();            // after init_state: overlap environments of every stored state
   double defl_w = 0.0;       // penalty weight w (Ha)
+  // per-bond adaptive bond dimension: discarded-weight target per decimation
+  // (0: fixed M) and the smallest bond kept under it
+  double adapt_disc = 0.0;
+  int adapt_mmin = 1;
   int n_stored() const { return (int)defl.size(); }
   // debug / test hooks
   void set_mps(const int* nsec, const int* sectors, const double* data, int center);

@@ -137,8 +137,9 @@ def lib():
         "gbd_davidson_counts": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "gbd_host_sym_eig": (C.c_int, [C.c_int32, _dp, _dp, _dp]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
-        "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, _ip, _ip,
-                                      _dp]),
+        "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                      C.c_int32, _ip, _ip, _dp]),
+        "gbd_set_adaptive_bond_dim": (C.c_int, [vp, C.c_double, C.c_int32]),
         "gbd_host_mpo": (C.c_int, [C.c_int32, _dp, C.c_int32, _dp, C.c_int32, _ip, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -323,6 +324,11 @@ class Context:
     def set_tc_tile(self, ncap):
         self._check(self.L.gbd_set_tc_tile(self.ptr, ncap), "gbd_set_tc_tile")
 
+    def set_adaptive_bond_dim(self, max_discarded, m_min=1):
+        """Per-bond adaptive bond dimension (0 = fixed M) for the following solves."""
+        self._check(self.L.gbd_set_adaptive_bond_dim(self.ptr, float(max_discarded), int(m_min)),
+                    "gbd_set_adaptive_bond_dim")
+
     def set_tc_order(self, order):
         self._check(self.L.gbd_set_tc_order(self.ptr, order), "gbd_set_tc_order")
 
@@ -473,7 +479,7 @@ def host_initial_dims(n, n_alpha, n_beta, M):
     return out
 
 
-def host_select(lam, key, j, M, cutoff=1e-12, tie=1e-10):
+def host_select(lam, key, j, M, cutoff=1e-12, tie=1e-10, max_discarded=0.0, m_min=1):
     L = lib()
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     key = np.ascontiguousarray(key, dtype=np.int32)
@@ -481,7 +487,8 @@ def host_select(lam, key, j, M, cutoff=1e-12, tie=1e-10):
     idx = np.zeros(max(len(lam), 1), dtype=np.int32)
     nk = C.c_int32()
     tot = C.c_double()
-    rc = L.gbd_host_select(len(lam), _d(lam), _i(key), _i(j), M, cutoff, tie, _i(idx), C.byref(nk), C.byref(tot))
+    rc = L.gbd_host_select(len(lam), _d(lam), _i(key), _i(j), M, cutoff, tie, float(max_discarded), int(m_min),
+                           _i(idx), C.byref(nk), C.byref(tot))
     if rc != GBD_OK:
         raise GbdError(f"gbd_host_select: {ERRORS.get(rc, rc)}")
     return idx[:nk.value].copy(), tot.value

@@ -128,3 +128,29 @@ def test_host_eigensolver_against_lapack(G, n):
     assert np.abs(w - ref).max() <= 1e-13 * scale
     assert np.abs(A @ Z - Z * w).max() <= 1e-13 * scale
     assert np.abs(Z.T @ Z - np.eye(n)).max() <= 1e-12
+
+
+def test_adaptive_selection_matches_oracle_bit_exactly(G):
+    # per-bond adaptive bond dimension: the library's host rule against the
+    # oracle's on random spectra with degeneracies, targets from 1e-9 to 1e-1
+    rng = np.random.default_rng(23)
+    for trial in range(60):
+        nsec = int(rng.integers(1, 6))
+        w = []
+        for q in range(nsec):
+            m = int(rng.integers(1, 9))
+            vals = np.sort(rng.exponential(0.1, m) ** 2)[::-1]
+            if trial % 3 == 0 and m > 1:
+                vals[1] = vals[0]
+            for j, v in enumerate(vals):
+                w.append((float(v), (int(q), int(q % 2)), j))
+        M = int(rng.integers(1, len(w) + 2))
+        delta = float(10 ** rng.uniform(-9, -1))
+        m_min = int(rng.integers(1, 4))
+        kept, tau = dmrg.select_states(w, M, max_discarded=delta, m_min=m_min)
+        idx, tot = G.host_select([x[0] for x in w], [x[1][0] * 64 + x[1][1] for x in w], [x[2] for x in w], M,
+                                 max_discarded=delta, m_min=m_min)
+        assert [w[i] for i in idx] == kept
+        assert abs((tot - sum(w[i][0] for i in idx)) - tau) < 1e-14
+    with pytest.raises(G.GbdError):
+        G.host_select([0.5, 0.5], [0, 0], [0, 1], 2, max_discarded=-1.0)
