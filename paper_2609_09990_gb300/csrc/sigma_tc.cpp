@@ -46,7 +46,8 @@ struct TcPlan {
   int* d_err = nullptr;
   double flops_alg = 0, flops_exec = 0;
   // algorithmic HBM bytes of one sigma: the Renl and Lenl sub-blocks once,
-  // Y^T written once and read once, psi read and sigma written in FP64
+  // the Y^T sections that some Lenl sub-block reads written once and read
+  // once, psi read and sigma written in FP64
   double bytes_alg = 0;
   // the same split by stage (A, B), and the bytes the TMA boxes of each
   // stage request from L2, by operand (A box, B box): whole boxes of 128
@@ -178,7 +179,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   //      row is one row of Y^T, so a 128-row A box covers many channels b.
   //      The B operand (psi rows of qin) and the column sections depend on
   //      (qin, set of si) only, so members with different (qout, so) share
-  //      a group; the row map sends each stacked row to its own Y^T row.
+  //      a group; each member's run record sends its stacked rows, and each
+  //      column section of them, to their place in the K-blocked Y^T(Qout).
   struct AGroup {
     int qin, mask;
     std::vector<std::array<int, 4>> mem;   // per member: sub index for each si (-1: none)
@@ -261,7 +263,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   }
   P->rs_pitch = up64(rs_width);
   rs_rows = std::max<int64_t>(rs_rows, 128);
-  phase(0);   // host: layouts, groups, row map
+  phase(0);   // host: layouts, groups, run records
   // ---- allocate and zero the panels
   for (int h = 0; h < nh; ++h) {
     P->psi[h] = dalloc<uint8_t>((size_t)(psi_rows * P->psi_pitch * P->eb));

@@ -5,13 +5,16 @@
 // (a multiple of 64 elements) holding many sub-blocks, each sub-block's K
 // range starting at a column that is a multiple of 16 and zero-padded to a
 // multiple of the MMA K step.  One TMA tensor map per panel (and per B box
-// height) then serves every block product of a launch.
+// height) then serves every block product of a launch.  A K-blocked panel
+// has a pitch of one 128-byte box row: its K range is cut into blocks of W
+// columns stacked vertically, so a term walks down it (TcTerm::ays/bys)
+// and every box is dense.
 //
 // A work tile is 128 rows of A (M) by n_mma (<= 256, multiple of 16) rows
 // of B (N) starting at A row ay + m0 and B row by + n0 of each term, so that
 // all tiles of one output block share one term list; it accumulates
 // C += sign * A_t B_t^T over its terms t in TMEM
-// (FP32) and is written by one of two epilogues:
+// (FP32) and is written by one of four epilogues:
 //   kTcYT    : C^T into a panel (BF16, TF32, or TF32 hi/lo), row j of the
 //              output is panel row out + j, output column = the padded
 //              position of tile row m0 + i (rmap: 4 breaks + 4 pads),
