@@ -157,6 +157,21 @@ int gbd_solve_states(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedul
                      double penalty, double target_s2, int32_t max_extra, gbd_result *results, double *s2,
                      int32_t *n_found);
 
+/* Fiedler ordering of the orbitals (Sec. "Cholesky decomposition for the
+ * wavefunction", ingredient (ii): the lattice is ordered by mutual
+ * information).  W: [n*n] symmetric, non-negative couplings between
+ * orbitals (diagonal ignored), e.g. a mutual-information matrix, supplied
+ * by the caller; this library does not compute two-orbital density
+ * matrices.  order[k] = the original orbital to place at site k: the
+ * eigenvector f of the second-smallest eigenvalue of the Laplacian
+ * diag(W 1) - W, ascending (equal values by index), in the direction that
+ * starts at the smaller index.  Permute the integrals before a solve:
+ * h'[a][b] = h[order[a]][order[b]], likewise each Cholesky slice.  Host
+ * only.  GBD_ERR_ARG for an asymmetric, negative or non-finite W;
+ * GBD_ERR_NOCONV when that eigenvalue is degenerate or the graph is
+ * disconnected. */
+int gbd_host_fiedler_order(int32_t n, const double *W, int32_t *order);
+
 /* Many independent active spaces in one call (the paper solves one active
  * space per call; batching is this library's addition).  problems[i] is
  * solved with schedules[i] into results[i] (caller-owned, as for

@@ -842,3 +842,42 @@ int gbd_correction_selftest(int32_t device, int32_t kind, int64_t n, const doubl
   cudaFree(d);
   return rc;
 }
+
+// Fiedler ordering of the orbitals from symmetric non-negative couplings W
+// (n x n, diagonal ignored): the Laplacian D - W, the eigenvector f of its
+// second-smallest eigenvalue, the orbitals in ascending f (equal values by
+// index), the direction whose first orbital has the smaller index.
+int gbd_host_fiedler_order(int32_t n, const double* W, int32_t* order) {
+  if (n < 1 || !W || !order) return GBD_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double a = W[(size_t)i * n + j], b = W[(size_t)j * n + i];
+      if (!std::isfinite(a) || (i != j && a < 0) || std::fabs(a - b) > 1e-12 * (1.0 + std::fabs(a)))
+        return GBD_ERR_ARG;
+    }
+  for (int i = 0; i < n; ++i) order[i] = i;
+  if (n <= 2) return GBD_OK;
+  try {
+    std::vector<double> L((size_t)n * n, 0.0), w(n), Z((size_t)n * n);
+    for (int i = 0; i < n; ++i) {
+      double d = 0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) {
+          L[(size_t)i * n + j] = -W[(size_t)i * n + j];
+          d += W[(size_t)i * n + j];
+        }
+      L[(size_t)i * n + i] = d;
+    }
+    if (gbd::sym_eig(n, L.data(), w.data(), Z.data()) != 0) return GBD_ERR_NOCONV;
+    const double tol = 1e-10 * std::max(1.0, std::fabs(w[n - 1]));
+    if (w[1] - w[0] <= tol || w[2] - w[1] <= tol) return GBD_ERR_NOCONV;
+    std::vector<int32_t> o(n);
+    std::iota(o.begin(), o.end(), 0);
+    std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return Z[(size_t)a * n + 1] < Z[(size_t)b * n + 1]; });
+    if (o[0] > o[n - 1]) std::reverse(o.begin(), o.end());
+    std::copy(o.begin(), o.end(), order);
+    return GBD_OK;
+  } catch (...) {
+    return GBD_ERR_ARG;
+  }
+}

@@ -136,6 +136,7 @@ def lib():
         "gbd_mlp_precond": (C.c_int, [vp, _dp, _dp, C.c_double, C.c_double, C.c_int64, _dp]),
         "gbd_davidson_counts": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "gbd_host_sym_eig": (C.c_int, [C.c_int32, _dp, _dp, _dp]),
+        "gbd_host_fiedler_order": (C.c_int, [C.c_int32, _dp, _ip]),
         "gbd_host_initial_dims": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, _ip, _ip, C.c_int32]),
         "gbd_host_select": (C.c_int, [C.c_int32, _dp, _ip, _ip, C.c_int32, C.c_double, C.c_double, C.c_double,
                                       C.c_int32, _ip, _ip, _dp]),
@@ -459,6 +460,17 @@ def host_sym_eig(A):
     if rc != GBD_OK:
         raise GbdError(f"gbd_host_sym_eig: {ERRORS.get(rc, rc)}")
     return w, Z
+
+
+def fiedler_order(W):
+    """gbd_host_fiedler_order: orbital order (order[k] = orbital at site k) from couplings W."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    n = W.shape[0]
+    order = np.zeros(max(n, 1), dtype=np.int32)
+    rc = lib().gbd_host_fiedler_order(n, _d(W), _i(order))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_fiedler_order: {ERRORS.get(rc, rc)}")
+    return order[:n].copy()
 
 
 def host_initial_dims(n, n_alpha, n_beta, M):

@@ -154,3 +154,38 @@ def test_adaptive_selection_matches_oracle_bit_exactly(G):
         assert abs((tot - sum(w[i][0] for i in idx)) - tau) < 1e-14
     with pytest.raises(G.GbdError):
         G.host_select([0.5, 0.5], [0, 0], [0, 1], 2, max_discarded=-1.0)
+
+
+def test_fiedler_order_matches_oracle(G):
+    from oracle import ordering
+    rng = np.random.default_rng(31)
+    checked = 0
+    for trial in range(40):
+        n = int(rng.integers(3, 24))
+        W = rng.uniform(0.0, 1.0, (n, n)) ** 4
+        W = 0.5 * (W + W.T)
+        try:
+            want = ordering.fiedler_order(W)
+        except ValueError:
+            continue
+        # skip near-ties of the Fiedler components, where two eigensolvers may
+        # legitimately order differently
+        Lp = np.diag(W.sum(1) - np.diag(W)) - (W - np.diag(np.diag(W)))
+        f = np.linalg.eigh(Lp)[1][:, 1]
+        if np.min(np.diff(np.sort(f))) < 1e-9:
+            continue
+        assert list(G.fiedler_order(W)) == list(want)
+        checked += 1
+    assert checked >= 30
+    # a scrambled path comes back in order; errors as the oracle's
+    perm = np.array([4, 1, 6, 0, 3, 5, 2])
+    P = np.zeros((7, 7))
+    for i in range(6):
+        P[perm[i], perm[i + 1]] = P[perm[i + 1], perm[i]] = 1.0
+    assert list(G.fiedler_order(P)) == list(perm if perm[0] < perm[-1] else perm[::-1])
+    D = np.zeros((4, 4))
+    D[0, 1] = D[1, 0] = D[2, 3] = D[3, 2] = 1.0
+    with pytest.raises(G.GbdError):
+        G.fiedler_order(D)
+    with pytest.raises(G.GbdError):
+        G.fiedler_order(np.array([[0.0, 1.0, 0.0], [0.5, 0.0, 1.0], [0.0, 1.0, 0.0]]))
