@@ -59,8 +59,9 @@ extern "C" {
  *                       (preconditioner: the Olsen-projected den), stopping at
  *                       |residual| < 0.1 |r| or at a direction of non-positive
  *                       curvature; each step costs one extra sigma build.
- * The deflation-aware diagonal serves deflated excited-state targets, which
- * this library does not solve for. */
+ * The deflation-aware diagonal belongs to deflated excited-state solves: in
+ * gbd_solve_states every member above sees den + penalty * sum_j phi_j^2
+ * as its diagonal. */
 #define GBD_PRECOND_DIAG 0
 #define GBD_PRECOND_LEARNED 1
 #define GBD_PRECOND_OLSEN 2

@@ -32,8 +32,10 @@ r = H x - theta x, where d is the diagonal of H:
                        preconditioned residual, which is the Olsen
                        correction.
 
-The deflation-aware diagonal needs deflated (excited-state) targets, which
-this build does not solve for.
+The deflation-aware diagonal belongs to deflated excited-state solves: the
+diagonal of H_eff + w sum_j phi_j phi_j^T is d + w sum_j phi_j^2, and the
+members above take it as their d (oracle/states.py holds the excited-state
+reference).
 
 Pinned in tests/test_oracle_precond.py:
   * x . t = 0 for Olsen and for the inner-PCG result;
