@@ -340,6 +340,20 @@ def states_run(args):
                       "excitation_energies_Ha": [r["energy"] - res[0]["energy"] for r in res]}))
 
 
+def reduce_over_ranks(tmax, work, world, device="cuda"):
+    """Whole-job numbers of a replicas run: the slowest rank's time (MAX) and
+    the summed work (SUM) over the process group; unchanged for one rank."""
+    if world <= 1:
+        return tmax, work
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(tmax)], device=device, dtype=torch.float64)
+    f = torch.tensor([float(work)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 def dist_barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -445,14 +459,7 @@ def main():
             return
         res = run_batched(args, rank, world)
         tmax, flops = res["time"], res["flops"]
-        if world > 1:
-            import torch
-            import torch.distributed as dist
-            t = torch.tensor([tmax], device="cuda")
-            f = torch.tensor([flops], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(f, op=dist.ReduceOp.SUM)
-            tmax, flops = float(t.item()), float(f.item())
+        tmax, flops = reduce_over_ranks(tmax, flops, world)
         if rank == 0:
             print(json.dumps({
                 "metric": "batched active spaces: sigma-build TFLOP/s", "value": flops / tmax / 1e12,
@@ -495,14 +502,7 @@ def main():
         return
     res = run_ours(args, rank, world)
     tmax, flops = res["time"], res["flops"]
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([tmax], device="cuda")
-        f = torch.tensor([flops], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(f, op=dist.ReduceOp.SUM)
-        tmax, flops = float(t.item()), float(f.item())
+    tmax, flops = reduce_over_ranks(tmax, flops, world)
     if rank != 0:
         return
     pk, pk_kind = peaks()
