@@ -364,7 +364,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
           }
         }
         term_k.push_back(ER.sdim[g.qin][si]);
-        terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)psi_row[g.qin], w, 0, cpadR[g.qin][si]});
+        terms.push_back({g.col[si], (int32_t)g.row0, (int32_t)psi_row[g.qin], w, 0, cpadR[g.qin][si], 0, 0});
       }
     const int gt1 = (int)terms.size();
     for (int64_t m0 = 0; m0 < grows; m0 += 128)

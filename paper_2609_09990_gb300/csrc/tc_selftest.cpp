@@ -98,7 +98,7 @@ extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t 
         TcTile T{};
         T.t0 = (int)terms.size();
         int nv = std::min(256, N - n0);
-        for (int t = 0; t < nterms; ++t) terms.push_back({t * Kp, 0, t * N + n0, Kp, t % 3 == 2 ? 1 : 0, 0});
+        for (int t = 0; t < nterms; ++t) terms.push_back({t * Kp, 0, t * N + n0, Kp, t % 3 == 2 ? 1 : 0, 0, 0, 0});
         T.t1 = (int)terms.size();
         T.m0 = m0;
         T.m_valid = std::min(128, M - m0);
