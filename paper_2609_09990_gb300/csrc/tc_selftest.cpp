@@ -77,8 +77,8 @@ extern "C" int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t 
     // A panel: row i, term t at columns [t*Kp, t*Kp+Kp); B panel: rows t*N+j
     std::vector<TcConv> conv;
     for (int t = 0; t < nterms; ++t) {
-      conv.push_back({dA + (size_t)t * Kp, 1.0, M, Kp, Kp * nterms, 0, t * Kp});
-      conv.push_back({dB + (size_t)t * N * Kp, 1.0, N, Kp, Kp, 0, 0});
+      conv.push_back({dA + (size_t)t * Kp, 1.0, M, Kp, Kp * nterms, 0, t * Kp, 0});
+      conv.push_back({dB + (size_t)t * N * Kp, 1.0, N, Kp, Kp, 0, 0, 0});
     }
     std::vector<TcConv> ca, cb;
     for (size_t i = 0; i < conv.size(); ++i) (i % 2 ? cb : ca).push_back(conv[i]);
