@@ -17,6 +17,9 @@ Modules
   states -- excited states of the sector: the eigenpairs that deflated
            sweeps converge to, with <S^2> from the 2-RDM (Sec. "Excited
            states: dual-penalty deflation and NACMEs").
+  entropy -- one- and two-orbital reduced density matrices (fermionic
+           partial traces), entropies and the mutual information.
+  ordering -- Fiedler ordering of orbitals from a coupling matrix.
   precond -- Davidson correction vectors: Jacobi, Olsen, shift-and-invert
            inner PCG (Sec. "Computational details", preconditioner family).
 

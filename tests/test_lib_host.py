@@ -189,3 +189,15 @@ def test_fiedler_order_matches_oracle(G):
         G.fiedler_order(D)
     with pytest.raises(G.GbdError):
         G.fiedler_order(np.array([[0.0, 1.0, 0.0], [0.5, 0.0, 1.0], [0.0, 1.0, 0.0]]))
+
+
+def test_fiedler_order_of_a_ground_state_mutual_information(G):
+    # the ordering input the paper uses: mutual information of a correlated
+    # ground state (oracle, CAS(6,6) FCI in the Fock space)
+    from oracle import entropy, fock, ordering
+    h, chol = make_integrals(6, 8, 5)
+    _, v, st = fock.ground_state(h, fock.eri_from_chol(chol), 3, 3)
+    full = np.zeros(1 << 12)
+    full[st] = v[:, 0]
+    I = entropy.mutual_information(full, 6)
+    assert list(G.fiedler_order(I)) == list(ordering.fiedler_order(I))
