@@ -1,11 +1,11 @@
 /* gbdmrg -- two-site DMRG sweep engine for GB300 (sm_103a), C ABI.
  *
- * The library maps active-space integrals to a converged matrix-product
- * state and returns its energy and one-/two-particle reduced density
- * matrices: the DMRG node of the paper's pipeline, which "maps active-space
- * integrals (h_act, B^Q_act) to the converged MPS and its RDMs" (Sec.
- * "Contraction-DAG transpose", the paragraph introducing the DMRG node, and
- * Sec. "The DMRG-QD-NEVPT2 energy").  Inside, every two-site step solves the
+ * The library takes active-space integrals (the one-electron matrix and the
+ * Cholesky factors of the two-electron integrals) to a converged
+ * matrix-product state and returns its energy and one-/two-particle reduced
+ * density matrices.  That is the role of the DMRG node in the paper's
+ * pipeline (Sec. "Contraction-DAG transpose", the paragraph introducing the
+ * DMRG node, and Sec. "The DMRG-QD-NEVPT2 energy").  Inside, every two-site step solves the
  * effective Hamiltonian matrix-free against the MPO with Davidson and
  * decimates the enlarged bond by SVD (Fig. 2, Sec. "Cholesky decomposition
  * for the wavefunction"); all contractions run in this library's CUDA
@@ -33,7 +33,8 @@ extern "C" {
 #define GBD_ERR_ARG (-1)      /* invalid argument (sizes, symmetry, NaN) */
 #define GBD_ERR_OOM (-2)      /* device allocation failed */
 #define GBD_ERR_CUDA (-3)     /* a CUDA call failed */
-#define GBD_ERR_NOCONV (-4)   /* Davidson or eigensolver did not converge */
+#define GBD_ERR_NOCONV (-4)   /* no converged or well-defined result (Davidson, eigensolver,
+                                 too few roots of the target spin, degenerate ordering) */
 #define GBD_ERR_TIMEOUT (-5)  /* a bounded device wait ran out */
 #define GBD_ERR_STATE (-6)    /* call order violated (e.g. sweep before prepare) */
 
