@@ -158,6 +158,30 @@ class FCI:
         return g1, g2
 
 
+def rdm3(F, C):
+    """Spin-summed 3-RDM Gamma3_pqrstu = sum_{s,t,v} <a+_ps a+_rt a+_tv a_uv a_st a_qs>,
+    one of the densities the paper forms on the device for its SC-NEVPT2 step
+    (Sec. "Computational details", the paragraph on the device-native
+    perturbative correction), from products of excitation operators:
+      E_pq E_rs E_tu = e_pqrstu + d_qt e_purs + d_st e_pqru + d_qr e_pstu
+                       + d_qr d_st E_pu,
+    with e_pqrs the 2-RDM operator (Gamma_pqrs = <e_pqrs>).  Small spaces
+    only (n^4 vectors of the CI length)."""
+    n = F.n
+    C = C.reshape(F.Na, F.Nb)
+    g1, g2 = F.rdms(C)
+    D = F.apply_E_all(C)                                   # D[t n + u] = E_tu C
+    T = np.stack([F.apply_E_all(D[tu]) for tu in range(n * n)], axis=1)   # [rs, tu] = E_rs E_tu C
+    M = D.reshape(n * n, -1) @ T.reshape(n ** 4, -1).T     # row (q, p): <E_pq E_rs E_tu>
+    G = M.reshape(n, n, n, n, n, n).transpose(1, 0, 2, 3, 4, 5).copy()
+    d = np.eye(n)
+    G -= np.einsum("qt,purs->pqrstu", d, g2)
+    G -= np.einsum("st,pqru->pqrstu", d, g2)
+    G -= np.einsum("qr,pstu->pqrstu", d, g2)
+    G -= np.einsum("qr,st,pu->pqrstu", d, d, g1)
+    return G
+
+
 def davidson(matvec, diag, tol=1e-10, max_iter=200, max_space=24, nroots=1, guess=None, correction=None):
     """Plain Davidson (Davidson 1975) with the diagonal preconditioner
     t = -r / (diag - theta), two Gram-Schmidt passes and restart from the

@@ -130,6 +130,37 @@ def rdms(vec: np.ndarray, states: np.ndarray, n_orb: int):
     return g1, g2
 
 
+def rdm3(vec: np.ndarray, states: np.ndarray, n_orb: int) -> np.ndarray:
+    """Spin-summed 3-RDM Gamma3_pqrstu = sum_{s,t,v} <a+_ps a+_rt a+_tv a_uv a_st a_qs>
+    by applying the operator strings of the definition (n_orb <= 4)."""
+    dim = 1 << (2 * n_orb)
+    full = np.zeros(dim)
+    full[states] = vec
+    n = n_orb
+    G = np.zeros((n,) * 6)
+    idx = range(n)
+    for p in idx:
+        for q in idx:
+            for r in idx:
+                for s_ in idx:
+                    for t in idx:
+                        for u in idx:
+                            acc = 0.0
+                            for a in range(2):
+                                for b in range(2):
+                                    for c in range(2):
+                                        P, Q = 2 * p + a, 2 * q + a
+                                        R, S = 2 * r + b, 2 * s_ + b
+                                        T, U = 2 * t + c, 2 * u + c
+                                        if len({P, R, T}) < 3 or len({Q, S, U}) < 3:
+                                            continue
+                                        op = apply_string([(P, True), (R, True), (T, True), (U, False), (S, False),
+                                                           (Q, False)], dim)
+                                        acc += full @ (op @ full)
+                            G[p, q, r, s_, t, u] = acc
+    return G
+
+
 def spin_square(n_orb: int) -> sp.csr_matrix:
     """S^2 = S_z^2 + (S_+ S_- + S_- S_+)/2 with S_+ = sum_p a+_pa a_pb,
     S_- = sum_p a+_pb a_pa, S_z = 1/2 sum_p (n_pa - n_pb), from the operator
