@@ -194,6 +194,22 @@ int gbd_solve_batched(gbd_ctx *ctx, int32_t n, const gbd_problem *problems, cons
  * hardware threads); otherwise at most `workers`. */
 int gbd_set_batch_workers(gbd_ctx *ctx, int32_t workers);
 
+/* Splitting a set of independent active spaces over several GPUs (one
+ * process per GPU; the paper runs on one device, so this is the library's
+ * own addition).  gbd_host_batch_costs writes the estimated cost of each
+ * problem, n_orb x M_max^3 x n_sweeps (the order gbd_solve_batched hands
+ * problems out in).  gbd_host_partition assigns n problems with costs
+ * cost[i] >= 0 to `ranks` ranks by longest-processing-time-first greedy:
+ * problems in descending cost (equal costs by index), each to the rank with
+ * the smallest load so far (equal loads: the lowest rank).  owner[i] = the
+ * rank of problem i; load[r] (may be NULL) = the summed cost of rank r.  The
+ * result is a deterministic function of the costs, so every rank computes
+ * the same partition without communication.  Host only, no GPU needed.
+ * GBD_ERR_ARG for n < 0, ranks < 1, NULL arrays with n > 0, or a negative
+ * or non-finite cost. */
+int gbd_host_batch_costs(int32_t n, const gbd_problem *problems, const gbd_schedule *schedules, double *cost);
+int gbd_host_partition(int32_t n, const double *cost, int32_t ranks, int32_t *owner, double *load);
+
 /* Learned Davidson preconditioner (not in the paper, which names Jacobi,
  * deflation-aware diagonal, Olsen and shift-and-invert members of a
  * run-time-selectable family, Sec. "Computational details"; the reading used

@@ -56,6 +56,9 @@ typedef struct {
   double tc_gemm_ms_by_stage[2];  /* tc_gemm_ms split into stage A and stage B */
   int64_t davidson_iterations;    /* outer Davidson iterations (all tiers) */
   int64_t inner_matvecs;          /* sigma builds inside inner-PCG corrections (in n_sigma too) */
+  int64_t n_solves;               /* Davidson solves (one per two-site step) */
+  int64_t n_solves_above_tol;     /* of which ended with ||r|| >= the step's tolerance */
+  double sweep_max_residual;      /* largest final ||r|| of the current or last sweep */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or
@@ -108,6 +111,17 @@ int gbd_set_tc_min_two_site(gbd_ctx *ctx, int64_t n);
  * precision on one step. */
 int gbd_probe_step(gbd_ctx *ctx, int32_t k, int32_t precision, int32_t fp64_refine, double tol, double *theta,
                    double *e64, double *r64);
+
+/* Keep a device copy of the current MPS, whose centre must be at bond
+ * (0,1) (after gbd_init_state, gbd_set_mps with center 0 or a full sweep);
+ * a later save replaces it.  gbd_restore_state puts the copy back (the copy
+ * stays) and rebuilds the environments, so that several sweeps can start
+ * from the same state.  GBD_ERR_STATE without an MPS / without a copy. */
+int gbd_save_state(gbd_ctx *ctx);
+int gbd_restore_state(gbd_ctx *ctx);
+/* Bond dimension M (>= 1) and Davidson tolerance tol (> 0) of schedule
+ * entry `sweep` for the following gbd_run_sweep calls. */
+int gbd_set_sweep_schedule(gbd_ctx *ctx, int32_t sweep, int32_t M, double tol);
 
 /* Validate the problem and schedule, build the MPO; no MPS yet. */
 int gbd_setup(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule);
@@ -177,7 +191,9 @@ int gbd_multi_dot(gbd_ctx *ctx, const double *V, int64_t stride, int32_t k, cons
  * that device's copy of the array (cudaGetSymbolAddress with the device
  * current); make that first call before any stream capture.
  * Returns GBD_ERR_ARG for NULL pointers, k < 1, k > 32 (the array's limit),
- * n < 0 or stride < n; GBD_ERR_CUDA if a CUDA call fails.  No cudaMalloc,
+ * n < 0 or stride < n; GBD_ERR_CUDA if a CUDA call fails, or without
+ * launching anything if a CUDA error from earlier work is already pending on
+ * the calling thread (that error is left in place).  n = 0 gives zeros.  No cudaMalloc,
  * cudaFree or allocating library routine is called. */
 int gbd_multi_dot_noalloc(int32_t device, const double *V, int64_t stride, int32_t k, const double *x, int64_t n,
                           double *out, void *stream);
@@ -195,6 +211,15 @@ int gbd_tc_selftest(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t 
  * GBD_ERR_ARG for NULL pointers, n < 1 or another kind. */
 int gbd_correction_selftest(int32_t device, int32_t kind, int64_t n, const double *x, const double *sx,
                             const double *diag, double theta, double *r_out, double *t_out, double *rr);
+/* The inner-PCG Davidson correction (GBD_PRECOND_PCG) as the solver computes
+ * it, at the current centre k (environments k and k+2 valid): the FP64 sigma
+ * of that step, its own H_eff diagonal, at most 4 PCG steps with relative
+ * tolerance 0.1, stopped by the first direction of non-positive curvature.
+ * x (unit norm), r and the output t are host arrays in the two-site vector
+ * format (length from gbd_two_site_size); matvecs = sigma builds it made.
+ * GBD_ERR_ARG for NULL pointers; GBD_ERR_STATE without valid environments. */
+int gbd_pcg_selftest(gbd_ctx *ctx, int32_t k, const double *x, const double *r, double theta, double *t,
+                     int64_t *matvecs);
 /* Failure detection without a fault: one bounded mbarrier wait (the helper
  * every role of the tensor-core kernel uses).  arrive = 0: nothing completes
  * the barrier, the wait runs out after its poll limit (2^22 polls, a few
@@ -215,10 +240,6 @@ int gbd_mlp_loss_grad(gbd_ctx *ctx, const float *X, const float *y, const float 
 int gbd_mlp_precond(gbd_ctx *ctx, const double *r, const double *d, double theta, double iter, int64_t n, double *t);
 /* Davidson iteration count and learned-preconditioner fallbacks so far. */
 int gbd_davidson_counts(gbd_ctx *ctx, int64_t *iterations, int64_t *fallbacks, int64_t *samples);
-/* FP64 and FP32 CUDA-core FMA throughput of `device` (TFLOP/s), measured
- * with independent FMA chains on every SM; the peak of the FP64 path. */
-int gbd_probe_peaks(int32_t device, double *fp64_tflops, double *fp32_tflops);
-
 /* ---- host-only pieces of the planner (no GPU needed) ---- */
 /* The decimation's host eigensolver (Householder + implicit QL): A [n*n]
  * symmetric row-major; w [n] ascending; Z [n*n] with column j = eigenvector j. */

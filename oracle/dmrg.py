@@ -391,7 +391,7 @@ def middle_blocks(psi, dims_k, dims_k2):
     return out
 
 
-def truncate(psi, dims_k, dims_k2, M, direction, cutoff=1e-12, tie=1e-10):
+def truncate(psi, dims_k, dims_k2, M, direction, cutoff=1e-12, tie=1e-10, max_discarded=0.0, m_min=1):
     """SVD decimation of the two-site state.  direction 'L': left tensor is
     U (left-orthonormal) and S V^T moves right; 'R': right tensor is V^T and
     U S moves left.  Returns (left_site, right_site, new bond dims, tau,
@@ -403,7 +403,7 @@ def truncate(psi, dims_k, dims_k2, M, direction, cutoff=1e-12, tie=1e-10):
         U, S, Vt = np.linalg.svd(mat, full_matrices=False)
         svds[Q] = (U, S, Vt)
         weights += [(S[j] ** 2, Q, j) for j in range(len(S))]
-    kept, tau = select_states(weights, M, cutoff, tie)
+    kept, tau = select_states(weights, M, cutoff, tie, max_discarded, m_min)
     keep_idx = {}
     for lam, Q, j in kept:
         keep_idx.setdefault(Q, []).append(j)
@@ -462,7 +462,8 @@ class DMRG:
     def heff_parts(self, k):
         return self.Lenv[k], self.mpo.W[k], self.mpo.W[k + 1], self.Renv[k + 2]
 
-    def step(self, k, M, tol, direction, max_iter=100, max_space=24, cutoff=1e-12, tie=1e-10):
+    def step(self, k, M, tol, direction, max_iter=100, max_space=24, cutoff=1e-12, tie=1e-10, max_discarded=0.0,
+             m_min=1):
         """One two-site step at (k, k+1): Davidson on H_eff, decimation,
         environment update in the sweep direction."""
         n = self.n
@@ -482,7 +483,7 @@ class DMRG:
                                     max_space=max_space, guess=x0)
         x = X[:, 0] / np.linalg.norm(X[:, 0])
         psi = unflatten(x, keys, dk, dk2)
-        left, right, nd, tau, kept = truncate(psi, dk, dk2, M, direction, cutoff, tie)
+        left, right, nd, tau, kept = truncate(psi, dk, dk2, M, direction, cutoff, tie, max_discarded, m_min)
         self.sites[k], self.sites[k + 1] = left, right
         self.dims[k + 1] = nd
         if direction == "L":
@@ -574,12 +575,15 @@ def mps_to_ci(dims, sites, n, Na, Nb):
 
 
 def run(h, chol, n_elec, two_sz, M_schedule, tol_schedule, seed, k_switch=None,
-        max_iter=100, max_space=24, cutoff=1e-12, tie=1e-10):
-    """Full solve: initial MPS, sweeps per the schedule, final energy."""
+        max_iter=100, max_space=24, cutoff=1e-12, tie=1e-10, max_discarded=0.0, m_min=1):
+    """Full solve: initial MPS, sweeps per the schedule, final energy.
+    max_discarded > 0 turns on the per-bond adaptive bond dimension of
+    select_states in every decimation (M of each sweep is the cap)."""
     d = DMRG(h, chol, n_elec, two_sz, M_schedule[0], seed, k_switch=k_switch)
     sweep_E = []
     for M, tol in zip(M_schedule, tol_schedule):
-        log = d.sweep(M, tol, max_iter=max_iter, max_space=max_space, cutoff=cutoff, tie=tie)
+        log = d.sweep(M, tol, max_iter=max_iter, max_space=max_space, cutoff=cutoff, tie=tie,
+                      max_discarded=max_discarded, m_min=m_min)
         sweep_E.append(log[-1][2])
     return d, sweep_E
 

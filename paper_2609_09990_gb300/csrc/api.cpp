@@ -110,6 +110,13 @@ gbd::Schedule to_schedule(const gbd_schedule* s) {
   return out;
 }
 
+// estimated cost of one active space: n_orb x M_max^3 x sweeps
+double problem_cost(const gbd_problem& p, const gbd_schedule& s) {
+  int mmax = 1;
+  for (int k = 0; k < s.n_sweeps; ++k) mmax = std::max(mmax, s.bond_dim[k]);
+  return (double)p.n_orb * mmax * (double)mmax * mmax * s.n_sweeps;
+}
+
 int setup(gbd_ctx* c, const gbd_problem* p, const gbd_schedule* s) {
   int rc = validate(c, p, s);
   if (rc != GBD_OK) return rc;
@@ -256,11 +263,7 @@ int gbd_solve_batched(gbd_ctx* ctx, int32_t n, const gbd_problem* problems, cons
     // most expensive first (longest-processing-time order)
     std::vector<int> order(n);
     std::vector<double> cost(n);
-    for (int i = 0; i < n; ++i) {
-      int mmax = 1;
-      for (int k = 0; k < schedules[i].n_sweeps; ++k) mmax = std::max(mmax, schedules[i].bond_dim[k]);
-      cost[i] = (double)problems[i].n_orb * mmax * (double)mmax * mmax * schedules[i].n_sweeps;
-    }
+    for (int i = 0; i < n; ++i) cost[i] = problem_cost(problems[i], schedules[i]);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
     int hw = (int)std::max(1u, std::thread::hardware_concurrency());
@@ -321,6 +324,33 @@ int gbd_solve_batched(gbd_ctx* ctx, int32_t n, const gbd_problem* problems, cons
     if (first_bad < n) return fail(ctx, results[first_bad].status, first_msg);
     return GBD_OK;
   });
+}
+
+int gbd_host_batch_costs(int32_t n, const gbd_problem* problems, const gbd_schedule* schedules, double* cost) {
+  if (n < 0 || (n > 0 && (!problems || !schedules || !cost))) return GBD_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (schedules[i].n_sweeps < 1 || !schedules[i].bond_dim) return GBD_ERR_ARG;
+    cost[i] = problem_cost(problems[i], schedules[i]);
+  }
+  return GBD_OK;
+}
+
+int gbd_host_partition(int32_t n, const double* cost, int32_t ranks, int32_t* owner, double* load) {
+  if (n < 0 || ranks < 1 || (n > 0 && (!cost || !owner))) return GBD_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!(cost[i] >= 0) || !std::isfinite(cost[i])) return GBD_ERR_ARG;
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> l(ranks, 0.0);
+  for (int i : order) {
+    int r = (int)(std::min_element(l.begin(), l.end()) - l.begin());   // first minimum: the lowest rank
+    owner[i] = r;
+    l[r] += cost[i];
+  }
+  if (load)
+    for (int r = 0; r < ranks; ++r) load[r] = l[r];
+  return GBD_OK;
 }
 
 int gbd_set_graphs(gbd_ctx* ctx, int32_t enable) {
@@ -412,6 +442,45 @@ int gbd_set_precision(gbd_ctx* ctx, int32_t precision, int32_t fp64_refine) {
     if (precision < 0 || precision > 2 || fp64_refine < 0) return fail(ctx, GBD_ERR_ARG, "bad precision");
     ctx->eng->sched.precision = precision;
     ctx->eng->sched.refine = fp64_refine;
+    return GBD_OK;
+  });
+}
+
+int gbd_pcg_selftest(gbd_ctx* ctx, int32_t k, const double* x, const double* r, double theta, double* t,
+                     int64_t* matvecs) {
+  return guarded(ctx, [&]() {
+    if (!x || !r || !t || !matvecs) return fail(ctx, GBD_ERR_ARG, "NULL argument");
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no MPS installed");
+    if (k < 0 || k + 1 >= ctx->eng->n) return fail(ctx, GBD_ERR_ARG, "centre outside the chain");
+    ctx->eng->pcg_selftest(k, x, r, theta, t, matvecs);
+    return GBD_OK;
+  });
+}
+
+int gbd_save_state(gbd_ctx* ctx) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no MPS to save");
+    ctx->eng->save_state();
+    return GBD_OK;
+  });
+}
+
+int gbd_restore_state(gbd_ctx* ctx) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->has_saved_state()) return fail(ctx, GBD_ERR_STATE, "no saved state");
+    ctx->eng->restore_state();
+    return GBD_OK;
+  });
+}
+
+int gbd_set_sweep_schedule(gbd_ctx* ctx, int32_t sweep, int32_t M, double tol) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "no problem set up");
+    gbd::Schedule& sc = ctx->eng->sched;
+    if (sweep < 0 || sweep >= (int)sc.M.size()) return fail(ctx, GBD_ERR_ARG, "sweep outside the schedule");
+    if (M < 1 || !(tol > 0) || !std::isfinite(tol)) return fail(ctx, GBD_ERR_ARG, "M < 1 or tol not positive");
+    sc.M[sweep] = M;
+    sc.tol[sweep] = tol;
     return GBD_OK;
   });
 }
@@ -689,6 +758,9 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   for (int i = 0; i < 5; ++i) s->tc_build_phase_ms[i] = t.tcb_ms[i];
   s->davidson_iterations = t.davidson_iters;
   s->inner_matvecs = t.inner_matvecs;
+  s->n_solves = t.n_solves;
+  s->n_solves_above_tol = t.n_above_tol;
+  s->sweep_max_residual = t.sweep_max_residual;
   for (int i = 0; i < 2; ++i) {
     s->tc_stage_alg_bytes[i] = t.tc_alg_st[i];
     s->tc_stage_box_bytes[2 * i] = t.tc_box_st[i][0];

@@ -328,6 +328,7 @@ Engine::~Engine() {
   for (auto& e : Lenv) free_env(e);
   for (auto& e : Renv) free_env(e);
   for (auto& s : sites) free_site(s);
+  free_snapshot();
   clear_states();
   if (psi) dfree(psi);
   cudaStreamSynchronize(stream);
@@ -1171,6 +1172,62 @@ void Engine::compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag) {
   dfree(d_one);
 }
 
+// Shift-and-invert inner PCG on the projected correction equation
+// (I - x x^T)(H - theta)(I - x x^T) t = -r, t orthogonal to x, from t = 0
+// with the projected diagonal preconditioner; a direction of non-positive
+// curvature ends it (on the first direction the result is the
+// preconditioned residual, i.e. the Olsen correction).  cg holds 4 psi_size
+// work vectors, partial/nblk the reduction scratch, dsums 4 doubles.
+void Engine::inner_pcg(const std::function<void(const double*, double*)>& op, const double* diag, const double* xr,
+                       const double* rr_vec, double th, double* tout, double* cg, double* partial, int nblk,
+                       double* dsums) {
+  const int64_t n = psi_size;
+  auto dot_host = [&](const double* a, const double* b) {
+    launch_multi_dot(a, n, 1, b, n, dsums + 2, partial, nblk, stream);
+    stats.launches += 2;
+    double v;
+    CK(cudaMemcpyAsync(&v, dsums + 2, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    sync();
+    settle();
+    stats.d2h += sizeof(double);
+    return v;
+  };
+  double *res = cg, *z = cg + n, *p = cg + 2 * n, *ap = cg + 3 * n;
+  launch_axpby(res, -1.0, rr_vec, 0.0, n, stream);
+  const double xr0 = dot_host(xr, res);
+  launch_axpby(res, -xr0, xr, 1.0, n, stream);
+  CK(cudaMemsetAsync(tout, 0, n * sizeof(double), stream));
+  launch_projected_precond(res, xr, diag, th, 1.0, n, z, partial, nblk, dsums, stream);
+  CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  stats.launches += 6;
+  double rz = dot_host(res, z);
+  const double nrhs = std::sqrt(std::max(dot_host(res, res), 0.0));
+  for (int j = 0; j < pcg_steps; ++j) {
+    op(p, ap);
+    stats.inner_matvecs++;
+    launch_axpby(ap, -th, p, 1.0, n, stream);
+    const double xa = dot_host(xr, ap);
+    launch_axpby(ap, -xa, xr, 1.0, n, stream);
+    stats.launches += 2;
+    const double pap = dot_host(p, ap);
+    if (!(pap > 0.0)) {
+      if (j == 0) CK(cudaMemcpyAsync(tout, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+      break;
+    }
+    const double alpha = rz / pap;
+    launch_axpby(tout, alpha, p, 1.0, n, stream);
+    launch_axpby(res, -alpha, ap, 1.0, n, stream);
+    stats.launches += 2;
+    if (std::sqrt(std::max(dot_host(res, res), 0.0)) < pcg_rel_tol * nrhs) break;
+    launch_projected_precond(res, xr, diag, th, 1.0, n, z, partial, nblk, dsums, stream);
+    const double rz1 = dot_host(res, z);
+    launch_axpby(p, 1.0, z, rz1 / rz, n, stream);
+    stats.launches += 4;
+    rz = rz1;
+  }
+  if (pcg_steps == 0) CK(cudaMemcpyAsync(tout, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+}
+
 // ------------------------------------------------------------------ Davidson
 // Davidson (ground state) on the two-site state: Rayleigh-Ritz in FP64 on
 // the host, vectors on the device; preconditioner t = -r / (diag - theta)
@@ -1232,47 +1289,6 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     double v;
     d2h(&v, dsums + 2, 1);
     return v;
-  };
-  // shift-and-invert inner PCG on the projected correction equation
-  // (I - x x^T)(H - theta)(I - x x^T) t = -r, t orthogonal to x, from t = 0
-  // with the projected diagonal preconditioner; a direction of non-positive
-  // curvature ends it (on the first direction the result is the
-  // preconditioned residual, i.e. the Olsen correction)
-  auto inner_pcg = [&](const double* xr, const double* rr_vec, double th, double* tout) {
-    double *res = cg, *z = cg + n, *p = cg + 2 * n, *ap = cg + 3 * n;
-    launch_axpby(res, -1.0, rr_vec, 0.0, n, stream);
-    const double xr0 = dot_host(xr, res);
-    launch_axpby(res, -xr0, xr, 1.0, n, stream);
-    CK(cudaMemsetAsync(tout, 0, n * sizeof(double), stream));
-    launch_projected_precond(res, xr, diag, th, 1.0, n, z, partial, nblk, dsums, stream);
-    CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-    stats.launches += 6;
-    double rz = dot_host(res, z);
-    const double nrhs = std::sqrt(std::max(dot_host(res, res), 0.0));
-    for (int j = 0; j < pcg_steps; ++j) {
-      opp(p, ap);
-      stats.inner_matvecs++;
-      launch_axpby(ap, -th, p, 1.0, n, stream);
-      const double xa = dot_host(xr, ap);
-      launch_axpby(ap, -xa, xr, 1.0, n, stream);
-      stats.launches += 2;
-      const double pap = dot_host(p, ap);
-      if (!(pap > 0.0)) {
-        if (j == 0) CK(cudaMemcpyAsync(tout, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-        break;
-      }
-      const double alpha = rz / pap;
-      launch_axpby(tout, alpha, p, 1.0, n, stream);
-      launch_axpby(res, -alpha, ap, 1.0, n, stream);
-      stats.launches += 2;
-      if (std::sqrt(std::max(dot_host(res, res), 0.0)) < pcg_rel_tol * nrhs) break;
-      launch_projected_precond(res, xr, diag, th, 1.0, n, z, partial, nblk, dsums, stream);
-      const double rz1 = dot_host(res, z);
-      launch_axpby(p, 1.0, z, rz1 / rz, n, stream);
-      stats.launches += 4;
-      rz = rz1;
-    }
-    if (pcg_steps == 0) CK(cudaMemcpyAsync(tout, z, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
   };
   // v0 = psi / |psi|, s0 = H v0
   dots(psi, 1, psi, drow + max_space + 1);
@@ -1350,7 +1366,7 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
       launch_projected_precond(r, x, diag, theta, -1.0, n, t, partial, nblk, dsums, stream);   // Olsen
       stats.launches += 3;
     } else if (pk == 3) {
-      inner_pcg(x, r, theta, t);
+      inner_pcg(opp, diag, x, r, theta, t, cg, partial, nblk, dsums);
     }
     if (k == max_space) {
       int kk = std::min(keep, k);
@@ -1612,6 +1628,9 @@ double Engine::solve_tiers(Sigma& sg, const double* diag, double tol, int precis
   }
   stats.max_final_residual = std::max(stats.max_final_residual, stats.last_residual);
   stats.sum_final_residual += stats.last_residual;
+  stats.sweep_max_residual = std::max(stats.sweep_max_residual, stats.last_residual);
+  stats.n_solves++;
+  if (stats.last_residual >= tol) stats.n_above_tol++;
   return theta;
 }
 
@@ -1667,6 +1686,43 @@ void Engine::probe_step(int k, int precision, int refine, double tol, double* th
   dfree(y);
   dfree(diag);
   free_sigma(sg, planned);
+  free_enl(sg.lenl);
+  free_enl(sg.renl);
+  sync();
+}
+
+void Engine::pcg_selftest(int k, const double* x_host, const double* r_host, double theta, double* t_host,
+                          int64_t* matvecs) {
+  if (k < 0 || k + 1 >= n || !Lenv[k].valid || !Renv[k + 2].valid)
+    throw Error(-6, "pcg_selftest needs valid environments at the centre k");
+  setup_two_site(k);
+  Sigma sg;
+  AxpyPlan ax;
+  build_lenl(k, Lenv[k], EL, sg.lenl, ax);
+  finish_enl(sg.lenl, ax);
+  build_renl(k + 1, Renv[k + 2], ER, sg.renl, ax);
+  finish_enl(sg.renl, ax);
+  double* diag = dalloc<double>(psi_size);
+  compute_diag(sg.lenl, sg.renl, diag);
+  plan_sigma(sg.lenl, sg.renl, sg);
+  const int64_t N = psi_size;
+  double* x = dalloc<double>(N);
+  double* r = dalloc<double>(N);
+  double* t = dalloc<double>(N);
+  double* cg = dalloc<double>((size_t)4 * N);
+  const int nblk = reduction_blocks(N);
+  double* partial = dalloc<double>((size_t)2 * nblk);
+  double* dsums = dalloc<double>(4);
+  CK(cudaMemcpyAsync(x, x_host, N * sizeof(double), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(r, r_host, N * sizeof(double), cudaMemcpyHostToDevice, stream));
+  const int64_t m0 = stats.inner_matvecs;
+  inner_pcg([&](const double* a, double* b) { sigma(sg, a, b); }, diag, x, r, theta, t, cg, partial, nblk, dsums);
+  CK(cudaMemcpyAsync(t_host, t, N * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  settle();
+  *matvecs = stats.inner_matvecs - m0;
+  for (void* q : {(void*)x, (void*)r, (void*)t, (void*)cg, (void*)partial, (void*)dsums, (void*)diag}) dfree(q);
+  free_sigma(sg, true);
   free_enl(sg.lenl);
   free_enl(sg.renl);
   sync();
@@ -1872,13 +1928,49 @@ void Engine::prepare(int n_, int n_elec, int two_sz, int n_chol, const double* h
     }
   }
   build_mpo(n, h.data(), eri.data(), n / 2, mpo);
-  clear_states();   // deflated states belong to the previous problem
+  clear_states();   // deflated states and a saved MPS belong to the previous problem
+  free_snapshot();
   stats = Stats();
   sweep_E.clear();
   prepared = false;
   t1_iters_cur = t1_steps_cur = t1_steps_prev = 0;
   t1_iters_prev = -1;
   skip_tier1 = false;
+}
+
+void Engine::free_snapshot() {
+  for (auto& st : snap_sites) free_site(st);
+  snap_sites.clear();
+  snap_bonds.clear();
+}
+
+void Engine::save_state() {
+  if (!prepared || (int)sites.size() != n) throw Error(-6, "save_state before an MPS exists");
+  free_snapshot();
+  snap_bonds = bonds;
+  for (const Site& st : sites) {
+    Site c = st;
+    c.d = dalloc<double>(st.size);
+    CK(cudaMemcpyAsync(c.d, st.d, st.size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    snap_sites.push_back(c);
+  }
+  sync();
+}
+
+void Engine::restore_state() {
+  if (snap_sites.empty()) throw Error(-6, "restore_state without a saved state");
+  for (auto& st : sites) free_site(st);
+  sites.assign(n, Site());
+  bonds = snap_bonds;
+  for (int i = 0; i < n; ++i) {
+    Site c = snap_sites[i];
+    c.d = dalloc<double>(c.size);
+    CK(cudaMemcpyAsync(c.d, snap_sites[i].d, c.size * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    sites[i] = c;
+  }
+  build_right_envs(2);
+  build_left_envs(0);
+  sync();
 }
 
 void Engine::init_state() {
@@ -1899,6 +1991,7 @@ double Engine::sweep(int s) {
   }
   t1_iters_cur = t1_steps_cur = 0;
   skip_tier1 = s > 0 && t1_steps_prev > 0 && t1_iters_prev < 2 * t1_steps_prev;
+  stats.sweep_max_residual = 0;
   for (int k = 0; k <= n - 2; ++k) e = step(k, 0, M, tol, nullptr, nullptr);
   for (int k = n - 2; k >= 0; --k) e = step(k, 1, M, tol, nullptr, nullptr);
   sweep_E.push_back(e);

@@ -83,6 +83,8 @@ struct Stats {
   int64_t inner_matvecs = 0;   // sigma builds inside the inner PCG corrections
   int64_t tier_iters[3] = {0, 0, 0};
   double max_final_residual = 0, sum_final_residual = 0;   // over Davidson solves
+  int64_t n_solves = 0, n_above_tol = 0;   // Davidson solves, and those that ended with ||r|| >= tol
+  double sweep_max_residual = 0;           // largest final ||r|| of the current (or last) sweep
   int64_t graph_launches = 0, autotune_trials = 0;
   double tc_gemm_ms_st[2] = {0, 0};   // tc_gemm_kernel time by stage (A, B)
   double tc_alg_st[2] = {0, 0}, tc_box_st[2][2] = {{0, 0}, {0, 0}}, tc_dense_st[2][2] = {{0, 0}, {0, 0}};   // per stage: algorithmic, TMA box bytes (A, B)
@@ -104,6 +106,9 @@ struct Stats {
     for (int i = 0; i < 3; ++i) tier_iters[i] += o.tier_iters[i];
     max_final_residual = std::max(max_final_residual, o.max_final_residual);
     sum_final_residual += o.sum_final_residual;
+    n_solves += o.n_solves;
+    n_above_tol += o.n_above_tol;
+    sweep_max_residual = std::max(sweep_max_residual, o.sweep_max_residual);
     graph_launches += o.graph_launches; autotune_trials += o.autotune_trials;
     for (int s = 0; s < 2; ++s) {
       tc_gemm_ms_st[s] += o.tc_gemm_ms_st[s];
@@ -168,6 +173,13 @@ class Engine {
   double adapt_disc = 0.0;
   int adapt_mmin = 1;
   int n_stored() const { return (int)defl.size(); }
+  // a device copy of the MPS with the centre at bond (0,1) (after
+  // init_state or a full sweep), and the return to it: sites and bonds are
+  // copied back and the environments rebuilt, so that several sweeps can
+  // start from one state
+  void save_state();
+  void restore_state();
+  bool has_saved_state() const { return !snap_sites.empty(); }
   // debug / test hooks
   void set_mps(const int* nsec, const int* sectors, const double* data, int center);
   int64_t two_site_size(int k);
@@ -226,6 +238,9 @@ class Engine {
   std::vector<Bond> bonds;
   std::vector<Site> sites;
   std::vector<Env> Lenv, Renv;
+  std::vector<Bond> snap_bonds;   // save_state()
+  std::vector<Site> snap_sites;
+  void free_snapshot();
 
   // ---- deflated states and their overlap environments
   struct Ov {                       // <current basis | stored basis> on one bond, per current sector
@@ -308,6 +323,8 @@ class Engine {
   // most `refine` FP64 iterations; the Ritz vector is left in psi
   double solve_tiers(Sigma& sg, const double* diag, double tol, int precision, int refine, bool& planned);
   void free_sigma(Sigma& sg, bool planned);
+  void inner_pcg(const std::function<void(const double*, double*)>& op, const double* diag, const double* xr,
+                 const double* rr_vec, double th, double* tout, double* cg, double* partial, int nblk, double* dsums);
   TcPlan* tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune tune = TcTune());
   TcPlan* tc_plan(const EnlOp& lenl, const EnlOp& renl, int prec);   // tc_build with the tuned shape
   TcPlan* tc_plan_impl(const EnlOp& lenl, const EnlOp& renl, int prec);
@@ -347,6 +364,10 @@ class Engine {
   // without decimation or environment update: Ritz value, and the FP64
   // Rayleigh quotient and FP64 residual norm of the resulting vector
   void probe_step(int k, int precision, int refine, double tol, double* theta, double* e64, double* r64);
+  // the inner-PCG correction of the Davidson solver at centre k with the
+  // FP64 sigma and the step's own H_eff diagonal, from host x, r and theta
+  void pcg_selftest(int k, const double* x_host, const double* r_host, double theta, double* t_host,
+                    int64_t* matvecs);
 
  private:
   void init_mps(uint64_t seed, int M);

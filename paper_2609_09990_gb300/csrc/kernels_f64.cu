@@ -377,6 +377,9 @@ extern "C" int gbd_multi_dot_noalloc(int32_t device, const double* V, int64_t st
   if (!V || !x || !out) return -1;
   if (k < 1 || k > kNoAllocMaxK || n < 0 || stride < n) return -1;
   if (device < 0 || device >= 256) return -1;
+  // an error left pending by earlier work on this thread is not ours to
+  // consume: report it, launch nothing and leave it in place
+  if (cudaPeekAtLastError() != cudaSuccess) return -3;
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess) return -3;
   if (cudaSetDevice(device) != cudaSuccess) return -3;

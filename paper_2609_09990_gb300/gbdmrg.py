@@ -58,7 +58,8 @@ class gbd_stats(C.Structure):
                 ("truncate_rho_ms", C.c_double), ("truncate_eig_ms", C.c_double), ("env_wall_ms", C.c_double),
                 ("tc_stage_alg_bytes", C.c_double * 2), ("tc_stage_box_bytes", C.c_double * 4),
                 ("tc_stage_dense_bytes", C.c_double * 4), ("tc_gemm_ms_by_stage", C.c_double * 2),
-                ("davidson_iterations", C.c_int64), ("inner_matvecs", C.c_int64)]
+                ("davidson_iterations", C.c_int64), ("inner_matvecs", C.c_int64), ("n_solves", C.c_int64),
+                ("n_solves_above_tol", C.c_int64), ("sweep_max_residual", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -92,6 +93,8 @@ def lib():
         "gbd_solve_batched": (C.c_int, [vp, C.c_int32, C.POINTER(gbd_problem), C.POINTER(gbd_schedule),
                                         C.POINTER(gbd_result)]),
         "gbd_set_batch_workers": (C.c_int, [vp, C.c_int32]),
+        "gbd_host_batch_costs": (C.c_int, [C.c_int32, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), _dp]),
+        "gbd_host_partition": (C.c_int, [C.c_int32, _dp, C.c_int32, _ip, _dp]),
         "gbd_set_graphs": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_min_two_site": (C.c_int, [vp, C.c_int64]),
         "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
@@ -100,6 +103,10 @@ def lib():
         "gbd_set_tc_order": (C.c_int, [vp, C.c_int32]),
         "gbd_probe_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp]),
         "gbd_init_state": (C.c_int, [vp]),
+        "gbd_save_state": (C.c_int, [vp]),
+        "gbd_pcg_selftest": (C.c_int, [vp, C.c_int32, _dp, _dp, C.c_double, _dp, C.POINTER(C.c_int64)]),
+        "gbd_restore_state": (C.c_int, [vp]),
+        "gbd_set_sweep_schedule": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double]),
         "gbd_set_precision": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "gbd_run_sweep": (C.c_int, [vp, C.c_int32, _dp]),
         "gbd_final_energy": (C.c_int, [vp, _dp]),
@@ -117,7 +124,6 @@ def lib():
         "gbd_get_batch_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
         "gbd_mps_init_value": (C.c_double, [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                             C.c_int32, C.c_int32]),
-        "gbd_probe_peaks": (C.c_int, [C.c_int32, _dp, _dp]),
         "gbd_wait_selftest": (C.c_int, [C.c_int32, C.c_int32, _ip, _ip]),
         "gbd_correction_selftest": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _dp, _dp, _dp, C.c_double, _dp, _dp,
                                                _dp]),
@@ -194,17 +200,8 @@ class Context:
             msg = self.L.gbd_last_error(self.ptr).decode()
             raise GbdError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
 
-    def _structs(self, h, chol, n_elec, two_sz, bond_dims, tols, seed=1, precision=GBD_FP64,
-                 preconditioner=GBD_PRECOND_DIAG, max_iter=100, max_subspace=24, svd_cutoff=1e-12,
-                 e_core=0.0, fp64_refine=2):
-        h = np.ascontiguousarray(h, dtype=np.float64)
-        chol = np.ascontiguousarray(chol, dtype=np.float64)
-        bd = np.ascontiguousarray(bond_dims, dtype=np.int32)
-        tl = np.ascontiguousarray(tols, dtype=np.float64)
-        self._keep = [h, chol, bd, tl]
-        p = gbd_problem(h.shape[0], n_elec, two_sz, chol.shape[0], _d(h), _d(chol), e_core)
-        s = gbd_schedule(len(bd), _i(bd), _d(tl), max_iter, max_subspace, precision, preconditioner,
-                         seed, svd_cutoff, fp64_refine)
+    def _structs(self, *args, **kw):
+        p, s, self._keep = _make_structs(*args, **kw)
         return p, s
 
     def solve(self, h, chol, n_elec, two_sz, bond_dims, tols, rdms=False, **kw):
@@ -279,6 +276,25 @@ class Context:
 
     def init_state(self):
         self._check(self.L.gbd_init_state(self.ptr), "gbd_init_state")
+
+    def pcg_selftest(self, k, x, r, theta):
+        """(t, matvecs) of the solver's inner-PCG correction at centre k."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        t = np.empty_like(x)
+        mv = C.c_int64()
+        self._check(self.L.gbd_pcg_selftest(self.ptr, k, _d(x), _d(r), float(theta), _d(t), C.byref(mv)),
+                    "gbd_pcg_selftest")
+        return t, mv.value
+
+    def save_state(self):
+        self._check(self.L.gbd_save_state(self.ptr), "gbd_save_state")
+
+    def restore_state(self):
+        self._check(self.L.gbd_restore_state(self.ptr), "gbd_restore_state")
+
+    def set_sweep_schedule(self, sweep, M, tol):
+        self._check(self.L.gbd_set_sweep_schedule(self.ptr, sweep, M, tol), "gbd_set_sweep_schedule")
 
     def run_sweep(self, sweep):
         e = C.c_double()
@@ -450,6 +466,48 @@ class Context:
 
 
 # ---- host-only planner pieces
+def _make_structs(h, chol, n_elec, two_sz, bond_dims, tols, seed=1, precision=GBD_FP64,
+                  preconditioner=GBD_PRECOND_DIAG, max_iter=100, max_subspace=24, svd_cutoff=1e-12,
+                  e_core=0.0, fp64_refine=2):
+    """(gbd_problem, gbd_schedule, arrays they point into: keep them alive)."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    chol = np.ascontiguousarray(chol, dtype=np.float64)
+    bd = np.ascontiguousarray(bond_dims, dtype=np.int32)
+    tl = np.ascontiguousarray(tols, dtype=np.float64)
+    p = gbd_problem(h.shape[0], n_elec, two_sz, chol.shape[0], _d(h), _d(chol), e_core)
+    s = gbd_schedule(len(bd), _i(bd), _d(tl), max_iter, max_subspace, precision, preconditioner,
+                     seed, svd_cutoff, fp64_refine)
+    return p, s, [h, chol, bd, tl]
+
+
+def host_batch_costs(problems):
+    """gbd_host_batch_costs over (h, chol, n_elec, two_sz, bond_dims, tols, kwargs) tuples."""
+    n = len(problems)
+    ps = (gbd_problem * max(n, 1))()
+    ss = (gbd_schedule * max(n, 1))()
+    keep = []
+    for i, (h, chol, ne, sz, bd, tl, kw) in enumerate(problems):
+        ps[i], ss[i], k = _make_structs(h, chol, ne, sz, bd, tl, **kw)
+        keep.append(k)
+    cost = np.zeros(max(n, 1))
+    rc = lib().gbd_host_batch_costs(n, ps, ss, _d(cost))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_batch_costs: {ERRORS.get(rc, rc)}")
+    return cost[:n].copy()
+
+
+def host_partition(cost, ranks):
+    """gbd_host_partition: (owner rank of each problem, summed cost per rank)."""
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    n = cost.size
+    owner = np.zeros(max(n, 1), dtype=np.int32)
+    load = np.zeros(max(ranks, 1))
+    rc = lib().gbd_host_partition(n, _d(cost), ranks, _i(owner), _d(load))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_partition: {ERRORS.get(rc, rc)}")
+    return owner[:n].copy(), load[:ranks].copy()
+
+
 def host_sym_eig(A):
     """Host eigensolver of the decimation: (w ascending, Z columns = eigenvectors)."""
     A = np.ascontiguousarray(A, dtype=np.float64)
@@ -555,15 +613,6 @@ def wait_selftest(arrive, device=0):
     if rc != GBD_OK:
         raise GbdError(f"gbd_wait_selftest: {ERRORS.get(rc, rc)}")
     return e.value, o.value
-
-
-def probe_peaks(device=0):
-    """Measured FP64 / FP32 FMA throughput (TFLOP/s) of the device."""
-    a, b = C.c_double(), C.c_double()
-    rc = lib().gbd_probe_peaks(device, C.byref(a), C.byref(b))
-    if rc != GBD_OK:
-        raise GbdError(f"gbd_probe_peaks: {ERRORS.get(rc, rc)}")
-    return a.value, b.value
 
 
 def mps_init_value(seed, site, na, nb, s, row, col):

@@ -1,10 +1,18 @@
 """Batched solve of independent active spaces: every result equals the one
-the single-problem entry point gives, whatever the number of workers;
-validation happens before any work; per-problem status."""
+the single-problem entry point gives, whatever the number of workers, and
+the oracle's (FCI where the bond dimension is exact, the oracle's DMRG run
+at the same bond dimension otherwise); validation happens before any work;
+per-problem status."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from gbd_synth import make_integrals
+from oracle import fock
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +56,28 @@ def test_batched_equals_single_solves(G):
             assert np.array_equal(a["sweep_energies"], b["sweep_energies"])
             assert np.array_equal(a["rdm1"], b["rdm1"])
             assert a["n_matvec"] == b["n_matvec"]
+
+
+def test_batched_energies_match_oracle(G):
+    # CASES[1] (n = 4, M = 16) and CASES[3] (n = 5, M = 24) keep every state
+    # of every bond: FCI.  The others are truncated: the oracle's DMRG run
+    # with the same seed, M and schedule (tests/golden/make_golden.py --dmrg).
+    ps = problems()
+    ctx = G.Context(0)
+    rc, res = ctx.solve_batched(ps, workers=0)
+    ctx.close()
+    assert rc == 0
+    for i in (1, 3):
+        h, chol, ne, sz = ps[i][:4]
+        w, _, _ = fock.ground_state(h, fock.eri_from_chol(chol), (ne + sz) // 2, (ne - sz) // 2)
+        assert abs(res[i]["energy"] - w[0]) < 1e-9, i
+    for i, name in ((0, "dmrg_batch_n6_seed11.json"), (2, "dmrg_batch_n8_seed13.json"),
+                    (4, "dmrg_batch_n7_seed15.json")):
+        with open(os.path.join(GOLDEN, name)) as f:
+            g = json.load(f)
+        assert (g["n_orb"], g["n_chol"], g["seed"], g["M"], g["sweeps"]) == CASES[i]
+        assert np.abs(res[i]["sweep_energies"] - np.array(g["sweep_energies"])).max() < 1e-9, i
+        assert abs(res[i]["energy"] - g["energy"]) < 1e-9, i
 
 
 def test_batched_validates_everything_first(G):

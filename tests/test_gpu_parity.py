@@ -155,3 +155,45 @@ def test_invalid_inputs_are_rejected(G):
     with pytest.raises(G.GbdError, match="GBD_ERR_STATE"):
         G.Context(0).run_sweep(0)
     ctx.close()
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _solve_like(G, g, **setup):
+    h, chol = make_integrals(g["n_orb"], g["n_chol"], g["seed"])
+    ctx = G.Context(0)
+    for k, v in setup.items():
+        getattr(ctx, k)(*v)
+    r = ctx.solve(h, chol, g["n_elec"], g["two_sz"], [g["M"]] * g["sweeps"], [g["tol"]] * g["sweeps"],
+                  seed=g["seed"])
+    bonds = [ctx.get_bond(b) for b in range(g["n_orb"] + 1)]
+    ctx.close()
+    return r, bonds
+
+
+@pytest.mark.parametrize("name", ["dmrg_cas8_m48_adaptive1e-6.json", "dmrg_cas8_m48_adaptive1e-4.json"])
+def test_adaptive_bond_dim_solve_matches_oracle(G, name):
+    # per-bond adaptive bond dimension in a GPU solve (cap M = 48) against
+    # the oracle's run with the same discarded-weight target (stored by
+    # tests/golden/make_golden.py --dmrg): kept sector dimensions of every
+    # bond bit for bit, sweep energies to 1e-9 Ha
+    g = _golden(name)
+    r, bonds = _solve_like(G, g, set_adaptive_bond_dim=(g["max_discarded"], g["m_min"]))
+    assert np.abs(r["sweep_energies"] - np.array(g["sweep_energies"])).max() < 1e-9
+    assert abs(r["energy"] - g["energy"]) < 1e-9
+    for b, ref in enumerate(g["bonds"]):
+        assert np.array_equal(bonds[b], np.array(ref, dtype=np.int32).reshape(-1, 3)), b
+
+
+def test_fp64_sweeps_cas10_m96_match_oracle(G):
+    # two FP64 sweeps of CAS(10,10) at M = 96: multi-sector tiles and both
+    # FP64 GEMM kernels (register-blocked and flat), against the oracle run
+    g = _golden("dmrg_cas10_m96_seed7.json")
+    r, bonds = _solve_like(G, g)
+    assert np.abs(r["sweep_energies"] - np.array(g["sweep_energies"])).max() < 1e-9
+    assert abs(r["energy"] - g["energy"]) < 1e-9
+    for b, ref in enumerate(g["bonds"]):
+        assert np.array_equal(bonds[b], np.array(ref, dtype=np.int32).reshape(-1, 3)), b

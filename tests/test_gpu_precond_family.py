@@ -81,3 +81,51 @@ def test_reduced_precision_solve_with_each_correction(G):
         ctx.close()
         assert st["n_sigma_tc"] > 0
         assert abs(r["energy"] - e_fci) < 3e-6, (kind, r["energy"] - e_fci)
+
+
+@pytest.mark.parametrize("case", ["near_converged", "random_mid_spectrum"])
+def test_inner_pcg_correction_matches_oracle(G, case):
+    # the solver's inner PCG (FP64 sigma of a real two-site step, its own
+    # H_eff diagonal) against oracle.precond.pcg_correction with the oracle's
+    # H_eff and diagonal, element by element; the random mid-spectrum Ritz
+    # value makes the projected operator indefinite, so the curvature guard
+    # ends the iteration there
+    from oracle import dmrg
+    from oracle import fci as fci_mod
+    n, ne, nq, seed, M, k = 8, 8, 10, 3, 30, 3
+    h, chol = make_integrals(n, nq, seed)
+    d = dmrg.DMRG(h, chol, ne, 0, M, seed=seed)
+    for j in range(k):
+        d.step(j, M, 1e-10, "L")
+    keys = dmrg.psi_keys(d.dims[k], d.dims[k + 2])
+    L, W1, W2, R = d.heff_parts(k)
+
+    def mv(v):
+        return dmrg.flatten(dmrg.apply_heff(L, W1, W2, R, dmrg.unflatten(v, keys, d.dims[k], d.dims[k + 2]),
+                                            d.mpo, k), keys, d.dims[k], d.dims[k + 2])
+
+    diag = dmrg.flatten(dmrg.heff_diag(L, W1, W2, R, keys, d.mpo, k, d.dims[k], d.dims[k + 2]),
+                        keys, d.dims[k], d.dims[k + 2])
+    rng = np.random.default_rng(41)
+    if case == "near_converged":
+        x0 = dmrg.flatten(dmrg.two_site_psi(d.sites[k], d.sites[k + 1], d.dims[k + 1]), keys, d.dims[k],
+                          d.dims[k + 2])
+        _, X = fci_mod.davidson(mv, diag, tol=1e-3, guess=x0)
+        x = X[:, 0] + 1e-4 * rng.standard_normal(X.shape[0])
+    else:
+        x = rng.standard_normal(diag.size)
+    x /= np.linalg.norm(x)
+    sx = mv(x)
+    theta = float(x @ sx)
+    r = sx - theta * x
+    t_ref, nmv_ref = precond.pcg_correction(mv, x, r, diag, theta, steps=4, rel_tol=0.1)
+    ctx = G.Context(0)
+    ctx.setup(h, chol, ne, 0, [M], [1e-10], seed=seed)
+    ns, tr, data = dmrg.canonical_blocks(d)
+    ctx.set_mps(ns, tr, data, k)
+    assert ctx.two_site_size(k) == x.size
+    t, nmv = ctx.pcg_selftest(k, x, r, theta)
+    ctx.close()
+    assert nmv == nmv_ref
+    assert np.abs(t - t_ref).max() <= 1e-9 * np.abs(t_ref).max(), np.abs(t - t_ref).max() / np.abs(t_ref).max()
+    assert abs(x @ t) <= 1e-10 * np.linalg.norm(t)

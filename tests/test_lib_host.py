@@ -201,3 +201,42 @@ def test_fiedler_order_of_a_ground_state_mutual_information(G):
     full[st] = v[:, 0]
     I = entropy.mutual_information(full, 6)
     assert list(G.fiedler_order(I)) == list(ordering.fiedler_order(I))
+
+
+def test_lpt_partition_against_brute_force(G):
+    # longest-processing-time-first greedy: the partition covers every
+    # problem once, is deterministic (ties by index and lowest rank), and its
+    # makespan is within (4/3 - 1/(3m)) of the optimum found by brute force
+    import itertools
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        m = 2 + trial % 3
+        n = 5 + trial % 4
+        cost = rng.integers(1, 20, size=n).astype(float)
+        owner, load = G.host_partition(cost, m)
+        assert owner.min() >= 0 and owner.max() < m
+        assert np.allclose([cost[owner == r].sum() for r in range(m)], load)
+        best = min(max(sum(cost[i] for i in range(n) if a[i] == r) for r in range(m))
+                   for a in itertools.product(range(m), repeat=n))
+        assert load.max() <= (4 / 3 - 1 / (3 * m)) * best + 1e-12
+    # ties: equal costs go round-robin from rank 0 in index order
+    owner, load = G.host_partition(np.ones(7), 3)
+    assert owner.tolist() == [0, 1, 2, 0, 1, 2, 0]
+    # more ranks than problems; no problems
+    owner, load = G.host_partition(np.array([3.0, 1.0]), 4)
+    assert owner.tolist() == [0, 1] and load.tolist() == [3.0, 1.0, 0.0, 0.0]
+    owner, load = G.host_partition(np.zeros(0), 2)
+    assert owner.size == 0 and load.tolist() == [0.0, 0.0]
+    for bad in (np.array([1.0, -1.0]), np.array([np.nan])):
+        with pytest.raises(G.GbdError, match="GBD_ERR_ARG"):
+            G.host_partition(bad, 2)
+    with pytest.raises(G.GbdError, match="GBD_ERR_ARG"):
+        G.host_partition(np.ones(3), 0)
+
+
+def test_batch_costs(G):
+    from gbd_synth import make_integrals
+    h, chol = make_integrals(5, 3, 1)
+    probs = [(h, chol, 5, 1, [8, 32, 16], [1e-6] * 3, {}), (h, chol, 5, 1, [4], [1e-6], {})]
+    c = G.host_batch_costs(probs)
+    assert c.tolist() == [5 * 32 ** 3 * 3, 5 * 4 ** 3 * 1]
