@@ -174,6 +174,38 @@ int gbd_solve_states(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedul
  * disconnected. */
 int gbd_host_fiedler_order(int32_t n, const double *W, int32_t *order);
 
+/* Spin-summed three-particle RDM of the state the last gbd_solve (or
+ * gbd_init_state / sweeps / gbd_set_mps) on this context left, one of the
+ * densities the paper forms on the device (Sec. "Computational details"):
+ *   rdm3[((((p n + q) n + r) n + s) n + t) n + u]
+ *     = sum_{sigma,tau,upsilon} <a+_p sigma a+_r tau a+_t upsilon a_u upsilon a_s tau a_q sigma>
+ * (the index convention of gbd_result.rdm2 extended by one pair), n^6
+ * doubles, caller-owned.  Computed in FP64 from the determinant expansion of
+ * the MPS; it needs 2 n^2 vectors of the determinant length on the device,
+ * so it is refused (GBD_ERR_ARG) above 64 GB of them (CAS(12,12): 2 GB).
+ * GBD_ERR_STATE without a state. */
+int gbd_rdm3(gbd_ctx *ctx, double *rdm3);
+
+/* Orbital entropies and mutual information of the same state (the paper
+ * orders the lattice by the mutual information, Sec. "Cholesky
+ * decomposition for the wavefunction", ingredient (ii)):
+ * s1[i] = -tr rho_i ln rho_i of the one-orbital RDM, mi[i n + j] = s_i + s_j
+ * - s_ij with s_ij the entropy of the two-orbital RDM (0 on the diagonal;
+ * values below 0 from rounding are set to 0).  The RDMs are fermionic partial
+ * traces of the determinant expansion (up to 4e8 determinants).  s1 or mi
+ * may be NULL.  GBD_ERR_STATE without a state. */
+int gbd_orbital_entropies(gbd_ctx *ctx, double *s1, double *mi);
+
+/* Orbital order by mutual information: a preliminary solve of `problem`
+ * with `schedule` (typically a small bond dimension and a few sweeps), the
+ * mutual information of its state (gbd_orbital_entropies), and the Fiedler
+ * order of that coupling (gbd_host_fiedler_order): order[k] = the orbital to
+ * place at site k; mi [n*n] (may be NULL) receives the coupling.  The caller
+ * permutes h and the Cholesky slices and solves again.  Errors as for
+ * gbd_solve and gbd_host_fiedler_order. */
+int gbd_mi_order(gbd_ctx *ctx, const gbd_problem *problem, const gbd_schedule *schedule, int32_t *order,
+                 double *mi);
+
 /* Many independent active spaces in one call (the paper solves one active
  * space per call; batching is this library's addition).  problems[i] is
  * solved with schedules[i] into results[i] (caller-owned, as for

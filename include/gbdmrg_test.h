@@ -157,6 +157,13 @@ int gbd_run_step(gbd_ctx *ctx, int32_t k, int32_t dir, int32_t M, double tol, do
 /* One- and two-particle RDMs of the current MPS (conventions of
  * gbd_result); rdm1 [n^2], rdm2 [n^4] or NULL. */
 int gbd_rdms(gbd_ctx *ctx, double *rdm1, double *rdm2);
+/* One- and two-orbital reduced density matrices of the current MPS (the
+ * inputs of gbd_orbital_entropies): rho1 [n][4][4] in the local basis |0>,
+ * |alpha>, |beta>, |alpha beta> = c+_alpha^x c+_beta^y |vac> (index x + 2y);
+ * rho2 [n(n-1)/2][16][16] for the pairs (i < j) in lexicographic order, pair
+ * index x_i + 4 x_j with the modes of i before those of j.  Either may be
+ * NULL. */
+int gbd_orbital_rdms(gbd_ctx *ctx, double *rho1, double *rho2);
 /* MPO channel keys of one bond (kind<<40 | nops<<32 | code0<<16 | code1). */
 int gbd_mpo_labels(gbd_ctx *ctx, int32_t bond, uint64_t *keys, int32_t cap, int32_t *count);
 /* One environment block (side 0 = left, 1 = right) for (channel, sector index). */

@@ -177,6 +177,24 @@ def spin_square(n_orb: int) -> sp.csr_matrix:
     return (Sz @ Sz + 0.5 * (Sp @ Sm + Sm @ Sp)).tocsr()
 
 
+def from_ci(C: np.ndarray, n_orb: int, n_alpha: int, n_beta: int) -> np.ndarray:
+    """Fock-space vector of a determinant-basis vector C[I_alpha, I_beta]
+    (oracle/fci.py: alpha creators in ascending orbital order, then beta
+    creators, strings at their colex addresses).  Each determinant is
+    rewritten in this module's site-major creator order; the reordering
+    passes every beta creator of orbital q over the alpha creators of the
+    orbitals p > q, so its sign is (-1)^(sum_q n_q,beta #{p > q: n_p,alpha})."""
+    from oracle import fci
+    C = np.asarray(C, dtype=np.float64).reshape(len(fci.strings(n_orb, n_alpha)), -1)
+    full = np.zeros(1 << (2 * n_orb))
+    for ia, aocc in enumerate(fci.strings(n_orb, n_alpha)):
+        for ib, bocc in enumerate(fci.strings(n_orb, n_beta)):
+            st = sum(1 << (2 * p) for p in aocc) | sum(1 << (2 * q + 1) for q in bocc)
+            ex = sum(1 for q in bocc for p in aocc if p > q)
+            full[st] = (-1.0) ** ex * C[ia, ib]
+    return full
+
+
 def eri_from_chol(chol: np.ndarray) -> np.ndarray:
     """(pq|rs) = sum_Q L^Q_pq L^Q_rs (Sec. "The DMRG-QD-NEVPT2 energy",
     Cholesky-factorised two-electron tensor)."""

@@ -598,6 +598,84 @@ int gbd_rdms(gbd_ctx* ctx, double* rdm1, double* rdm2) {
   });
 }
 
+int gbd_rdm3(gbd_ctx* ctx, double* rdm3) {
+  return guarded(ctx, [&]() {
+    if (!rdm3) return fail(ctx, GBD_ERR_ARG, "rdm3 is NULL");
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    ctx->eng->rdm3(rdm3);
+    return GBD_OK;
+  });
+}
+
+int gbd_orbital_rdms(gbd_ctx* ctx, double* rho1, double* rho2) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    ctx->eng->orbital_rdms(rho1, rho2);
+    return GBD_OK;
+  });
+}
+
+namespace {
+// -tr rho ln rho from the eigenvalues above 1e-14 of the symmetrised rho
+double entropy_of(int m, const double* rho) {
+  std::vector<double> A((size_t)m * m), w(m), Z((size_t)m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = 0.5 * (rho[(size_t)i * m + j] + rho[(size_t)j * m + i]);
+  if (gbd::sym_eig(m, A.data(), w.data(), Z.data()) != 0) throw gbd::Error(GBD_ERR_NOCONV, "entropy eigensolver failed");
+  double s = 0;
+  for (double x : w)
+    if (x > 1e-14) s -= x * std::log(x);
+  return s;
+}
+
+void entropies(gbd::Engine& e, double* s1, double* mi) {
+  const int n = e.n;
+  std::vector<double> r1((size_t)n * 16), r2((size_t)std::max(1, n * (n - 1) / 2) * 256);
+  e.orbital_rdms(r1.data(), r2.data());
+  std::vector<double> s(n);
+  for (int i = 0; i < n; ++i) s[i] = entropy_of(4, r1.data() + (size_t)i * 16);
+  if (s1) std::copy(s.begin(), s.end(), s1);
+  if (mi) {
+    for (int i = 0; i < n; ++i) mi[(size_t)i * n + i] = 0.0;
+    for (int i = 0, pr = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j, ++pr) {
+        const double v = std::max(0.0, s[i] + s[j] - entropy_of(16, r2.data() + (size_t)pr * 256));
+        mi[(size_t)i * n + j] = mi[(size_t)j * n + i] = v;
+      }
+  }
+}
+}  // namespace
+
+int gbd_orbital_entropies(gbd_ctx* ctx, double* s1, double* mi) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    entropies(*ctx->eng, s1, mi);
+    return GBD_OK;
+  });
+}
+
+int gbd_mi_order(gbd_ctx* ctx, const gbd_problem* p, const gbd_schedule* s, int32_t* order, double* mi) {
+  return guarded(ctx, [&]() {
+    if (!order) return fail(ctx, GBD_ERR_ARG, "order is NULL");
+    int rc = setup(ctx, p, s);
+    if (rc != GBD_OK) return rc;
+    gbd::Engine& e = *ctx->eng;
+    if (s->preconditioner == GBD_PRECOND_LEARNED && !e.mlp_loaded)
+      return fail(ctx, GBD_ERR_STATE, "learned preconditioner requested but no weights are loaded");
+    std::vector<double> se(s->n_sweeps);
+    gbd_result r{};
+    r.sweep_energies = se.data();
+    run_solve(e, p, s, &r);
+    const int n = p->n_orb;
+    std::vector<double> I((size_t)n * n);
+    entropies(e, nullptr, I.data());
+    if (mi) std::copy(I.begin(), I.end(), mi);
+    rc = gbd_host_fiedler_order(n, I.data(), order);
+    if (rc != GBD_OK) return fail(ctx, rc, "Fiedler order of the mutual information failed");
+    return GBD_OK;
+  });
+}
+
 int gbd_mpo_labels(gbd_ctx* ctx, int32_t bond, uint64_t* keys, int32_t cap, int32_t* count) {
   return guarded(ctx, [&]() {
     if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");

@@ -159,6 +159,15 @@ class Engine {
   double sweep(int s);     // returns the Ritz value of the last step
   double final_energy();
   void rdms(double* rdm1, double* rdm2);
+  // spin-summed 3-RDM [n^6] of the current MPS (determinant expansion;
+  // needs 2 n^2 determinant-length vectors on the device)
+  void rdm3(double* out);
+  // one- and two-orbital reduced density matrices of the current MPS:
+  // rho1 [n][4][4], rho2 [n(n-1)/2][16][16] for the pairs (i<j) in
+  // lexicographic order (local basis of orbital i: |0>, |a>, |b>, |ab> =
+  // c+_a^x c+_b^y |vac>; pair basis index 4 x_i + x_j with the modes of i
+  // before those of j)
+  void orbital_rdms(double* rho1, double* rho2);
   // excited states by penalty deflation: the converged lower states stay
   // resident (both site layouts) and enter every two-site step through
   // overlap environments; sigma gains w sum_j phi_j (phi_j . x) and the
@@ -371,6 +380,7 @@ class Engine {
 
  private:
   void init_mps(uint64_t seed, int M);
+  double* expand_ci(int64_t& Na_str, int64_t& Nb_str);
   void build_right_envs(int from_k);
   void build_left_envs(int to_k);
   struct Rec {

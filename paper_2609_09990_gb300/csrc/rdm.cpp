@@ -23,6 +23,12 @@ void launch_scatter_ci(const double* A, int npref, int nsuf, const int* aP, cons
                        double* C, cudaStream_t s);
 void launch_apply_e_chunk(const double* C, int64_t Nb, const int* excA, const int* excB, int n2, int ja0, int cs,
                           double* D, cudaStream_t s);
+void launch_apply_e_vecs(const double* V, int nv, int64_t Na, int64_t Nb, const int* excA, const int* excB, int n2,
+                         int rs, double* out, cudaStream_t s);
+int pair_rdm_blocks(int64_t ndet);
+void launch_pair_rdm(const double* C, int64_t NaS, int64_t NbS, const uint32_t* strA, const uint32_t* strB,
+                     const int* binom, int n, int NaTot, const int* pairs, int npairs, double* partial,
+                     cudaStream_t s);
 
 namespace {
 
@@ -83,9 +89,12 @@ std::vector<int> excitations(int n, int k) {
 
 }  // namespace
 
-void Engine::rdms(double* rdm1, double* rdm2) {
+// The current MPS expanded into the determinant basis: C[Ia * Nb_str + Ib]
+// (device, caller frees), not normalised.
+double* Engine::expand_ci(int64_t& Na_str, int64_t& Nb_str) {
   const int h = n / 2;
-  const int64_t Na_str = (int64_t)binom_i(n, Na), Nb_str = (int64_t)binom_i(n, Nb);
+  Na_str = (int64_t)binom_i(n, Na);
+  Nb_str = (int64_t)binom_i(n, Nb);
   const int64_t ndet = Na_str * Nb_str;
   if (ndet > (int64_t)400000000) throw Error(-1, "RDMs need the determinant expansion; too many determinants");
   // site block X_i(q, s): m_i(q) x m_{i+1}(q+s) with its leading dimension
@@ -267,6 +276,13 @@ void Engine::rdms(double* rdm1, double* rdm2) {
   }
   for (auto& f : pre) if (f.d) dfree(f.d);
   for (auto& f : suf) if (f.d) dfree(f.d);
+  return C;
+}
+
+void Engine::rdms(double* rdm1, double* rdm2) {
+  int64_t Na_str = 0, Nb_str = 0;
+  double* C = expand_ci(Na_str, Nb_str);
+  const int64_t ndet = Na_str * Nb_str;
   // ---- D[pq] = E_pq C in chunks of alpha strings; gamma and <E E> by GEMM
   const int n2 = n * n;
   auto excA = excitations(n, Na), excB = excitations(n, Nb);
@@ -344,6 +360,209 @@ void Engine::rdms(double* rdm1, double* rdm2) {
             if (q == r) v -= g1[p * n + s];
             rdm2[(((size_t)p * n + q) * n + r) * n + s] = v;
           }
+}
+
+// ---------------------------------------------------------------- 3-RDM
+// Gamma3_pqrstu = sum_{s,t,v} <a+_ps a+_rt a+_tv a_uv a_st a_qs> (Sec.
+// "Computational details": one- through three-particle RDMs on the device)
+// from products of excitation operators,
+//   <E_pq E_rs E_tu> = Gamma3_pqrstu + d_qt Gamma_purs + d_st Gamma_pqru
+//                      + d_qr Gamma_pstu + d_qr d_st gamma_pu,
+// and <E_pq E_rs E_tu> = D[qp] . (E_rs D[tu]) with D[tu] = E_tu C: for each
+// rs, the n^2 vectors E_rs D[tu] and one split-K Gram GEMM against D.  FP64.
+void Engine::rdm3(double* out) {
+  int64_t NaS = 0, NbS = 0;
+  double* C = expand_ci(NaS, NbS);
+  const int64_t ndet = NaS * NbS;
+  const int n2 = n * n;
+  if (ndet > (int64_t)0x7fffffff || 2.0 * n2 * (double)ndet * sizeof(double) > 64e9) {
+    dfree(C);
+    throw Error(-1, "3-RDM: the determinant expansion needs 2 n^2 vectors of the determinant length (at most 64 GB)");
+  }
+  auto excA = excitations(n, Na), excB = excitations(n, Nb);
+  int* d_excA = dalloc<int>(excA.size());
+  int* d_excB = dalloc<int>(excB.size());
+  CK(cudaMemcpyAsync(d_excA, excA.data(), excA.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(d_excB, excB.data(), excB.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  double* D = dalloc<double>((size_t)n2 * ndet);
+  double* F = dalloc<double>((size_t)n2 * ndet);
+  launch_apply_e_chunk(C, NbS, d_excA, d_excB, n2, 0, (int)NaS, D, stream);
+  stats.launches++;
+  CK(cudaGetLastError());
+  const int SPLIT = 32;
+  const int parts = (int)std::min<int64_t>(SPLIT, std::max<int64_t>(1, ndet / 4096));
+  const int64_t step = (ndet + parts - 1) / parts;
+  double* Mp = dalloc<double>((size_t)parts * n2 * n2);
+  double* M3 = dalloc<double>((size_t)n2 * n2 * n2);
+  double* M2 = dalloc<double>((size_t)n2 * n2 + n2);
+  // Gram of D against a set of n2 vectors W (D . W^T), split over K and summed
+  // in a fixed order into dst
+  auto gram = [&](const double* W, int ldw_is_vec, double* dst, int ncols) {
+    GemmPlan p;
+    for (int s = 0; s < parts; ++s) {
+      const int64_t k0 = (int64_t)s * step, k1 = std::min<int64_t>(ndet, k0 + step);
+      p.add_out(Mp + (size_t)s * n2 * ncols, ncols, n2, ncols, 0);
+      if (k1 > k0) p.add_term(D + k0, (int)ndet, W + k0, ldw_is_vec ? 1 : (int)ndet, (int)(k1 - k0),
+                              ldw_is_vec ? 0 : 2, 1.0);
+    }
+    upload(p);
+    run(p);
+    release(p);
+    AxpyPlan ax;
+    ax.outs.push_back({dst, (int64_t)n2 * ncols, 0, 0});
+    for (int s = 0; s < parts; ++s) ax.terms.push_back({Mp + (size_t)s * n2 * ncols, 1.0});
+    ax.outs.back().t1 = (int)ax.terms.size();
+    upload(ax);
+    run(ax);
+    release(ax);
+  };
+  gram(D, 0, M2, n2);            // <E_qp C | E_rs C>
+  gram(C, 1, M2 + (size_t)n2 * n2, 1);   // <E_qp C | C>
+  for (int rs = 0; rs < n2; ++rs) {
+    launch_apply_e_vecs(D, n2, NaS, NbS, d_excA, d_excB, n2, rs, F, stream);
+    stats.launches++;
+    CK(cudaGetLastError());
+    gram(F, 0, M3 + (size_t)rs * n2 * n2, n2);
+  }
+  int nblk = reduction_blocks(ndet);
+  double* partial = dalloc<double>(nblk);
+  double* nrm_d = dalloc<double>(1);
+  launch_multi_dot(C, ndet, 1, C, ndet, nrm_d, partial, nblk, stream);
+  stats.launches += 2;
+  std::vector<double> h3((size_t)n2 * n2 * n2), h2((size_t)n2 * n2 + n2);
+  double nrm2 = 0;
+  CK(cudaMemcpyAsync(h3.data(), M3, h3.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(h2.data(), M2, h2.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(&nrm2, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  stats.d2h += (h3.size() + h2.size() + 1) * sizeof(double);
+  for (void* q : {(void*)C, (void*)d_excA, (void*)d_excB, (void*)D, (void*)F, (void*)Mp, (void*)M3, (void*)M2,
+                  (void*)partial, (void*)nrm_d})
+    dfree(q);
+  if (!(nrm2 > 0)) throw Error(-4, "MPS has zero norm in the determinant expansion");
+  // gamma_pq = <E_pq> = <E_qp C | C>; Gamma_pqrs = <E_pq E_rs> - d_qr gamma_ps
+  std::vector<double> g1(n2), g2((size_t)n2 * n2);
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) g1[p * n + q] = h2[(size_t)n2 * n2 + q * n + p] / nrm2;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r)
+        for (int s2 = 0; s2 < n; ++s2) {
+          double v = h2[(size_t)(q * n + p) * n2 + r * n + s2] / nrm2;
+          if (q == r) v -= g1[p * n + s2];
+          g2[(size_t)(p * n + q) * n2 + r * n + s2] = v;
+        }
+  auto G2 = [&](int p, int q, int r, int s2) { return g2[(size_t)(p * n + q) * n2 + r * n + s2]; };
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r)
+        for (int s2 = 0; s2 < n; ++s2)
+          for (int t = 0; t < n; ++t)
+            for (int u = 0; u < n; ++u) {
+              double v = h3[((size_t)(r * n + s2) * n2 + q * n + p) * n2 + t * n + u] / nrm2;
+              if (q == t) v -= G2(p, u, r, s2);
+              if (s2 == t) v -= G2(p, q, r, u);
+              if (q == r) v -= G2(p, s2, t, u);
+              if (q == r && s2 == t) v -= g1[p * n + u];
+              out[((((size_t)(p * n + q) * n + r) * n + s2) * n + t) * n + u] = v;
+            }
+}
+
+// ---------------------------------------------------------------- orbital RDMs
+// One- and two-orbital reduced density matrices (the inputs of the orbital
+// entropies and the mutual information that order the lattice, Sec.
+// "Cholesky decomposition for the wavefunction", ingredient (ii)): rho_ij
+// from the determinant expansion by pair_rdm_kernel (fermionic partial trace
+// with the pair's modes moved to the front), rho_i as its partial trace.
+void Engine::orbital_rdms(double* rho1, double* rho2) {
+  int64_t NaS = 0, NbS = 0;
+  double* C = expand_ci(NaS, NbS);
+  const int64_t ndet = NaS * NbS;
+  const int npairs = n * (n - 1) / 2;
+  auto sa = strings(n, Na), sb = strings(n, Nb);
+  std::vector<int> binom(33 * 33, 0), pairs;
+  for (int o = 0; o <= 32; ++o)
+    for (int k = 0; k <= 32; ++k) binom[o * 33 + k] = k <= o ? (int)binom_i(o, k) : 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) pairs.insert(pairs.end(), {i, j});
+  uint32_t* d_sa = dalloc<uint32_t>(sa.size());
+  uint32_t* d_sb = dalloc<uint32_t>(sb.size());
+  int* d_binom = dalloc<int>(binom.size());
+  int* d_pairs = dalloc<int>(std::max<size_t>(pairs.size(), 1));
+  CK(cudaMemcpyAsync(d_sa, sa.data(), sa.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(d_sb, sb.data(), sb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(d_binom, binom.data(), binom.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  if (!pairs.empty())
+    CK(cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  const int nb = pair_rdm_blocks(ndet);
+  double* partial = dalloc<double>((size_t)std::max(npairs, 1) * nb * 26);
+  if (npairs > 0) {
+    launch_pair_rdm(C, NaS, NbS, d_sa, d_sb, d_binom, n, Na, d_pairs, npairs, partial, stream);
+    stats.launches++;
+    CK(cudaGetLastError());
+  }
+  int nblk = reduction_blocks(ndet);
+  double* red = dalloc<double>(nblk);
+  double* nrm_d = dalloc<double>(1);
+  launch_multi_dot(C, ndet, 1, C, ndet, nrm_d, red, nblk, stream);
+  stats.launches += 2;
+  std::vector<double> hp((size_t)std::max(npairs, 1) * nb * 26);
+  double nrm2 = 0;
+  CK(cudaMemcpyAsync(hp.data(), partial, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(&nrm2, nrm_d, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  for (void* q : {(void*)C, (void*)d_sa, (void*)d_sb, (void*)d_binom, (void*)d_pairs, (void*)partial, (void*)red,
+                  (void*)nrm_d})
+    dfree(q);
+  if (!(nrm2 > 0)) throw Error(-4, "MPS has zero norm in the determinant expansion");
+  // slots -> (local states): sector (na, nb), variants u (alpha on i / on j
+  // when na = 1), v (beta likewise), k = u * nbv + v
+  struct Sec { int na, nb, base; };
+  const Sec secs[9] = {{0, 0, 0}, {0, 2, 1}, {2, 0, 2}, {2, 2, 3}, {1, 0, 4}, {1, 2, 7}, {0, 1, 10}, {2, 1, 13},
+                       {1, 1, 16}};
+  auto local = [](int na, int nb, int u, int v) {
+    int ai, aj, bi, bj;
+    if (na == 1) { ai = u == 0; aj = u == 1; } else { ai = aj = na / 2; }
+    if (nb == 1) { bi = v == 0; bj = v == 1; } else { bi = bj = nb / 2; }
+    return ai + 2 * bi + 4 * (aj + 2 * bj);
+  };
+  std::vector<double> r2((size_t)std::max(npairs, 1) * 256, 0.0);
+  for (int pr = 0; pr < npairs; ++pr) {
+    double slot[26] = {0};
+    for (int b = 0; b < nb; ++b)
+      for (int t = 0; t < 26; ++t) slot[t] += hp[((size_t)pr * nb + b) * 26 + t];
+    double* R = r2.data() + (size_t)pr * 256;
+    for (const Sec& sc : secs) {
+      const int nav = sc.na == 1 ? 2 : 1, nbv = sc.nb == 1 ? 2 : 1, d = nav * nbv;
+      int x[4];
+      for (int u = 0, k = 0; u < nav; ++u)
+        for (int v = 0; v < nbv; ++v, ++k) x[k] = local(sc.na, sc.nb, u, v);
+      int t = sc.base;
+      for (int a = 0; a < d; ++a)
+        for (int b = a; b < d; ++b, ++t) {
+          R[x[a] * 16 + x[b]] = slot[t] / nrm2;
+          R[x[b] * 16 + x[a]] = slot[t] / nrm2;
+        }
+    }
+  }
+  if (rho2) std::memcpy(rho2, r2.data(), (size_t)npairs * 256 * sizeof(double));
+  if (rho1) {
+    // rho_i = tr_j rho_ij for a pair containing i (j > i: trace the high
+    // index; i = n-1: pair (0, n-1), trace the low one)
+    for (int i = 0; i < n; ++i) {
+      double* o = rho1 + (size_t)i * 16;
+      std::fill(o, o + 16, 0.0);
+      if (n < 2) continue;
+      const bool low = i < n - 1;
+      const int a = low ? i : 0, b = low ? n - 1 : i;
+      const int pr = a * n - a * (a + 1) / 2 + (b - a - 1);
+      const double* R = r2.data() + (size_t)pr * 256;
+      for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y)
+          for (int z = 0; z < 4; ++z)
+            o[x * 4 + y] += low ? R[(x + 4 * z) * 16 + (y + 4 * z)] : R[(z + 4 * x) * 16 + (z + 4 * y)];
+    }
+  }
 }
 
 }  // namespace gbd

@@ -118,6 +118,10 @@ def lib():
         "gbd_run_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp,
                                    C.c_int32, _ip]),
         "gbd_rdms": (C.c_int, [vp, _dp, _dp]),
+        "gbd_rdm3": (C.c_int, [vp, _dp]),
+        "gbd_orbital_rdms": (C.c_int, [vp, _dp, _dp]),
+        "gbd_orbital_entropies": (C.c_int, [vp, _dp, _dp]),
+        "gbd_mi_order": (C.c_int, [vp, C.POINTER(gbd_problem), C.POINTER(gbd_schedule), _ip, _dp]),
         "gbd_mpo_labels": (C.c_int, [vp, C.c_int32, C.POINTER(C.c_uint64), C.c_int32, _ip]),
         "gbd_env_block": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, C.c_int64, _ip, _ip]),
         "gbd_get_stats": (C.c_int, [vp, C.POINTER(gbd_stats)]),
@@ -381,6 +385,35 @@ class Context:
         r2 = np.zeros((n, n, n, n))
         self._check(self.L.gbd_rdms(self.ptr, _d(r1), _d(r2)), "gbd_rdms")
         return r1, r2
+
+    def rdm3(self, n):
+        """gbd_rdm3: the spin-summed 3-RDM [n]*6 of the current state."""
+        out = np.zeros((n,) * 6)
+        self._check(self.L.gbd_rdm3(self.ptr, _d(out)), "gbd_rdm3")
+        return out
+
+    def orbital_rdms(self, n):
+        """gbd_orbital_rdms: (rho1 [n,4,4], rho2 [n(n-1)/2,16,16])."""
+        r1 = np.zeros((n, 4, 4))
+        r2 = np.zeros((max(n * (n - 1) // 2, 1), 16, 16))
+        self._check(self.L.gbd_orbital_rdms(self.ptr, _d(r1), _d(r2)), "gbd_orbital_rdms")
+        return r1, r2[:n * (n - 1) // 2]
+
+    def orbital_entropies(self, n):
+        """gbd_orbital_entropies: (s1 [n], mutual information [n,n])."""
+        s1 = np.zeros(n)
+        mi = np.zeros((n, n))
+        self._check(self.L.gbd_orbital_entropies(self.ptr, _d(s1), _d(mi)), "gbd_orbital_entropies")
+        return s1, mi
+
+    def mi_order(self, h, chol, n_elec, two_sz, bond_dims, tols, **kw):
+        """gbd_mi_order: (order, mutual information) from a preliminary solve."""
+        p, s = self._structs(h, chol, n_elec, two_sz, bond_dims, tols, **kw)
+        n = p.n_orb
+        order = np.zeros(n, dtype=np.int32)
+        mi = np.zeros((n, n))
+        self._check(self.L.gbd_mi_order(self.ptr, C.byref(p), C.byref(s), _i(order), _d(mi)), "gbd_mi_order")
+        return order, mi
 
     def mpo_labels(self, bond):
         cnt = C.c_int32()

@@ -75,3 +75,23 @@ def test_mutual_information_of_a_ground_state():
     I = entropy.mutual_information(full, 4)
     assert np.allclose(I, I.T) and I.min() > -1e-12 and np.all(np.diag(I) == 0)
     assert I.max() > 1e-3                       # a correlated state
+
+
+@pytest.mark.parametrize("n,na,nb", [(4, 2, 2), (4, 3, 1), (5, 2, 3)])
+def test_ci_to_fock_reproduces_the_fock_ground_state(n, na, nb):
+    # the determinant-basis ground state (fci.py, alpha-first creator order)
+    # rewritten in the site-major Fock basis is the Fock-space ground state
+    # (brute-force eigh of the Jordan-Wigner H) up to a global sign; a wrong
+    # reordering sign breaks the equality
+    from oracle import fci
+    h, chol = make_integrals(n, 4, 31 + n + na)
+    eri = fock.eri_from_chol(chol)
+    w, v, st = fock.ground_state(h, eri, na, nb)
+    f = fci.FCI(h, eri, na, nb)
+    e, x = fci.davidson(lambda c: f.sigma(c).ravel(), f.diagonal().ravel(), tol=1e-12)
+    assert abs(e[0] - w[0]) < 1e-10
+    full = fock.from_ci(x[:, 0] / np.linalg.norm(x[:, 0]), n, na, nb)
+    ref = np.zeros_like(full)
+    ref[st] = v[:, 0]
+    assert np.abs(abs(full @ ref) - 1.0) < 1e-10
+    assert min(np.abs(full - ref).max(), np.abs(full + ref).max()) < 1e-6
