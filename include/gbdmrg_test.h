@@ -96,6 +96,15 @@ int gbd_set_preconditioner(gbd_ctx *ctx, int32_t preconditioner);
  * 3 = TF32x3 (default), 4 = BF16x3 (the codes of gbd_apply_heff_prec). */
 int gbd_set_accurate_tier(gbd_ctx *ctx, int32_t prec);
 
+/* Stopping rule of the accurate (TF32x3 / BF16x3) Davidson tier: a plateau
+ * (||r|| not cut by 30 % over 3 iterations) ends it once ||r|| is below
+ * floor_mult x u x max(1, |theta|), u being the tier's measured relative
+ * sigma error (default floor_mult 1); hard_stag > 0 also ends a
+ * reduced-precision tier after hard_stag iterations without a 30 % cut at
+ * any level (default 8; 0: off).  GBD_ERR_ARG for floor_mult <= 0 or
+ * hard_stag < 0. */
+int gbd_set_tier_stop(gbd_ctx *ctx, double floor_mult, int32_t hard_stag);
+
 /* Reduced-precision schedules solve steps whose two-site state has fewer
  * than n elements (chain ends) in FP64: there the tensor-core plan costs
  * more than it saves.  Default 4096; 0 = always the tensor-core tiers. */
@@ -227,6 +236,15 @@ int gbd_correction_selftest(int32_t device, int32_t kind, int64_t n, const doubl
  * GBD_ERR_ARG for NULL pointers; GBD_ERR_STATE without valid environments. */
 int gbd_pcg_selftest(gbd_ctx *ctx, int32_t k, const double *x, const double *r, double theta, double *t,
                      int64_t *matvecs);
+/* Dense throughput of the tensor-core grouped GEMM (the roof the sigma's
+ * tensor view is compared with): one M x N x K product in precision prec
+ * (0 BF16, 1 TF32, 2 TF32x3, 3 BF16x3) on 128 x 256 tiles, timed with CUDA
+ * events over `reps` launches after one warm-up.  tflops = 2 M N K per
+ * launch / time; ms_per_launch the average launch.  M a multiple of 128, N
+ * of 256, K of 64.  Device memory: (M + N) K x 2 (split types) element
+ * panels plus M N doubles. */
+int gbd_tc_rate(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t reps, double *tflops,
+                double *ms_per_launch);
 /* Failure detection without a fault: one bounded mbarrier wait (the helper
  * every role of the tensor-core kernel uses).  arrive = 0: nothing completes
  * the barrier, the wait runs out after its poll limit (2^22 polls, a few

@@ -412,6 +412,17 @@ int gbd_set_accurate_tier(gbd_ctx* ctx, int32_t prec) {
   });
 }
 
+int gbd_set_tier_stop(gbd_ctx* ctx, double floor_mult, int32_t hard_stag) {
+  return guarded(ctx, [&]() {
+    if (!(floor_mult > 0) || !std::isfinite(floor_mult) || hard_stag < 0)
+      return fail(ctx, GBD_ERR_ARG, "floor_mult must be positive and hard_stag >= 0");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tier2_floor_mult = floor_mult;
+    ctx->eng->hard_stag_iters = hard_stag;
+    return GBD_OK;
+  });
+}
+
 int gbd_set_tc_min_two_site(gbd_ctx* ctx, int64_t n) {
   return guarded(ctx, [&]() {
     if (n < 0) return fail(ctx, GBD_ERR_ARG, "n < 0");

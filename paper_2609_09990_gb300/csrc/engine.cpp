@@ -1350,6 +1350,10 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     rhist.push_back(rn);
     const double floor_here = stag_rel * std::max(1.0, std::fabs(theta));
     if (stag_rel > 0 && rhist.size() > 3 && rn > 0.7 * rhist[rhist.size() - 4] && rn < floor_here) break;
+    // a reduced-precision tier that has not cut ||r|| by 30 % over
+    // hard_stag_iters iterations stops at any level
+    const size_t hs = (size_t)hard_stag_iters;
+    if (stag_rel > 0 && hs > 0 && rhist.size() > hs && rn > 0.7 * rhist[rhist.size() - 1 - hs]) break;
     stats.davidson_iters++;
     if (recording) record_iteration(r, diag, x, scalars(theta, rn, it));
     if (learned && !fallback) {
@@ -1617,7 +1621,7 @@ double Engine::solve_tiers(Sigma& sg, const double* diag, double tol, int precis
     if (stats.last_residual >= tol) {
       P = tc_plan(sg.lenl, sg.renl, tier2);
       theta = davidson([&](const double* x, double* y) { tc_apply(P, x, y); }, diag, tol, sched.max_iter,
-                       sched.max_space, 10.0 * u2);
+                       sched.max_space, tier2_floor_mult * u2);
       tc_free(P);
       tier_done(1);
     }
@@ -1713,13 +1717,19 @@ void Engine::pcg_selftest(int k, const double* x_host, const double* r_host, dou
   const int nblk = reduction_blocks(N);
   double* partial = dalloc<double>((size_t)2 * nblk);
   double* dsums = dalloc<double>(4);
-  CK(cudaMemcpyAsync(x, x_host, N * sizeof(double), cudaMemcpyHostToDevice, stream));
-  CK(cudaMemcpyAsync(r, r_host, N * sizeof(double), cudaMemcpyHostToDevice, stream));
+  // host vectors in the canonical two-site format <-> the fused layout
+  const std::vector<CanonMap> maps = canonical_maps(k);
+  std::vector<double> hx(N), hr(N), ht(N);
+  to_fused(maps, x_host, hx.data());
+  to_fused(maps, r_host, hr.data());
+  CK(cudaMemcpyAsync(x, hx.data(), N * sizeof(double), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(r, hr.data(), N * sizeof(double), cudaMemcpyHostToDevice, stream));
   const int64_t m0 = stats.inner_matvecs;
   inner_pcg([&](const double* a, double* b) { sigma(sg, a, b); }, diag, x, r, theta, t, cg, partial, nblk, dsums);
-  CK(cudaMemcpyAsync(t_host, t, N * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(ht.data(), t, N * sizeof(double), cudaMemcpyDeviceToHost, stream));
   sync();
   settle();
+  from_fused(maps, ht.data(), t_host);
   *matvecs = stats.inner_matvecs - m0;
   for (void* q : {(void*)x, (void*)r, (void*)t, (void*)cg, (void*)partial, (void*)dsums, (void*)diag}) dfree(q);
   free_sigma(sg, true);
@@ -2115,12 +2125,12 @@ int64_t Engine::two_site_size(int k) {
 
 // psi in the canonical two-site order: for q_l in bond k (sorted), s1, s2 with
 // q_r = q_l + s1 + s2 in bond k+2: a m_k(q_l) x m_{k+2}(q_r) block
-void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, int prec) {
-  setup_two_site(k);
+// blocks of the canonical two-site vector format (q_l, s1, s2 with q_r =
+// q_l + s1 + s2) in the engine's fused layout of the current step
+std::vector<Engine::CanonMap> Engine::canonical_maps(int k) const {
   const Bond& bk = bonds[k];
   const Bond& bk2 = bonds[k + 2];
-  struct Map { int64_t src, dst; int rows, cols, ld; };
-  std::vector<Map> maps;
+  std::vector<CanonMap> maps;
   int64_t pos = 0;
   for (int j = 0; j < bk.nsec(); ++j)
     for (int s1 = 0; s1 < 4; ++s1)
@@ -2133,10 +2143,27 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, 
         maps.push_back({pos, psi_off[q] + (int64_t)EL.soff[q][s1] * ld + ER.soff[q][s2], ml, mr, ld});
         pos += (int64_t)ml * mr;
       }
-  std::vector<double> hp(psi_size, 0.0);
+  return maps;
+}
+
+void Engine::to_fused(const std::vector<CanonMap>& maps, const double* in, double* out) const {
+  std::fill(out, out + psi_size, 0.0);
   for (auto& m : maps)
     for (int a = 0; a < m.rows; ++a)
-      for (int c = 0; c < m.cols; ++c) hp[m.dst + (int64_t)a * m.ld + c] = in[m.src + (int64_t)a * m.cols + c];
+      for (int c = 0; c < m.cols; ++c) out[m.dst + (int64_t)a * m.ld + c] = in[m.src + (int64_t)a * m.cols + c];
+}
+
+void Engine::from_fused(const std::vector<CanonMap>& maps, const double* in, double* out) const {
+  for (auto& m : maps)
+    for (int a = 0; a < m.rows; ++a)
+      for (int c = 0; c < m.cols; ++c) out[m.src + (int64_t)a * m.cols + c] = in[m.dst + (int64_t)a * m.ld + c];
+}
+
+void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, int prec) {
+  setup_two_site(k);
+  const std::vector<CanonMap> maps = canonical_maps(k);
+  std::vector<double> hp(psi_size, 0.0);
+  to_fused(maps, in, hp.data());
   CK(cudaMemcpyAsync(psi, hp.data(), psi_size * sizeof(double), cudaMemcpyHostToDevice, stream));
   Sigma sg;
   AxpyPlan ax;
@@ -2157,16 +2184,12 @@ void Engine::apply_heff(int k, const double* in, double* out, double* diag_out, 
   CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
   sync();
   settle();   // the stats include this build when the call returns
-  for (auto& m : maps)
-    for (int a = 0; a < m.rows; ++a)
-      for (int c = 0; c < m.cols; ++c) out[m.src + (int64_t)a * m.cols + c] = hy[m.dst + (int64_t)a * m.ld + c];
+  from_fused(maps, hy.data(), out);
   if (diag_out) {
     compute_diag(sg.lenl, sg.renl, y);
     CK(cudaMemcpyAsync(hy.data(), y, psi_size * sizeof(double), cudaMemcpyDeviceToHost, stream));
     sync();
-    for (auto& m : maps)
-      for (int a = 0; a < m.rows; ++a)
-        for (int c = 0; c < m.cols; ++c) diag_out[m.src + (int64_t)a * m.cols + c] = hy[m.dst + (int64_t)a * m.ld + c];
+    from_fused(maps, hy.data(), diag_out);
   }
   if (prec == 0) {
     release(sg.A);

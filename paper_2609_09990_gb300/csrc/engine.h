@@ -220,6 +220,12 @@ class Engine {
   double pcg_rel_tol = 0.1;   // ... stopping when |residual| < pcg_rel_tol |r|
   int tc_order = 0;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
+  // stopping of the accurate tier: a plateau (no 30 % drop over 3
+  // iterations) ends it below tier2_floor_mult * u2 * max(1, |theta|);
+  // hard_stag_iters > 0: no 30 % drop over that many iterations ends it at
+  // any level
+  double tier2_floor_mult = 1.0;
+  int hard_stag_iters = 8;
   int64_t tc_min_two_site = 4096;   // smaller two-site states: reduced-precision schedules use FP64
   // tier-1 (BF16/TF32) Davidson iterations and steps of the current and the
   // previous sweep: a warm sweep whose predecessor averaged < 2 tier-1
@@ -332,6 +338,10 @@ class Engine {
   // most `refine` FP64 iterations; the Ritz vector is left in psi
   double solve_tiers(Sigma& sg, const double* diag, double tol, int precision, int refine, bool& planned);
   void free_sigma(Sigma& sg, bool planned);
+  struct CanonMap { int64_t src, dst; int rows, cols, ld; };
+  std::vector<CanonMap> canonical_maps(int k) const;
+  void to_fused(const std::vector<CanonMap>& maps, const double* in, double* out) const;
+  void from_fused(const std::vector<CanonMap>& maps, const double* in, double* out) const;
   void inner_pcg(const std::function<void(const double*, double*)>& op, const double* diag, const double* xr,
                  const double* rr_vec, double th, double* tout, double* cg, double* partial, int nblk, double* dsums);
   TcPlan* tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune tune = TcTune());

@@ -192,6 +192,123 @@ out:
   return rc;
 }
 
+// Dense throughput of tc_gemm_kernel: one M x N x K product (operands made
+// of a constant byte pattern: the values do not matter for timing), 128 x 256
+// tiles, launched `reps` times after one warm-up; CUDA events around the
+// timed launches.  flops = 2 M N K per launch (TF32x3 / BF16x3 execute three
+// MMAs per product and are reported by the same algorithmic count).
+extern "C" int gbd_tc_rate(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t reps,
+                           double* tflops, double* ms_per_launch) {
+  using namespace gbd;
+  if (prec < 0 || prec > 3 || M < 128 || N < 256 || K < 64 || reps < 1 || !tflops || !ms_per_launch ||
+      M % 128 || N % 256 || K % 64)
+    return GBD_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return GBD_ERR_CUDA;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const bool bfp = prec == kBF16 || prec == kBF16x3, split = prec == kTF32x3 || prec == kBF16x3;
+  const int eb = bfp ? 2 : 4;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  void *pa[2] = {nullptr, nullptr}, *pb[2] = {nullptr, nullptr};
+  int* derr = nullptr;
+  TcConv* dconv = nullptr;
+  TcTile* dtiles = nullptr;
+  TcTerm* dterms = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = GBD_OK;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == GBD_OK) rc = e == cudaErrorMemoryAllocation ? GBD_ERR_OOM : GBD_ERR_CUDA;
+  };
+  // FP64 sources of 128 rows x K, converted repeatedly into the panels
+  ck(cudaMalloc(&dA, (size_t)128 * K * 8));
+  ck(cudaMalloc(&dC, (size_t)M * N * 8));
+  for (int h = 0; h < (split ? 2 : 1); ++h) {
+    ck(cudaMalloc(&pa[h], (size_t)M * K * eb));
+    ck(cudaMalloc(&pb[h], (size_t)N * K * eb));
+  }
+  ck(cudaMalloc(&derr, sizeof(int)));
+  ck(cudaMemset(derr, 0, sizeof(int)));
+  ck(cudaEventCreate(&e0));
+  ck(cudaEventCreate(&e1));
+  if (rc != GBD_OK) goto out;
+  {
+    ck(cudaMemset(dA, 0x3F, (size_t)128 * K * 8));   // every double 0x3F3F... (about 4.8e-4)
+    std::vector<TcConv> ca, cb;
+    for (int r = 0; r < M; r += 128) ca.push_back({dA, 1.0, 128, K, K, r, 0, 0});
+    for (int r = 0; r < N; r += 128) cb.push_back({dA, 1.0, 128, K, K, r, 0, 0});
+    ck(cudaMalloc(&dconv, std::max(ca.size(), cb.size()) * sizeof(TcConv)));
+    ck(cudaMemcpy(dconv, ca.data(), ca.size() * sizeof(TcConv), cudaMemcpyHostToDevice));
+    launch_tc_convert(dconv, (int)ca.size(), prec, pa[0], pa[1], K, 0);
+    ck(cudaDeviceSynchronize());
+    ck(cudaMemcpy(dconv, cb.data(), cb.size() * sizeof(TcConv), cudaMemcpyHostToDevice));
+    launch_tc_convert(dconv, (int)cb.size(), prec, pb[0], pb[1], K, 0);
+    ck(cudaDeviceSynchronize());
+    std::vector<TcTile> tiles;
+    std::vector<TcTerm> terms;
+    for (int m0 = 0; m0 < M; m0 += 128)
+      for (int n0 = 0; n0 < N; n0 += 256) {
+        TcTile T{};
+        T.t0 = (int)terms.size();
+        terms.push_back({0, 0, n0, K, 0, 0, 0, 0});
+        T.t1 = (int)terms.size();
+        T.m0 = m0;
+        T.m_valid = 128;
+        T.n_mma = 256;
+        T.n_valid = 256;
+        T.bsel = 4;
+        T.mode = kTcSigma;
+        T.beta = 0;
+        T.ld = M;
+        T.out = (int64_t)n0 * M;
+        tiles.push_back(T);
+      }
+    ck(cudaMalloc(&dtiles, tiles.size() * sizeof(TcTile)));
+    ck(cudaMalloc(&dterms, terms.size() * sizeof(TcTerm)));
+    ck(cudaMemcpy(dtiles, tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice));
+    ck(cudaMemcpy(dterms, terms.data(), terms.size() * sizeof(TcTerm), cudaMemcpyHostToDevice));
+    TcMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    for (int h = 0; h < (split ? 2 : 1); ++h) {
+      if (!tc_encode_panel(&maps.a[h], eb, pa[h], K, M, 128)) rc = GBD_ERR_CUDA;
+      for (int s = 0; s < 5; ++s)
+        if (!tc_encode_panel(&maps.b[h][s], eb, pb[h], K, N, 16u << s)) rc = GBD_ERR_CUDA;
+    }
+    if (rc != GBD_OK) goto out;
+    TcLaunch L{dtiles, dterms, (int)tiles.size(), prec, nullptr, nullptr, dC, derr, nullptr, nullptr, nullptr, 256,
+               tc_stages(prec, 256)};
+    if (!launch_tc_gemm(maps, L, sms, 0)) rc = GBD_ERR_CUDA;   // warm-up
+    ck(cudaEventRecord(e0, 0));
+    for (int r = 0; r < reps && rc == GBD_OK; ++r)
+      if (!launch_tc_gemm(maps, L, sms, 0)) rc = GBD_ERR_CUDA;
+    ck(cudaEventRecord(e1, 0));
+    ck(cudaGetLastError());
+    ck(cudaDeviceSynchronize());
+    int herr = 0;
+    ck(cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (rc != GBD_OK) goto out;
+    if (herr) { rc = GBD_ERR_TIMEOUT; goto out; }
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_per_launch = ms / reps;
+    *tflops = 2.0 * M * (double)N * K / (*ms_per_launch * 1e-3) / 1e12;
+  }
+out:
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dC);
+  for (int h = 0; h < 2; ++h) {
+    cudaFree(pa[h]);
+    cudaFree(pb[h]);
+  }
+  cudaFree(derr);
+  cudaFree(dconv);
+  cudaFree(dtiles);
+  cudaFree(dterms);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
+
 // Failure detection of the tensor-core kernels without a fault: a bounded
 // mbarrier wait on a barrier that is never completed returns with the
 // error flag raised; the same wait with an arrival succeeds.

@@ -98,6 +98,7 @@ def lib():
         "gbd_set_graphs": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_min_two_site": (C.c_int, [vp, C.c_int64]),
         "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_tier_stop": (C.c_int, [vp, C.c_double, C.c_int32]),
         "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_order": (C.c_int, [vp, C.c_int32]),
@@ -133,6 +134,7 @@ def lib():
                                                _dp]),
         "gbd_tc_selftest": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
                                       _dp, _dp]),
+        "gbd_tc_rate": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, _dp]),
         "gbd_multi_dot": (C.c_int, [vp, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, _dp]),
         "gbd_multi_dot_noalloc": (C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                             C.c_void_p, C.c_void_p]),
@@ -355,6 +357,9 @@ class Context:
 
     def set_preconditioner(self, preconditioner):
         self._check(self.L.gbd_set_preconditioner(self.ptr, preconditioner), "gbd_set_preconditioner")
+
+    def set_tier_stop(self, floor_mult, hard_stag=0):
+        self._check(self.L.gbd_set_tier_stop(self.ptr, float(floor_mult), int(hard_stag)), "gbd_set_tier_stop")
 
     def set_accurate_tier(self, prec):
         """3 = TF32x3 (default), 4 = BF16x3."""
@@ -637,6 +642,15 @@ def correction_selftest(kind, x, sx, diag, theta, device=0):
     if rc != GBD_OK:
         raise GbdError(f"gbd_correction_selftest: {ERRORS.get(rc, rc)}")
     return r, t, rr.value
+
+
+def tc_rate(prec, M, N, K, reps=10, device=0):
+    """(TFLOP/s, ms per launch) of one dense M x N x K tensor-core product."""
+    t, m = C.c_double(), C.c_double()
+    rc = lib().gbd_tc_rate(device, prec, M, N, K, reps, C.byref(t), C.byref(m))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_tc_rate: {ERRORS.get(rc, rc)}")
+    return t.value, m.value
 
 
 def wait_selftest(arrive, device=0):
