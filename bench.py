@@ -366,7 +366,7 @@ def run_batched(args, rank, world):
                 load_imbalance=float(load.max() / load.mean()) if load.size else 1.0)
 
 
-def sigma_probe(prec, orders=(0,), warm_sweeps=0):
+def sigma_probe(prec, orders=(0,), warm_sweeps=0, davidson=False):
     """Profiling driver for the tensor-core sigma: CAS(16,16) M=512, initial
     state (or, with warm_sweeps > 0, the state after that many sweeps in the
     mixed tiers), steps up to the central bond (7,8), then three sigma builds
@@ -378,7 +378,10 @@ def sigma_probe(prec, orders=(0,), warm_sweeps=0):
     CUDA profiler is started right before the timed builds, so
     `ncu --profile-from-start off -k regex:tc_gemm_kernel -c 2` captures the
     first of them.  With several stage-B tile orders, each is timed on three
-    more builds."""
+    more builds.  davidson=True: instead of the sigma builds, one Davidson
+    solve of the central problem in the mixed tiers (gbd_probe_step), for
+    profiling the vector kernels at the size where the sweep spends its
+    time."""
     from paper_2609_09990_gb300 import gbdmrg as G
     import torch
     wl = WORKLOADS["cas16_m512"]
@@ -398,6 +401,20 @@ def sigma_probe(prec, orders=(0,), warm_sweeps=0):
         ctx.apply_heff_prec(k, x, prec)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
+    if davidson:
+        # one Davidson solve of the central two-site problem in the mixed
+        # tiers (plan build, tensor-core sigma builds, vector kernels)
+        s0 = ctx.stats()
+        t = time.perf_counter()
+        theta, e64, r64 = ctx.probe_step(k, PREC["bf16"], 0, 1e-6)
+        s1 = ctx.stats()
+        print(json.dumps({"davidson_probe": True, "warm_sweeps": warm_sweeps, "bond": k, "psi_len": int(x.size),
+                          "seconds": time.perf_counter() - t, "iterations": s1["davidson_iterations"] -
+                          s0["davidson_iterations"], "sigma_builds": s1["n_sigma"] - s0["n_sigma"],
+                          "final_residual_fp64": r64, "kernel_launches": s1["kernel_launches"] -
+                          s0["kernel_launches"]}))
+        ctx.close()
+        return
     ref = None
     for order in orders:
         ctx.set_tc_order(order)
@@ -554,10 +571,13 @@ def main():
     ap.add_argument("--penalty", type=float, default=2.0, help="deflation penalty (Ha) of --states")
     ap.add_argument("--probe-warm-sweeps", type=int, default=0, help="--sigma-probe on the state after this many "
                     "mixed-precision sweeps (profiler started before the timed builds)")
+    ap.add_argument("--probe-davidson", action="store_true", help="--sigma-probe: one mixed-precision Davidson "
+                    "solve at the central bond instead of the sigma builds")
     ap.add_argument("--probe-orders", default="0", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2")
     args = ap.parse_args()
     if args.sigma_probe:
-        sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")), args.probe_warm_sweeps)
+        sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")), args.probe_warm_sweeps,
+                    args.probe_davidson)
         return
     if args.states:
         states_run(args)

@@ -316,6 +316,8 @@ Engine::Engine(int dev) : device(dev) {
   CK(cudaEventCreate(&evgm));
   CK(cudaMallocHost(&tc_err_host, sizeof(int)));
   *tc_err_host = 0;
+  pin_cap = (size_t)16 << 20;
+  CK(cudaMallocHost(&pin_ring, pin_cap));
   cudaMemPool_t pool;
   CK(cudaDeviceGetDefaultMemPool(&pool, device));
   uint64_t thr = UINT64_MAX;
@@ -332,6 +334,14 @@ Engine::~Engine() {
   clear_states();
   if (psi) dfree(psi);
   cudaStreamSynchronize(stream);
+  for (auto& u : pin_inflight) cudaEventDestroy(u.ev);
+  for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  for (auto& t : env_timers) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (cudaEvent_t e : timer_pool) cudaEventDestroy(e);
+  if (pin_ring) cudaFreeHost(pin_ring);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
   if (evg0) cudaEventDestroy(evg0);
@@ -386,7 +396,58 @@ void Engine::check(const AxpyPlan& p) const {
   }
 }
 
-void Engine::sync() { CK(cudaStreamSynchronize(stream)); }
+void Engine::sync() {
+  CK(cudaStreamSynchronize(stream));
+  drain_timers();
+}
+
+void Engine::drain_timers() {
+  for (auto& t : env_timers) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, t.a, t.b));
+    stats.env_ms += ms;
+    timer_pool.push_back(t.a);
+    timer_pool.push_back(t.b);
+  }
+  env_timers.clear();
+}
+
+cudaEvent_t Engine::pool_event() {
+  if (!ev_pool.empty()) {
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return e;
+}
+
+void Engine::h2d(void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  if (!pin_ring || bytes > pin_cap / 4) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream));
+    return;
+  }
+  const uint64_t n = (bytes + 255) & ~(uint64_t)255;
+  uint64_t start = pin_pos;
+  const uint64_t off = start % pin_cap;
+  if (off + n > pin_cap) start += pin_cap - off;   // wrap: the region starts at ring offset 0
+  // the ring bytes of [start, start + n) last held positions
+  // [start - cap, start + n - cap): wait for the copies that read them
+  while (!pin_inflight.empty() && pin_inflight.front().start + pin_cap < start + n) {
+    CK(cudaEventSynchronize(pin_inflight.front().ev));
+    ev_pool.push_back(pin_inflight.front().ev);
+    pin_inflight.pop_front();
+  }
+  uint8_t* slot = pin_ring + (start % pin_cap);
+  std::memcpy(slot, src, bytes);
+  CK(cudaMemcpyAsync(dst, slot, bytes, cudaMemcpyHostToDevice, stream));
+  cudaEvent_t e = pool_event();
+  CK(cudaEventRecord(e, stream));
+  pin_inflight.push_back({start, start + n, e});
+  pin_pos = start + n;
+}
 
 void Engine::upload(GemmPlan& p) {
   check(p);
@@ -427,15 +488,10 @@ void Engine::upload(GemmPlan& p) {
   });
   p.d_tiles = dalloc<GemmTile>(std::max<size_t>(p.tiles.size(), 1));
   p.d_flat = dalloc<GemmTile>(std::max<size_t>(p.flat.size(), 1));
-  if (!p.flat.empty())
-    CK(cudaMemcpyAsync(p.d_flat, p.flat.data(), p.flat.size() * sizeof(GemmTile), cudaMemcpyHostToDevice, stream));
-  if (!p.terms.empty())
-    CK(cudaMemcpyAsync(p.d_terms, p.terms.data(), p.terms.size() * sizeof(GemmTerm), cudaMemcpyHostToDevice, stream));
-  if (!p.outs.empty())
-    CK(cudaMemcpyAsync(p.d_outs, p.outs.data(), p.outs.size() * sizeof(GemmOut), cudaMemcpyHostToDevice, stream));
-  if (!p.tiles.empty())
-    CK(cudaMemcpyAsync(p.d_tiles, p.tiles.data(), p.tiles.size() * sizeof(GemmTile), cudaMemcpyHostToDevice, stream));
-  sync();   // host vectors may be reused after return
+  h2d(p.d_flat, p.flat.data(), p.flat.size() * sizeof(GemmTile));
+  h2d(p.d_terms, p.terms.data(), p.terms.size() * sizeof(GemmTerm));
+  h2d(p.d_outs, p.outs.data(), p.outs.size() * sizeof(GemmOut));
+  h2d(p.d_tiles, p.tiles.data(), p.tiles.size() * sizeof(GemmTile));
 }
 
 void Engine::release(GemmPlan& p) {
@@ -453,11 +509,8 @@ void Engine::upload(AxpyPlan& p) {
   check(p);
   p.d_terms = dalloc<AxpyTerm>(p.terms.size());
   p.d_outs = dalloc<AxpyOut>(p.outs.size());
-  if (!p.terms.empty())
-    CK(cudaMemcpyAsync(p.d_terms, p.terms.data(), p.terms.size() * sizeof(AxpyTerm), cudaMemcpyHostToDevice, stream));
-  if (!p.outs.empty())
-    CK(cudaMemcpyAsync(p.d_outs, p.outs.data(), p.outs.size() * sizeof(AxpyOut), cudaMemcpyHostToDevice, stream));
-  sync();
+  h2d(p.d_terms, p.terms.data(), p.terms.size() * sizeof(AxpyTerm));
+  h2d(p.d_outs, p.outs.data(), p.outs.size() * sizeof(AxpyOut));
 }
 
 void Engine::release(AxpyPlan& p) {
@@ -872,19 +925,31 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
   const double th0 = now_ms();
   upload(p1);
   upload(p2);
-  CK(cudaEventRecord(ev0, stream));
-  run(p1);
-  run(p2);
-  CK(cudaEventRecord(ev1, stream));
-  sync();
-  float ms = 0;
-  CK(cudaEventElapsedTime(&ms, ev0, ev1));
-  stats.env_ms += ms;
+  timed_env_launch(p1, p2);
   stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
   release(p1);
   release(p2);
   dfree(T);
+}
+
+// the two GEMM launches of an environment update between a pair of timing
+// events; their time is read after the next stream synchronisation
+void Engine::timed_env_launch(GemmPlan& p1, GemmPlan& p2) {
+  EnvTimer t;
+  for (cudaEvent_t* e : {&t.a, &t.b}) {
+    if (!timer_pool.empty()) {
+      *e = timer_pool.back();
+      timer_pool.pop_back();
+    } else {
+      CK(cudaEventCreate(e));
+    }
+  }
+  CK(cudaEventRecord(t.a, stream));
+  run(p1);
+  run(p2);
+  CK(cudaEventRecord(t.b, stream));
+  env_timers.push_back(t);
 }
 
 // R_{k+1}[b](Qout <- Qin) = B_Qout (Renl[b] B_Qin^T); B fused-right.
@@ -929,14 +994,7 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
   const double th0 = now_ms();
   upload(p1);
   upload(p2);
-  CK(cudaEventRecord(ev0, stream));
-  run(p1);
-  run(p2);
-  CK(cudaEventRecord(ev1, stream));
-  sync();
-  float ms = 0;
-  CK(cudaEventElapsedTime(&ms, ev0, ev1));
-  stats.env_ms += ms;
+  timed_env_launch(p1, p2);
   stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
   release(p1);
@@ -1142,7 +1200,7 @@ void Engine::compute_diag(const EnlOp& lenl, const EnlOp& renl, double* diag) {
   GemmPlan g;
   static const double one = 1.0;
   double* d_one = dalloc<double>(1);
-  CK(cudaMemcpyAsync(d_one, &one, sizeof(double), cudaMemcpyHostToDevice, stream));
+  h2d(d_one, &one, sizeof(double));
   for (const auto& s : lenl.subs) {
     if (s.qin != s.qout || s.sin != s.sout || col[s.b] < 0 || s.rows != s.cols) continue;
     // column vector of the diagonal: rows r -> DL(q)[soff + r, col]
@@ -1266,7 +1324,7 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
     stats.d2h += cnt * sizeof(double);
   };
   auto h2d = [&](double* dev, const double* host, int cnt) {
-    CK(cudaMemcpyAsync(dev, host, cnt * sizeof(double), cudaMemcpyHostToDevice, stream));
+    this->h2d(dev, host, cnt * sizeof(double));
     stats.h2d += cnt * sizeof(double);
   };
   auto dots = [&](const double* base, int k, const double* vec, double* out_dev) {
@@ -1423,8 +1481,10 @@ double Engine::davidson(const std::function<void(const double*, double*)>& op, c
   dots(x, 1, x, drow + max_space + 1);
   launch_normalize(x, drow + max_space + 1, n, psi, stream);
   stats.launches++;
-  sync();
-  if (recording) record_converged(psi);
+  if (recording) {
+    sync();
+    record_converged(psi);
+  }
   if (dbad) dfree(dbad);
   for (void* p : {(void*)V, (void*)S, (void*)Vt, (void*)St, (void*)x, (void*)sx, (void*)r, (void*)t, (void*)partial,
                   (void*)dres, (void*)dorth, (void*)drow, (void*)coef})
@@ -1549,7 +1609,7 @@ void Engine::truncate(int k, int dir, int M, double* tau_out, std::vector<double
       }
   }
   U.d = dalloc<double>(U.size);
-  CK(cudaMemcpyAsync(U.d, hU.data(), U.size * sizeof(double), cudaMemcpyHostToDevice, stream));
+  h2d(U.d, hU.data(), U.size * sizeof(double));
   stats.h2d += U.size * sizeof(double);
   sites[which] = U;
   // center = U^T psi (L->R, site k+1 fused-right) or psi B^T (R->L, site k fused-left)
@@ -1574,7 +1634,6 @@ void Engine::truncate(int k, int dir, int M, double* tau_out, std::vector<double
   run(pc);
   release(pc);
   sites[cw] = C;
-  sync();
 }
 
 // ------------------------------------------------------------------ one step
@@ -1752,7 +1811,6 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
   build_renl(k + 1, Renv[k + 2], ER, sg.renl, ax);
   th += now_ms() - t1;
   finish_enl(sg.renl, ax);
-  sync();
   stats.enl_ms += now_ms() - te;
   stats.enl_host_ms += th;
   double tdg = now_ms();
@@ -1792,7 +1850,7 @@ double Engine::step(int k, int dir, int M, double tol, double* tau, std::vector<
   }
   free_enl(sg.lenl);
   free_enl(sg.renl);
-  sync();
+  // no synchronisation: the next step's host planning overlaps these launches
   stats.n_steps++;
   stats.step_ms += now_ms() - t0;
   return theta;
@@ -2004,6 +2062,7 @@ double Engine::sweep(int s) {
   stats.sweep_max_residual = 0;
   for (int k = 0; k <= n - 2; ++k) e = step(k, 0, M, tol, nullptr, nullptr);
   for (int k = n - 2; k >= 0; --k) e = step(k, 1, M, tol, nullptr, nullptr);
+  sync();   // every launch of the sweep done and timed
   sweep_E.push_back(e);
   return e;
 }
@@ -2216,7 +2275,9 @@ void Engine::multi_dot(const double* V, int64_t stride, int k, const double* x, 
 }
 
 double Engine::run_step(int k, int dir, int M, double tol, double* tau, std::vector<double>* kept) {
-  return step(k, dir, M, tol, tau, kept);
+  const double e = step(k, dir, M, tol, tau, kept);
+  sync();
+  return e;
 }
 
 void Engine::env_block(int side, int bond, int ch, int sec, std::vector<double>& out, int& rows, int& cols) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <array>
+#include <deque>
 #include <functional>
 #include <map>
 #include <memory>
@@ -309,6 +310,27 @@ class Engine {
   void run(AxpyPlan& p);
   void sync();
   void settle();
+  // Host-to-device copies of plans and small tensors go through a pinned
+  // staging ring, so that they neither wait for the stream (as copies from
+  // pageable memory do) nor need a synchronisation before the host buffer
+  // is reused: the bytes are copied into the ring at once, and a region is
+  // reused only after the event recorded behind its copy has completed.
+  // Copies larger than a quarter of the ring take the pageable path.
+  uint8_t* pin_ring = nullptr;
+  size_t pin_cap = 0;
+  uint64_t pin_pos = 0;                    // bytes staged so far (absolute position)
+  struct PinUse { uint64_t start, end; cudaEvent_t ev; };
+  std::deque<PinUse> pin_inflight;
+  std::vector<cudaEvent_t> ev_pool;        // timing-disabled events for the ring
+  cudaEvent_t pool_event();
+  void h2d(void* dst, const void* src, size_t bytes);
+  // environment-update launches timed by event pairs, read after the next
+  // stream synchronisation (no synchronisation of their own)
+  struct EnvTimer { cudaEvent_t a, b; };
+  std::vector<EnvTimer> env_timers;
+  std::vector<cudaEvent_t> timer_pool;     // timing events for env_timers
+  void drain_timers();
+  void timed_env_launch(GemmPlan& p1, GemmPlan& p2);
   int sigma_pending = 0;          // 1: FP64 sigma, 2: tensor-core sigma awaiting accounting
   int* tc_err_host = nullptr;     // pinned copy of the tensor-core error flag
 

@@ -288,12 +288,11 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     }
     if (tasks.empty()) return;
     TcConv* d = dalloc<TcConv>(tasks.size());
-    CK(cudaMemcpyAsync(d, tasks.data(), tasks.size() * sizeof(TcConv), cudaMemcpyHostToDevice, stream));
+    h2d(d, tasks.data(), tasks.size() * sizeof(TcConv));
     launch_tc_convert(d, (int)tasks.size(), prec, panel[0], panel[1], pitch, stream);
     stats.launches++;
     CK(cudaGetLastError());
-    sync();
-    dfree(d);
+    dfree(d);   // stream-ordered: after the conversion
   };
   {
     std::vector<int64_t> r0(renl.subs.size(), -1), c0(renl.subs.size(), 0);
@@ -325,12 +324,12 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   if (!yrowtab.empty()) {
     P->d_yrows = dalloc<TcYRow>(yrowtab.size());
     P->d_ymem = dalloc<int32_t>(ymem.size());
-    CK(cudaMemcpyAsync(P->d_yrows, yrowtab.data(), yrowtab.size() * sizeof(TcYRow), cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(P->d_ymem, ymem.data(), ymem.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream));
+    h2d(P->d_yrows, yrowtab.data(), yrowtab.size() * sizeof(TcYRow));
+    h2d(P->d_ymem, ymem.data(), ymem.size() * sizeof(int32_t));
   }
   P->nsec = nq;
   P->d_sec = dalloc<TcPsiSector>(std::max(nq, 1));
-  CK(cudaMemcpyAsync(P->d_sec, sec.data(), nq * sizeof(TcPsiSector), cudaMemcpyHostToDevice, stream));
+  h2d(P->d_sec, sec.data(), nq * sizeof(TcPsiSector));
   phase(1);   // panels allocated, zeroed and converted
   // ---- stage A tiles: Y^T rows (b, so part of E_R(qout)) x E_L(qin)
   //      columns = sum over si  Rsub(b; si -> so) psi(qin)[:, si part]^T
@@ -433,13 +432,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     }
     P->d_tiles[which] = dalloc<TcTile>(std::max<size_t>(tiles.size(), 1));
     P->d_terms[which] = dalloc<TcTerm>(std::max<size_t>(terms.size(), 1));
-    if (!tiles.empty())
-      CK(cudaMemcpyAsync(P->d_tiles[which], tiles.data(), tiles.size() * sizeof(TcTile), cudaMemcpyHostToDevice,
-                         stream));
-    if (!terms.empty())
-      CK(cudaMemcpyAsync(P->d_terms[which], terms.data(), terms.size() * sizeof(TcTerm), cudaMemcpyHostToDevice,
-                         stream));
-    sync();
+    h2d(P->d_tiles[which], tiles.data(), tiles.size() * sizeof(TcTile));
+    h2d(P->d_terms[which], terms.data(), terms.size() * sizeof(TcTerm));
     tiles.clear();
     terms.clear();
     term_k.clear();
@@ -552,7 +546,7 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     if (!red.empty()) {
       P->part = dalloc<float>((size_t)slot);
       P->d_red = dalloc<TcRed>(red.size());
-      CK(cudaMemcpyAsync(P->d_red, red.data(), red.size() * sizeof(TcRed), cudaMemcpyHostToDevice, stream));
+      h2d(P->d_red, red.data(), red.size() * sizeof(TcRed));
     }
   }
   phase(2);   // host: stage B tiles and split K
@@ -577,7 +571,6 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   phase(4);   // tensor maps
   P->d_err = dalloc<int>(1);
   CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), stream));
-  sync();
   return P;
 }
 
