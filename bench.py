@@ -50,12 +50,13 @@ PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 PRECOND = {"diag": 0, "olsen": 2, "pcg": 3}
 METRIC = "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u22641e-6 Ha"
 # DRAM bytes (read + write, ncu) per algorithmic byte of tc_gemm_kernel, from
-# one --set full capture of `bench.py --sigma-probe 3` (TF32x3 sigma at the
-# central bond of cas16_m512: stage A 494.6 + 240.4 MB, stage B 650.1 + 35.7
-# MB, for 655.0 MB of algorithmic bytes).  The launches of a sweep move the
-# same kinds of panels, so traffic is reported as this ratio times their
-# algorithmic bytes per launch.
-TC_DRAM_PER_ALG_BYTE = (494.5536e6 + 240.401664e6 + 650.058496e6 + 35.650304e6) / 655036096.0
+# one capture of `bench.py --sigma-probe 3 --probe-warm-sweeps 3` (TF32x3
+# sigma at the central bond of the CAS(16,16) M=512 state after three mixed
+# sweeps: stage A 1051.7 + 928.4 MB, stage B 2761.4 + 160.1 MB, for 2359.8 MB
+# of algorithmic bytes).  The launches of a sweep move the same kinds of
+# panels, so traffic is reported as this ratio times their algorithmic bytes
+# per launch.
+TC_DRAM_PER_ALG_BYTE = (1051.665152e6 + 928.384512e6 + 2761.424384e6 + 160.108032e6) / 2359843136.0
 DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
 
 
@@ -687,8 +688,8 @@ def main():
         nl = res["breakdown"]["tc_sigma_builds"] * 2 * args.steps   # two tc_gemm_kernel launches per sigma
         if args.tier2 == "tf32x3" and nl > 0:
             roof["traffic"] = TC_DRAM_PER_ALG_BYTE * res["tc"]["tc_bytes"] / nl
-            roof["traffic_note"] = ("bytes per launch: ncu DRAM/algorithmic ratio %.2f measured at the central bond, "
-                                    "times the timed launches' algorithmic bytes" % TC_DRAM_PER_ALG_BYTE)
+            roof["traffic_note"] = ("bytes per launch: ncu DRAM/algorithmic ratio %.2f measured at the central bond of "
+                                    "the warm state, times the timed launches' algorithmic bytes" % TC_DRAM_PER_ALG_BYTE)
         roof["other_view"] = alt_v
         roof["tc_gemm_ms_per_sweep"] = res["tc"]["tc_gemm_ms"] / args.steps
         roof["launches_per_sweep"] = res["breakdown"]["tc_sigma_builds"] * 2
