@@ -81,7 +81,7 @@ int gbd_set_adaptive_bond_dim(gbd_ctx *ctx, double max_discarded, int32_t m_min)
 
 /* Order in which the persistent tensor-core CTAs take the stage-B tiles of
  * the sigma (output sector q, 128-row block m0 of E_R(q), split-K chunk,
- * N tile n0 of E_L(q)): 0 (default) by (q, m0, chunk, n0), 1 by
+ * N tile n0 of E_L(q)): 0 by (q, m0, chunk, n0), 1 (default) by
  * (q, chunk, m0, n0), 2 by (q, chunk, n0, m0).  Tiles running at the same
  * time share operand boxes through L2 in different ways; every tile
  * computes the same products in the same order, so the result is

@@ -219,7 +219,7 @@ class Engine {
   int tc_fixed_cap = 0;       // > 0: that N cap for every tensor-core plan (no tuning)
   int pcg_steps = 4;          // inner PCG (preconditioner 3): at most this many matvecs per correction
   double pcg_rel_tol = 0.1;   // ... stopping when |residual| < pcg_rel_tol |r|
-  int tc_order = 0;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
+  int tc_order = 1;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
   // stopping of the accurate tier: a plateau (no 30 % drop over 3
   // iterations) ends it below tier2_floor_mult * u2 * max(1, |theta|);
