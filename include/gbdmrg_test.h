@@ -59,6 +59,8 @@ typedef struct {
   int64_t n_solves;               /* Davidson solves (one per two-site step) */
   int64_t n_solves_above_tol;     /* of which ended with ||r|| >= the step's tolerance */
   double sweep_max_residual;      /* largest final ||r|| of the current or last sweep */
+  double enlarge_dev_ms;          /* device time of the block-axpy launches forming the enlarged operators */
+  double enlarge_bytes;           /* their algorithmic bytes: 8 (terms + 1) per output element */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or

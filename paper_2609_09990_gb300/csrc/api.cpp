@@ -850,6 +850,8 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->n_solves = t.n_solves;
   s->n_solves_above_tol = t.n_above_tol;
   s->sweep_max_residual = t.sweep_max_residual;
+  s->enlarge_dev_ms = t.enl_dev_ms;
+  s->enlarge_bytes = t.enl_bytes;
   for (int i = 0; i < 2; ++i) {
     s->tc_stage_alg_bytes[i] = t.tc_alg_st[i];
     s->tc_stage_box_bytes[2 * i] = t.tc_box_st[i][0];

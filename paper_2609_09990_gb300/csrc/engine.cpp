@@ -405,7 +405,7 @@ void Engine::drain_timers() {
   for (auto& t : env_timers) {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, t.a, t.b));
-    stats.env_ms += ms;
+    *t.acc += ms;
     timer_pool.push_back(t.a);
     timer_pool.push_back(t.b);
   }
@@ -425,6 +425,22 @@ cudaEvent_t Engine::pool_event() {
 
 void Engine::h2d(void* dst, const void* src, size_t bytes) {
   if (bytes == 0) return;
+  constexpr size_t kRingMax = (size_t)256 << 20;
+  if (pin_ring && bytes > pin_cap / 4 && pin_cap < kRingMax) {
+    // grow the ring (rare: a few times per engine at most): every staged
+    // copy has to finish before the old ring is released
+    size_t cap = pin_cap;
+    while (bytes > cap / 4 && cap < kRingMax) cap *= 2;
+    CK(cudaStreamSynchronize(stream));
+    for (auto& u : pin_inflight) ev_pool.push_back(u.ev);
+    pin_inflight.clear();
+    CK(cudaFreeHost(pin_ring));
+    pin_ring = nullptr;
+    pin_cap = 0;
+    pin_pos = 0;
+    CK(cudaMallocHost(&pin_ring, cap));
+    pin_cap = cap;
+  }
   if (!pin_ring || bytes > pin_cap / 4) {
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream));
     return;
@@ -507,17 +523,29 @@ void Engine::release(GemmPlan& p) {
 
 void Engine::upload(AxpyPlan& p) {
   check(p);
+  p.cstart.resize(p.outs.size());
+  p.nchunks = 0;
+  p.bytes = 0;
+  for (size_t o = 0; o < p.outs.size(); ++o) {
+    p.cstart[o] = p.nchunks;
+    p.nchunks += (p.outs[o].len + kAxpyChunk - 1) / kAxpyChunk;
+    p.bytes += 8.0 * (p.outs[o].t1 - p.outs[o].t0 + 1) * (double)p.outs[o].len;
+  }
   p.d_terms = dalloc<AxpyTerm>(p.terms.size());
   p.d_outs = dalloc<AxpyOut>(p.outs.size());
+  p.d_cstart = dalloc<int64_t>(p.cstart.size());
   h2d(p.d_terms, p.terms.data(), p.terms.size() * sizeof(AxpyTerm));
   h2d(p.d_outs, p.outs.data(), p.outs.size() * sizeof(AxpyOut));
+  h2d(p.d_cstart, p.cstart.data(), p.cstart.size() * sizeof(int64_t));
 }
 
 void Engine::release(AxpyPlan& p) {
   dfree(p.d_terms);
   dfree(p.d_outs);
+  dfree(p.d_cstart);
   p.d_terms = nullptr;
   p.d_outs = nullptr;
+  p.d_cstart = nullptr;
 }
 
 void Engine::run(GemmPlan& p) {
@@ -850,7 +878,12 @@ void Engine::finish_enl(EnlOp& op, AxpyPlan& ax) {
   for (auto& s : op.subs)
     if (s.own_off >= 0) s.ptr = op.own + s.own_off;
   upload(ax);
-  run(ax);
+  if (!ax.outs.empty()) {
+    EnvTimer t = timer_begin(&stats.enl_dev_ms);
+    run(ax);
+    timer_end(t);
+    stats.enl_bytes += ax.bytes;
+  }
   release(ax);
   ax.clear();
 }
@@ -935,8 +968,9 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
 
 // the two GEMM launches of an environment update between a pair of timing
 // events; their time is read after the next stream synchronisation
-void Engine::timed_env_launch(GemmPlan& p1, GemmPlan& p2) {
+Engine::EnvTimer Engine::timer_begin(double* acc) {
   EnvTimer t;
+  t.acc = acc;
   for (cudaEvent_t* e : {&t.a, &t.b}) {
     if (!timer_pool.empty()) {
       *e = timer_pool.back();
@@ -946,10 +980,19 @@ void Engine::timed_env_launch(GemmPlan& p1, GemmPlan& p2) {
     }
   }
   CK(cudaEventRecord(t.a, stream));
-  run(p1);
-  run(p2);
+  return t;
+}
+
+void Engine::timer_end(EnvTimer t) {
   CK(cudaEventRecord(t.b, stream));
   env_timers.push_back(t);
+}
+
+void Engine::timed_env_launch(GemmPlan& p1, GemmPlan& p2) {
+  EnvTimer t = timer_begin(&stats.env_ms);
+  run(p1);
+  run(p2);
+  timer_end(t);
 }
 
 // R_{k+1}[b](Qout <- Qin) = B_Qout (Renl[b] B_Qin^T); B fused-right.

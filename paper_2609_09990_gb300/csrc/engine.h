@@ -96,6 +96,7 @@ struct Stats {
   double enl_host_ms = 0, diag_ms = 0;   // host part of the enlarged operators; the H_eff diagonal
   double trunc_rho_ms = 0, trunc_eig_ms = 0;   // decimation: density matrices to the host; host eigensolves
   double env_wall_ms = 0;   // environment update: upload (plan checks) + kernels, wall
+  double enl_dev_ms = 0, enl_bytes = 0;   // block-axpy launches of the enlarged operators: device time, bytes
   double tcb_ms[5] = {0, 0, 0, 0, 0};   // plan-build phases: layout/groups, panels, tiles, upload, maps
   void add(const Stats& o) {   // sum of the additive counters (batched solves)
     sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
@@ -121,6 +122,7 @@ struct Stats {
     }
     tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms; enl_host_ms += o.enl_host_ms; diag_ms += o.diag_ms;
     trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms; env_wall_ms += o.env_wall_ms;
+    enl_dev_ms += o.enl_dev_ms; enl_bytes += o.enl_bytes;
     for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
     for (int i = 0; i < 4; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
     max_discarded = std::max(max_discarded, o.max_discarded);
@@ -326,11 +328,13 @@ class Engine {
   void h2d(void* dst, const void* src, size_t bytes);
   // environment-update launches timed by event pairs, read after the next
   // stream synchronisation (no synchronisation of their own)
-  struct EnvTimer { cudaEvent_t a, b; };
+  struct EnvTimer { cudaEvent_t a, b; double* acc; };   // acc: the stats counter the time goes to
   std::vector<EnvTimer> env_timers;
   std::vector<cudaEvent_t> timer_pool;     // timing events for env_timers
   void drain_timers();
   void timed_env_launch(GemmPlan& p1, GemmPlan& p2);
+  EnvTimer timer_begin(double* acc);
+  void timer_end(EnvTimer t);
   int sigma_pending = 0;          // 1: FP64 sigma, 2: tensor-core sigma awaiting accounting
   int* tc_err_host = nullptr;     // pinned copy of the tensor-core error flag
 

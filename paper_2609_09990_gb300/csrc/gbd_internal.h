@@ -129,10 +129,15 @@ struct AxpyOut { double* dst; int64_t len; int32_t t0, t1; };
 struct AxpyPlan {
   std::vector<AxpyTerm> terms;
   std::vector<AxpyOut> outs;
+  std::vector<int64_t> cstart;   // first work chunk of every output (upload fills it)
   AxpyTerm* d_terms = nullptr;
   AxpyOut* d_outs = nullptr;
-  void clear() { terms.clear(); outs.clear(); }
+  int64_t* d_cstart = nullptr;
+  int64_t nchunks = 0;
+  double bytes = 0;              // 8 (terms + 1) len summed over the outputs
+  void clear() { terms.clear(); outs.clear(); cstart.clear(); nchunks = 0; bytes = 0; }
 };
+constexpr int kAxpyChunk = 2048;   // output elements per work chunk of the block axpy
 
 // ---------------------------------------------------------------- kernels (kernels.cu)
 void launch_gemm_f64(const GemmPlan& p, cudaStream_t s);

@@ -118,13 +118,42 @@ gemm_f64_flat_kernel(const GemmTerm* __restrict__ terms, const GemmOut* __restri
   }
 }
 
-__global__ void axpy_kernel(const AxpyTerm* __restrict__ terms, const AxpyOut* __restrict__ outs, int nouts) {
-  for (int oi = blockIdx.x; oi < nouts; oi += gridDim.x) {
-    const AxpyOut o = outs[oi];
-    for (int64_t e = threadIdx.x; e < o.len; e += blockDim.x) {
-      double s = 0.0;
-      for (int t = o.t0; t < o.t1; ++t) s = fma(terms[t].coef, terms[t].src[e], s);
-      o.dst[e] = s;
+// Block axpy over fixed work chunks of kAxpyChunk output elements (the
+// chunks of all outputs in one list, cstart[o] = first chunk of output o):
+// a long output no longer occupies one CTA while the others idle.  Each
+// thread keeps 8 independent sums (elements 256 apart), so eight loads are
+// in flight per term; every element is summed over its terms in list order,
+// as before.
+constexpr int kAxpyThreads = 256;
+__global__ void __launch_bounds__(kAxpyThreads) axpy_kernel(const AxpyTerm* __restrict__ terms,
+                                                            const AxpyOut* __restrict__ outs,
+                                                            const int64_t* __restrict__ cstart, int nouts,
+                                                            int64_t nchunks) {
+  constexpr int kPer = kAxpyChunk / kAxpyThreads;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int lo = 0, hi = nouts - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cstart[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    const AxpyOut o = outs[lo];
+    const int64_t e0 = (c - cstart[lo]) * kAxpyChunk + threadIdx.x;
+    double s[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) s[i] = 0.0;
+    for (int t = o.t0; t < o.t1; ++t) {
+      const double a = terms[t].coef;
+      const double* __restrict__ src = terms[t].src;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int64_t e = e0 + (int64_t)i * kAxpyThreads;
+        if (e < o.len) s[i] = fma(a, src[e], s[i]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int64_t e = e0 + (int64_t)i * kAxpyThreads;
+      if (e < o.len) o.dst[e] = s[i];
     }
   }
 }
@@ -281,10 +310,10 @@ void launch_gemm_f64(const GemmPlan& p, cudaStream_t s) {
 }
 
 void launch_axpy(const AxpyPlan& p, cudaStream_t s) {
-  int no = (int)p.outs.size();
-  if (no == 0) return;
-  int grid = no < 152 * 16 ? no : 152 * 16;
-  axpy_kernel<<<grid, 128, 0, s>>>(p.d_terms, p.d_outs, no);
+  const int no = (int)p.outs.size();
+  if (no == 0 || p.nchunks == 0) return;
+  const int64_t grid = p.nchunks < 152 * 8 ? p.nchunks : 152 * 8;
+  axpy_kernel<<<(int)grid, kAxpyThreads, 0, s>>>(p.d_terms, p.d_outs, p.d_cstart, no, p.nchunks);
 }
 
 void launch_set_identity(double* d, int m, cudaStream_t s) {

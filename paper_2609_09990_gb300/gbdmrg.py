@@ -59,7 +59,8 @@ class gbd_stats(C.Structure):
                 ("tc_stage_alg_bytes", C.c_double * 2), ("tc_stage_box_bytes", C.c_double * 4),
                 ("tc_stage_dense_bytes", C.c_double * 4), ("tc_gemm_ms_by_stage", C.c_double * 2),
                 ("davidson_iterations", C.c_int64), ("inner_matvecs", C.c_int64), ("n_solves", C.c_int64),
-                ("n_solves_above_tol", C.c_int64), ("sweep_max_residual", C.c_double)]
+                ("n_solves_above_tol", C.c_int64), ("sweep_max_residual", C.c_double),
+                ("enlarge_dev_ms", C.c_double), ("enlarge_bytes", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
