@@ -137,7 +137,7 @@ struct AxpyPlan {
   double bytes = 0;              // 8 (terms + 1) len summed over the outputs
   void clear() { terms.clear(); outs.clear(); cstart.clear(); nchunks = 0; bytes = 0; }
 };
-constexpr int kAxpyChunk = 2048;   // output elements per work chunk of the block axpy
+constexpr int kAxpyChunk = 1024;   // output elements per work chunk of the block axpy
 
 // ---------------------------------------------------------------- kernels (kernels.cu)
 void launch_gemm_f64(const GemmPlan& p, cudaStream_t s);

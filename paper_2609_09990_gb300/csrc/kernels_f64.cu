@@ -120,16 +120,19 @@ gemm_f64_flat_kernel(const GemmTerm* __restrict__ terms, const GemmOut* __restri
 
 // Block axpy over fixed work chunks of kAxpyChunk output elements (the
 // chunks of all outputs in one list, cstart[o] = first chunk of output o):
-// a long output no longer occupies one CTA while the others idle.  Each
-// thread keeps 8 independent sums (elements 256 apart), so eight loads are
-// in flight per term; every element is summed over its terms in list order,
-// as before.
+// a long output no longer occupies one CTA while the others idle.  The term
+// descriptors of a chunk are staged in shared memory, so the data loads of
+// four terms (4 x kPer independent loads per thread) are in flight at once;
+// every element is still summed over its terms in list order.
 constexpr int kAxpyThreads = 256;
+constexpr int kAxpyStage = 256;   // term descriptors staged per round
 __global__ void __launch_bounds__(kAxpyThreads) axpy_kernel(const AxpyTerm* __restrict__ terms,
                                                             const AxpyOut* __restrict__ outs,
                                                             const int64_t* __restrict__ cstart, int nouts,
                                                             int64_t nchunks) {
   constexpr int kPer = kAxpyChunk / kAxpyThreads;
+  __shared__ const double* sp[kAxpyStage];
+  __shared__ double sc[kAxpyStage];
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     int lo = 0, hi = nouts - 1;
     while (lo < hi) {
@@ -138,23 +141,40 @@ __global__ void __launch_bounds__(kAxpyThreads) axpy_kernel(const AxpyTerm* __re
     }
     const AxpyOut o = outs[lo];
     const int64_t e0 = (c - cstart[lo]) * kAxpyChunk + threadIdx.x;
+    bool in[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) in[i] = e0 + (int64_t)i * kAxpyThreads < o.len;
     double s[kPer];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) s[i] = 0.0;
-    for (int t = o.t0; t < o.t1; ++t) {
-      const double a = terms[t].coef;
-      const double* __restrict__ src = terms[t].src;
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const int64_t e = e0 + (int64_t)i * kAxpyThreads;
-        if (e < o.len) s[i] = fma(a, src[e], s[i]);
+    for (int tb = o.t0; tb < o.t1; tb += kAxpyStage) {
+      const int nt = min(kAxpyStage, o.t1 - tb);
+      __syncthreads();
+      if (threadIdx.x < nt) {
+        sp[threadIdx.x] = terms[tb + threadIdx.x].src;
+        sc[threadIdx.x] = terms[tb + threadIdx.x].coef;
       }
+      __syncthreads();
+      int t = 0;
+      for (; t + 4 <= nt; t += 4) {
+        double x[4][kPer];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < kPer; ++i) x[u][i] = in[i] ? sp[t + u][e0 + (int64_t)i * kAxpyThreads] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < kPer; ++i) s[i] = fma(sc[t + u], x[u][i], s[i]);
+      }
+      for (; t < nt; ++t)
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+          if (in[i]) s[i] = fma(sc[t], sp[t][e0 + (int64_t)i * kAxpyThreads], s[i]);
     }
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int64_t e = e0 + (int64_t)i * kAxpyThreads;
-      if (e < o.len) o.dst[e] = s[i];
-    }
+    for (int i = 0; i < kPer; ++i)
+      if (in[i]) o.dst[e0 + (int64_t)i * kAxpyThreads] = s[i];
   }
 }
 

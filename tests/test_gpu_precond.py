@@ -72,7 +72,7 @@ def test_training_keeps_the_converged_energy(G, tmp_path):
     path = str(tmp_path / "precond.bin")
     ctx.save_precond(path)
     r_learn = ctx.solve(h, chol, 6, 0, [64] * 4, [1e-10] * 4, seed=1, preconditioner=1)
-    it1, fb, _ = ctx.davidson_counts()
+    it1, fb, _ = ctx.davidson_counts()   # counters restart with every solve
     ctx.close()
     ctx2 = G.Context(0)
     r_diag = ctx2.solve(h, chol, 6, 0, [64] * 4, [1e-10] * 4, seed=1, preconditioner=0)
@@ -85,7 +85,12 @@ def test_training_keeps_the_converged_energy(G, tmp_path):
     r_load = ctx3.solve(h, chol, 6, 0, [64] * 4, [1e-10] * 4, seed=1, preconditioner=1)
     assert abs(r_load["energy"] - r_diag["energy"]) < 1e-10
     ctx3.close()
-    print("Davidson iterations: learned", it1, "diagonal", it2, "fallbacks", fb)
+    # what the network gains: the relative change in Davidson iterations of
+    # the same solve.  The pointwise network is about neutral (a few percent
+    # either way); the bound guards against it costing iterations.
+    gain = (it2 - it1) / it2
+    print("Davidson iterations: learned", it1, "diagonal", it2, "fallbacks", fb, "gain %.3f" % gain)
+    assert gain >= -0.15
 
 
 def test_learned_without_weights_is_rejected(G):
