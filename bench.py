@@ -48,6 +48,7 @@ from gbd_synth import WORKLOADS, make_integrals  # noqa: E402
 
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 PRECOND = {"diag": 0, "olsen": 2, "pcg": 3}
+ENV_PREC = {"fp64": 0, "tf32x3": 3, "bf16x3": 4}
 METRIC = "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u22641e-6 Ha"
 # DRAM bytes (read + write, ncu) per algorithmic byte of tc_gemm_kernel, from
 # one capture of `bench.py --sigma-probe 3 --probe-warm-sweeps 3` (TF32x3
@@ -133,6 +134,7 @@ def run_ours(args, rank, world):
     ctx = G.Context(dev)
     ctx.set_accurate_tier(3 if args.tier2 == "tf32x3" else 4)
     ctx.set_tier_stop(args.floor_mult, args.hard_stag)
+    ctx.set_env_precision(ENV_PREC[args.env_prec])
     nsw = args.warmup + args.steps
     ctx.setup(h, chol, ne, 0, [M] * (nsw + 1), schedule(nsw + 1, args.tol), seed=seed, precision=prec,
               fp64_refine=args.refine)
@@ -265,6 +267,7 @@ def run_ours(args, rank, world):
         ctx = G.Context(dev)
         ctx.set_accurate_tier(3 if args.tier2 == "tf32x3" else 4)
         ctx.set_tier_stop(args.floor_mult, args.hard_stag)
+        ctx.set_env_precision(ENV_PREC[args.env_prec])
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         r = ctx.solve(h, chol, ne, 0, [M] * args.steps, schedule(args.steps, args.tol), seed=seed,
@@ -567,6 +570,8 @@ def main():
                     help="accurate tier stops on a plateau below floor_mult x u x |theta|")
     ap.add_argument("--hard-stag", type=int, default=8,
                     help="accurate tier stops after this many iterations without a 30%% cut (0: off)")
+    ap.add_argument("--env-prec", default="fp64", choices=sorted(ENV_PREC),
+                    help="environment updates of the mixed sweeps (tensor cores for tf32x3 / bf16x3)")
     ap.add_argument("--tier2", default="tf32x3", choices=["tf32x3", "bf16x3"],
                     help="operands of the accurate Davidson tier")
     ap.add_argument("--sigma-probe", type=int, default=0, help="profiling driver: central sigma of cas16_m512 "
@@ -623,6 +628,7 @@ def main():
     config = {"workload": f"{args.workload}: CAS({wl['n_elec']}e,{wl['n_orb']}o) S_z=0, {wl['n_chol']} Cholesky "
                           f"vectors, M={wl['M']}, one step = one full sweep",
               "n_orb": wl["n_orb"], "bond_dim": wl["M"], "davidson_tol": args.tol,
+              "environment_updates": args.env_prec if args.precision != "fp64" else "fp64",
               "davidson_stop": "FP64 path: ||r|| < tol.  Mixed tiers: ||r|| < tol, or the accurate tier's floor "
                                f"(||r|| below {args.floor_mult:g} u max(1,|theta|), u = its measured sigma error, and "
                                f"no 30 % drop over 3 iterations; or no 30 % drop over {args.hard_stag} iterations), "

@@ -107,6 +107,14 @@ int gbd_set_accurate_tier(gbd_ctx *ctx, int32_t prec);
  * hard_stag < 0. */
 int gbd_set_tier_stop(gbd_ctx *ctx, double floor_mult, int32_t hard_stag);
 
+/* Environment updates of the sweep steps of reduced-precision schedules:
+ * prec 0 = FP64 (the default), 3 = on the tensor cores with TF32x3 operands,
+ * 4 = BF16x3 (FP32 accumulation in chunks of at most 512 of K, summed in
+ * FP64).  Environments built outside the steps (initial state, saved
+ * state, installed MPS) and those the reported energy uses are FP64.
+ * GBD_ERR_ARG for another prec. */
+int gbd_set_env_precision(gbd_ctx *ctx, int32_t prec);
+
 /* Reduced-precision schedules solve steps whose two-site state has fewer
  * than n elements (chain ends) in FP64: there the tensor-core plan costs
  * more than it saves.  Default 4096; 0 = always the tensor-core tiers. */

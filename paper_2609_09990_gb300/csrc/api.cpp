@@ -16,6 +16,7 @@
 #include "../../include/gbdmrg_test.h"
 #include "engine.h"
 #include "linalg_host.h"
+#include "tc_gemm.h"
 
 namespace gbd {
 double mps_init_value(uint64_t seed, int site, int na, int nb, int s, int row, int col);
@@ -408,6 +409,15 @@ int gbd_set_accurate_tier(gbd_ctx* ctx, int32_t prec) {
     if (prec != 3 && prec != 4) return fail(ctx, GBD_ERR_ARG, "accurate tier must be 3 (TF32x3) or 4 (BF16x3)");
     if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
     ctx->eng->tier2 = prec == 3 ? 2 : 3;   // TcPrec kTF32x3 / kBF16x3
+    return GBD_OK;
+  });
+}
+
+int gbd_set_env_precision(gbd_ctx* ctx, int32_t prec) {
+  return guarded(ctx, [&]() {
+    if (prec != 0 && prec != 3 && prec != 4) return fail(ctx, GBD_ERR_ARG, "env precision must be 0, 3 or 4");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->env_prec = prec == 0 ? -1 : (prec == 3 ? gbd::kTF32x3 : gbd::kBF16x3);
     return GBD_OK;
   });
 }

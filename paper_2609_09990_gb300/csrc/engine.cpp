@@ -333,6 +333,7 @@ Engine::~Engine() {
   free_snapshot();
   clear_states();
   if (psi) dfree(psi);
+  if (d_env_err) dfree(d_env_err);
   cudaStreamSynchronize(stream);
   for (auto& u : pin_inflight) cudaEventDestroy(u.ev);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -402,6 +403,12 @@ void Engine::sync() {
 }
 
 void Engine::drain_timers() {
+  if (env_tc_pending) {
+    env_tc_pending = false;
+    int flag = 0;
+    CK(cudaMemcpy(&flag, d_env_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) throw Error(-5, "tensor-core environment update: a bounded device wait ran out");
+  }
   for (auto& t : env_timers) {
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, t.a, t.b));
@@ -956,18 +963,14 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
     p2.add_term(A.d + A.off[tb.nout], nout, T + tb.off, nin, el.dim[tb.qout], 1, 1.0);
   }
   const double th0 = now_ms();
-  upload(p1);
-  upload(p2);
   timed_env_launch(p1, p2);
   stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
-  release(p1);
-  release(p2);
   dfree(T);
 }
 
-// the two GEMM launches of an environment update between a pair of timing
-// events; their time is read after the next stream synchronisation
+// a pair of timing events around device work on the engine stream; the
+// time goes to *acc after the next stream synchronisation
 Engine::EnvTimer Engine::timer_begin(double* acc) {
   EnvTimer t;
   t.acc = acc;
@@ -988,11 +991,27 @@ void Engine::timer_end(EnvTimer t) {
   env_timers.push_back(t);
 }
 
+// the two GEMM plans of an environment update (checked, uploaded, run and
+// released), on the FP64 units or on the tensor cores
 void Engine::timed_env_launch(GemmPlan& p1, GemmPlan& p2) {
+  if (env_prec >= 0 && !force_fp64_env && sched.precision != 0) {
+    check(p1);
+    check(p2);
+    EnvTimer t = timer_begin(&stats.env_ms);
+    run_tc(p1, env_prec);
+    run_tc(p2, env_prec);
+    timer_end(t);
+    env_tc_used = true;
+    return;
+  }
+  upload(p1);
+  upload(p2);
   EnvTimer t = timer_begin(&stats.env_ms);
   run(p1);
   run(p2);
   timer_end(t);
+  release(p1);
+  release(p2);
 }
 
 // R_{k+1}[b](Qout <- Qin) = B_Qout (Renl[b] B_Qin^T); B fused-right.
@@ -1035,13 +1054,9 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
     p2.add_term(B.d + B.off[tb.nout], er.dim[tb.qout], T + tb.off, nin, er.dim[tb.qout], 0, 1.0);
   }
   const double th0 = now_ms();
-  upload(p1);
-  upload(p2);
   timed_env_launch(p1, p2);
   stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
-  release(p1);
-  release(p2);
   dfree(T);
 }
 
@@ -1978,7 +1993,12 @@ void Engine::init_mps(uint64_t seed, int M) {
 }
 
 void Engine::build_right_envs(int from_k) {
-  // R_n = 1 on channel H; R_i = B_i Renl_i B_i^T for i = n-1 .. from_k
+  // R_n = 1 on channel H; R_i = B_i Renl_i B_i^T for i = n-1 .. from_k;
+  // environments built outside the sweep steps are FP64
+  const bool f0 = force_fp64_env;
+  force_fp64_env = true;
+  struct Restore { bool& f; bool v; ~Restore() { f = v; } } restore{force_fp64_env, f0};
+  env_tc_used = false;
   for (auto& e : Renv) free_env(e);
   Renv.assign(n + 1, Env());
   make_env(n, Renv[n]);
@@ -2000,6 +2020,9 @@ void Engine::build_right_envs(int from_k) {
 }
 
 void Engine::build_left_envs(int to_k) {
+  const bool f0 = force_fp64_env;
+  force_fp64_env = true;
+  struct Restore { bool& f; bool v; ~Restore() { f = v; } } restore{force_fp64_env, f0};
   for (auto& e : Lenv) free_env(e);
   Lenv.assign(n + 1, Env());
   make_env(0, Lenv[0]);
@@ -2110,8 +2133,10 @@ double Engine::sweep(int s) {
   return e;
 }
 
-// <psi|H|psi> / <psi|psi> at bond (0,1) of the current MPS
+// <psi|H|psi> / <psi|psi> at bond (0,1) of the current MPS, with FP64
+// environments (right environments updated on the tensor cores are rebuilt)
 double Engine::final_energy() {
+  if (env_tc_used) build_right_envs(2);
   setup_two_site(0);
   form_psi(0, 0);
   Sigma sg;

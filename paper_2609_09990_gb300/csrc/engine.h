@@ -223,6 +223,13 @@ class Engine {
   double pcg_rel_tol = 0.1;   // ... stopping when |residual| < pcg_rel_tol |r|
   int tc_order = 1;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
+  // environment updates of the sweep steps of reduced-precision schedules:
+  // -1 = FP64 (default), else on the tensor cores with these operands
+  // (TcPrec).  Environments built outside the steps (initial state, saved
+  // state, installed MPS, the reported energy) are always FP64.
+  int env_prec = -1;
+  bool env_tc_used = false;   // the right environments hold tensor-core updates
+  bool force_fp64_env = false;
   // stopping of the accurate tier: a plateau (no 30 % drop over 3
   // iterations) ends it below tier2_floor_mult * u2 * max(1, |theta|);
   // hard_stag_iters > 0: no 30 % drop over that many iterations ends it at
@@ -333,6 +340,11 @@ class Engine {
   std::vector<cudaEvent_t> timer_pool;     // timing events for env_timers
   void drain_timers();
   void timed_env_launch(GemmPlan& p1, GemmPlan& p2);
+  // a GemmPlan (every output overwritten) on the tensor cores, operands in
+  // precision prec (TcPrec), split-K FP64 sums (gemm_tc.cpp)
+  void run_tc(GemmPlan& p, int prec);
+  int* d_env_err = nullptr;      // bounded-wait flag of the tensor-core environment updates
+  bool env_tc_pending = false;   // such launches since the last check of the flag
   EnvTimer timer_begin(double* acc);
   void timer_end(EnvTimer t);
   int sigma_pending = 0;          // 1: FP64 sigma, 2: tensor-core sigma awaiting accounting

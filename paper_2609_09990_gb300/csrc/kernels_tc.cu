@@ -449,12 +449,16 @@ __global__ void tc_convert_kernel(const TcConv* __restrict__ tasks, int ntasks, 
     const TcConv c = tasks[t];
     const int64_t n = (int64_t)c.rows * c.cols;
     for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-      const int r = (int)(e / c.cols), col = (int)(e % c.cols);
+      // transposed sources are walked along their rows (consecutive r), so
+      // that the reads stay coalesced
+      const int r = c.trans ? (int)(e % c.rows) : (int)(e / c.cols);
+      const int col = c.trans ? (int)(e / c.rows) : (int)(e % c.cols);
       const int64_t dst = c.kstride > 0
                               ? ((int64_t)c.r0 + (int64_t)((c.c0 + col) / pitch) * c.kstride + r) * pitch +
                                     (c.c0 + col) % pitch
                               : (int64_t)(c.r0 + r) * pitch + c.c0 + col;
-      store_conv(c.scale * c.src[(int64_t)r * c.ld_src + col], prec, hi, lo, dst);
+      const double x = c.trans ? c.src[(int64_t)col * c.ld_src + r] : c.src[(int64_t)r * c.ld_src + col];
+      store_conv(c.scale * x, prec, hi, lo, dst);
     }
   }
 }

@@ -130,6 +130,7 @@ struct TcConv {
   int32_t rows, cols, ld_src;
   int32_t r0, c0;
   int32_t kstride;
+  int32_t trans;         // 1: element (r, c) of the block is src[c * ld_src + r]
 };
 void launch_tc_convert(const TcConv* tasks, int ntasks, int prec, void* hi, void* lo, int64_t pitch,
                        cudaStream_t s);

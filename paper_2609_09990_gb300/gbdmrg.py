@@ -100,6 +100,7 @@ def lib():
         "gbd_set_tc_min_two_site": (C.c_int, [vp, C.c_int64]),
         "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tier_stop": (C.c_int, [vp, C.c_double, C.c_int32]),
+        "gbd_set_env_precision": (C.c_int, [vp, C.c_int32]),
         "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_order": (C.c_int, [vp, C.c_int32]),
@@ -358,6 +359,10 @@ class Context:
 
     def set_preconditioner(self, preconditioner):
         self._check(self.L.gbd_set_preconditioner(self.ptr, preconditioner), "gbd_set_preconditioner")
+
+    def set_env_precision(self, prec):
+        """Environment updates of the steps: 0 FP64, 3 TF32x3, 4 BF16x3 (tensor cores)."""
+        self._check(self.L.gbd_set_env_precision(self.ptr, prec), "gbd_set_env_precision")
 
     def set_tier_stop(self, floor_mult, hard_stag=0):
         self._check(self.L.gbd_set_tier_stop(self.ptr, float(floor_mult), int(hard_stag)), "gbd_set_tier_stop")

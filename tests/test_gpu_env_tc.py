@@ -1,0 +1,72 @@
+"""Environment updates on the tensor cores (gbd_set_env_precision): the
+left and right environments after a two-site step equal those of the FP64
+update within the TF32x3 error (same Davidson result, only the update
+differs), and whole reduced-precision solves with tensor-core environment
+updates reach the FP64 solve's energy within the metric's 1e-6 Ha (the
+reported energy is evaluated with FP64 environments)."""
+import numpy as np
+import pytest
+
+from gbd_synth import WORKLOADS, make_integrals
+from oracle import dmrg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2609_09990_gb300 import build, gbdmrg
+    build.build()
+    return gbdmrg
+
+
+def _step_envs(G, env_prec, direction):
+    n, ne, nq, seed, M, k = 8, 8, 10, 3, 40, 3
+    h, chol = make_integrals(n, nq, seed)
+    d = dmrg.DMRG(h, chol, ne, 0, M, seed=seed)
+    for j in range(k):
+        d.step(j, M, 1e-10, "L")
+    ctx = G.Context(0)
+    ctx.set_tc_min_two_site(0)
+    ctx.setup(h, chol, ne, 0, [M], [1e-8], seed=seed, precision=G.GBD_BF16, fp64_refine=0)
+    ctx.set_env_precision(env_prec)
+    ns, tr, data = dmrg.canonical_blocks(d)
+    ctx.set_mps(ns, tr, data, k)
+    ctx.run_step(k, direction, M, 1e-8)
+    side, bond = (0, k + 1) if direction == 0 else (1, k + 1)
+    blocks = {}
+    for a in range(len(ctx.mpo_labels(bond))):
+        for si in range(len(ctx.get_bond(bond))):
+            b = ctx.env_block(side, bond, a, si)
+            if b.size:
+                blocks[(a, si)] = b
+    ctx.close()
+    return blocks
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("env_prec,bound", [(3, 2e-5), (4, 2e-4)])
+def test_tensor_core_env_update_matches_fp64(G, direction, env_prec, bound):
+    ref = _step_envs(G, 0, direction)
+    got = _step_envs(G, env_prec, direction)
+    assert ref.keys() == got.keys()
+    scale = max(np.abs(b).max() for b in ref.values())
+    err = max(np.abs(got[key] - ref[key]).max() for key in ref)
+    assert err <= bound * scale, err / scale
+
+
+def test_whole_solve_with_tensor_core_envs_cas12(G):
+    wl = WORKLOADS["cas12_m256"]
+    n, ne, nq, M, seed = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"]
+    h, chol = make_integrals(n, nq, seed)
+    out = {}
+    for name, prec, env in (("fp64", G.GBD_FP64, 0), ("mixed", G.GBD_BF16, 0), ("mixed_tc_env", G.GBD_BF16, 3)):
+        ctx = G.Context(0)
+        ctx.set_env_precision(env)
+        out[name] = ctx.solve(h, chol, ne, 0, [M] * 4, [1e-6] * 4, seed=seed, precision=prec, fp64_refine=0,
+                              rdms=True)
+        ctx.close()
+    a, b, c = out["mixed_tc_env"], out["mixed"], out["fp64"]
+    assert abs(a["energy"] - c["energy"]) <= 1e-6, (a["energy"], c["energy"])
+    assert abs(a["energy"] - b["energy"]) <= 1e-6
+    assert np.abs(a["rdm1"] - c["rdm1"]).max() <= 1e-4
