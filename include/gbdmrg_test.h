@@ -255,6 +255,14 @@ int gbd_pcg_selftest(gbd_ctx *ctx, int32_t k, const double *x, const double *r, 
  * panels plus M N doubles. */
 int gbd_tc_rate(int32_t device, int32_t prec, int32_t M, int32_t N, int32_t K, int32_t reps, double *tflops,
                 double *ms_per_launch);
+/* Self-test of the tensor-core executor of grouped GEMM plans (the path of
+ * gbd_set_env_precision): an M x N output summing nterms products of K
+ * columns (flags: 1 = A transposed, 2 = B transposed; alternating signs) and
+ * a smaller second output, on random operands, run on the tensor cores
+ * (prec 3 TF32x3, 4 BF16x3) and by the FP64 grouped GEMM.  Returns max
+ * |difference| and max |FP64 result|. */
+int gbd_gemm_tc_selftest(gbd_ctx *ctx, int32_t M, int32_t N, int32_t K, int32_t nterms, int32_t flags, int32_t prec,
+                         uint64_t seed, double *max_err, double *max_ref);
 /* Failure detection without a fault: one bounded mbarrier wait (the helper
  * every role of the tensor-core kernel uses).  arrive = 0: nothing completes
  * the barrier, the wait runs out after its poll limit (2^22 polls, a few

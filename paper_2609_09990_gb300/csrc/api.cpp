@@ -422,6 +422,19 @@ int gbd_set_env_precision(gbd_ctx* ctx, int32_t prec) {
   });
 }
 
+int gbd_gemm_tc_selftest(gbd_ctx* ctx, int32_t M, int32_t N, int32_t K, int32_t nterms, int32_t flags, int32_t prec,
+                         uint64_t seed, double* max_err, double* max_ref) {
+  return guarded(ctx, [&]() {
+    if (M < 1 || N < 1 || K < 1 || nterms < 1 || flags < 0 || flags > 3 || (prec != 3 && prec != 4) || !max_err ||
+        !max_ref || (int64_t)M * N > (1 << 26) || (int64_t)K * std::max(M, N) * nterms > (1 << 27))
+      return fail(ctx, GBD_ERR_ARG, "invalid self-test arguments");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->gemm_tc_selftest(M, N, K, nterms, flags, prec == 3 ? gbd::kTF32x3 : gbd::kBF16x3, seed, max_err,
+                               max_ref);
+    return GBD_OK;
+  });
+}
+
 int gbd_set_tier_stop(gbd_ctx* ctx, double floor_mult, int32_t hard_stag) {
   return guarded(ctx, [&]() {
     if (!(floor_mult > 0) || !std::isfinite(floor_mult) || hard_stag < 0)

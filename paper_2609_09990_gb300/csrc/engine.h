@@ -421,6 +421,8 @@ class Engine {
   // without decimation or environment update: Ritz value, and the FP64
   // Rayleigh quotient and FP64 residual norm of the resulting vector
   void probe_step(int k, int precision, int refine, double tol, double* theta, double* e64, double* r64);
+  void gemm_tc_selftest(int M, int N, int K, int nterms, int flags, int prec, uint64_t seed, double* max_err,
+                        double* max_ref);
   // the inner-PCG correction of the Davidson solver at centre k with the
   // FP64 sigma and the step's own H_eff diagonal, from host x, r and theta
   void pcg_selftest(int k, const double* x_host, const double* r_host, double theta, double* t_host,

@@ -197,3 +197,73 @@ void Engine::run_tc(GemmPlan& p, int prec) {
 }
 
 }  // namespace gbd
+
+namespace gbd {
+
+// Self-test of run_tc against the FP64 grouped GEMM on random operands: two
+// outputs (M x N and a smaller one sharing the first term's A block), nterms
+// terms each of K columns with transposition flags `flags` (1 transA, 2
+// transB) and alternating signs; max |C_tc - C_fp64| and max |C_fp64|.
+void Engine::gemm_tc_selftest(int M, int N, int K, int nterms, int flags, int prec, uint64_t seed, double* max_err,
+                              double* max_ref) {
+  const bool ta = flags & 1, tb = flags & 2;
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 1;
+  auto rnd = [&]() {
+    st ^= st >> 12;
+    st ^= st << 25;
+    st ^= st >> 27;
+    return (double)((st * 0x2545F4914F6CDD1Dull) >> 11) / 9007199254740992.0 - 0.5;
+  };
+  const int lda = (ta ? M : K) + 3, ldb = (tb ? K : N) + 5;
+  const size_t asz = (size_t)(ta ? K : M) * lda, bsz = (size_t)(tb ? N : K) * ldb;
+  std::vector<double> hA(asz * nterms), hB(bsz * nterms);
+  for (double& v : hA) v = rnd();
+  for (double& v : hB) v = rnd();
+  double* A = dalloc<double>(hA.size());
+  double* B = dalloc<double>(hB.size());
+  const int ldc = N + 7;
+  const int M2 = std::max(1, M / 3), N2 = std::max(1, N / 2);
+  const size_t csz = (size_t)M * ldc + (size_t)M2 * N2;
+  double* C1 = dalloc<double>(csz);
+  double* C2 = dalloc<double>(csz);
+  h2d(A, hA.data(), hA.size() * sizeof(double));
+  h2d(B, hB.data(), hB.size() * sizeof(double));
+  CK(cudaMemsetAsync(C1, 0, csz * sizeof(double), stream));
+  CK(cudaMemsetAsync(C2, 0, csz * sizeof(double), stream));
+  auto plan = [&](double* C, GemmPlan& p) {
+    p.add_out(C, ldc, M, N, 0);
+    for (int t = 0; t < nterms; ++t)
+      p.add_term(A + asz * t, lda, B + bsz * t, ldb, K, flags, t % 2 ? -1.0 : 1.0);
+    // second output: the first term's operands on a corner, scaled by 0.5
+    p.add_out(C + (size_t)M * ldc, N2, M2, N2, 0);
+    p.add_term(A, lda, B, ldb, K, flags, 0.5);
+  };
+  GemmPlan p1, p2;
+  plan(C1, p1);
+  plan(C2, p2);
+  check(p1);
+  run_tc(p1, prec);
+  upload(p2);
+  run(p2);
+  release(p2);
+  std::vector<double> h1(csz), h2(csz);
+  CK(cudaMemcpyAsync(h1.data(), C1, csz * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(h2.data(), C2, csz * sizeof(double), cudaMemcpyDeviceToHost, stream));
+  sync();
+  double me = 0, mr = 0;
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      me = std::max(me, std::fabs(h1[(size_t)i * ldc + j] - h2[(size_t)i * ldc + j]));
+      mr = std::max(mr, std::fabs(h2[(size_t)i * ldc + j]));
+    }
+  for (size_t e = (size_t)M * ldc; e < csz; ++e) {
+    me = std::max(me, std::fabs(h1[e] - h2[e]));
+    mr = std::max(mr, std::fabs(h2[e]));
+  }
+  *max_err = me;
+  *max_ref = mr;
+  for (void* q : {(void*)A, (void*)B, (void*)C1, (void*)C2}) dfree(q);
+  sync();
+}
+
+}  // namespace gbd

@@ -101,6 +101,8 @@ def lib():
         "gbd_set_accurate_tier": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tier_stop": (C.c_int, [vp, C.c_double, C.c_int32]),
         "gbd_set_env_precision": (C.c_int, [vp, C.c_int32]),
+        "gbd_gemm_tc_selftest": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                           C.c_uint64, _dp, _dp]),
         "gbd_set_preconditioner": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_tile": (C.c_int, [vp, C.c_int32]),
         "gbd_set_tc_order": (C.c_int, [vp, C.c_int32]),
@@ -363,6 +365,13 @@ class Context:
     def set_env_precision(self, prec):
         """Environment updates of the steps: 0 FP64, 3 TF32x3, 4 BF16x3 (tensor cores)."""
         self._check(self.L.gbd_set_env_precision(self.ptr, prec), "gbd_set_env_precision")
+
+    def gemm_tc_selftest(self, M, N, K, nterms, flags, prec=3, seed=1):
+        """(max |tensor-core - FP64|, max |FP64|) of a random grouped GEMM plan."""
+        e, r = C.c_double(), C.c_double()
+        self._check(self.L.gbd_gemm_tc_selftest(self.ptr, M, N, K, nterms, flags, prec, seed, C.byref(e),
+                                                C.byref(r)), "gbd_gemm_tc_selftest")
+        return e.value, r.value
 
     def set_tier_stop(self, floor_mult, hard_stag=0):
         self._check(self.L.gbd_set_tier_stop(self.ptr, float(floor_mult), int(hard_stag)), "gbd_set_tier_stop")

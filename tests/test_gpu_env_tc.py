@@ -77,3 +77,17 @@ def test_whole_solve_with_tensor_core_envs_cas12(G):
         e_rdm = np.einsum("pq,pq->", h, r["rdm1"]) + 0.5 * np.einsum("pqrs,pqrs->", eri, r["rdm2"])
         assert abs(r["energy"] - e_rdm) <= 1e-9, (r["energy"], e_rdm)
     assert a["energy"] <= c["energy"] + 1e-6, (a["energy"], c["energy"])
+
+
+@pytest.mark.parametrize("M,N,K,nterms", [(30, 20, 50, 3), (300, 200, 700, 2), (129, 257, 1100, 1), (7, 133, 8, 4)])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec,bound", [(3, 1e-5), (4, 2e-4)])
+def test_tensor_core_gemm_plan_matches_fp64(G, M, N, K, nterms, flags, prec, bound):
+    # the executor of the tensor-core environment updates on shapes with
+    # several 128 x 128 tiles, K split into 512-wide pieces and chunks,
+    # transposed operands, signs and a folded scale
+    ctx = G.Context(0)
+    err, ref = ctx.gemm_tc_selftest(M, N, K, nterms, flags, prec, seed=M + N + K + flags)
+    ctx.close()
+    assert ref > 0
+    assert err <= bound * ref, err / ref
