@@ -448,6 +448,24 @@ def sigma_probe(prec, orders=(0,), warm_sweeps=0, davidson=False):
     ctx.close()
 
 
+def precond_probe(n):
+    """Profiling driver for the fused learned-preconditioner kernel: n
+    elements of (r, diag) and a seeded random network, one application
+    (features, MLP with FP16 weights, Jacobi step) through gbd_mlp_precond."""
+    from paper_2609_09990_gb300 import gbdmrg as G
+    rng = np.random.default_rng(4)
+    nparam = 128 * 8 + 128 + 128 + 1
+    p = np.concatenate([rng.normal(0, 0.3, 128 * 8), rng.normal(0, 0.1, 128), rng.normal(0, 0.1, 128), [0.05]])
+    assert p.size == nparam
+    r = rng.normal(size=n) * 1e-3
+    d = rng.normal(size=n) * 3 - 10
+    ctx = G.Context(0)
+    ctx.set_precond_weights(p.astype(np.float32))
+    t = ctx.mlp_precond(r, d, -10.5, 3.0)
+    ctx.close()
+    print(json.dumps({"precond_probe": n, "finite": bool(np.all(np.isfinite(t)))}))
+
+
 def states_run(args):
     """Excited states by penalty deflation on a workload (gbd_solve_states):
     the lowest `--states` roots of any spin (no <S^2> guard), each from its
@@ -581,10 +599,15 @@ def main():
     ap.add_argument("--penalty", type=float, default=2.0, help="deflation penalty (Ha) of --states")
     ap.add_argument("--probe-warm-sweeps", type=int, default=0, help="--sigma-probe on the state after this many "
                     "mixed-precision sweeps (profiler started before the timed builds)")
+    ap.add_argument("--precond-probe", type=int, default=0, help="profiling driver: one fused learned-"
+                    "preconditioner application on this many elements (no bench line)")
     ap.add_argument("--probe-davidson", action="store_true", help="--sigma-probe: one mixed-precision Davidson "
                     "solve at the central bond instead of the sigma builds")
     ap.add_argument("--probe-orders", default="0", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2")
     args = ap.parse_args()
+    if args.precond_probe:
+        precond_probe(args.precond_probe)
+        return
     if args.sigma_probe:
         sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")), args.probe_warm_sweeps,
                     args.probe_davidson)
