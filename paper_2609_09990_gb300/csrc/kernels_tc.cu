@@ -428,7 +428,6 @@ __global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, co
     }
   }
 }
-}
 
 // ---------------------------------------------------------------- conversions
 __device__ __forceinline__ void store_conv(double x, int prec, void* hi, void* lo, int64_t idx) {
