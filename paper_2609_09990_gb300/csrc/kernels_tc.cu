@@ -399,33 +399,34 @@ __global__ void bounded_wait_probe_kernel(int arrive, int* err, int* waited_ok) 
 }
 
 // ---------------------------------------------------------------- split-K sum
-// one thread per output element of a task; the slots are summed in FP64
-// with eight interleaved partial sums combined in a fixed order
-// (deterministic).  The eight loads of a round are independent, so a long
-// slot list is not a chain of dependent memory latencies.
-__global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, const float* __restrict__ part,
-                                 double* __restrict__ out) {
-  // one CTA per task at a time (no search for the task of an element);
-  // consecutive threads take consecutive rows i of one output column j
-  for (int t = blockIdx.x; t < ntasks; t += gridDim.x) {
-    const TcRed R = tasks[t];
-    const int64_t ss = (int64_t)128 * R.n_stride;
-    const int cnt = R.m_valid * R.n_valid;
-    for (int loc = threadIdx.x; loc < cnt; loc += blockDim.x) {
-      const int j = loc / R.m_valid, i = loc - j * R.m_valid;
-      const float* p = part + R.slot0 + (int64_t)j * 128 + i;
-      double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int s = 0;
-      for (; s + 8 <= R.nslot; s += 8) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = p[(s + u) * ss];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a[u] += (double)v[u];
-      }
-      for (int u = 0; s < R.nslot; ++s, ++u) a[u] += (double)p[s * ss];
-      out[R.out + (int64_t)j * R.ld + R.m0 + i] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+// one thread per output element; the slots are summed in FP64 with eight
+// interleaved partial sums combined in a fixed order (deterministic).  The
+// eight loads of a round are independent, so a long slot list is not a
+// chain of dependent memory latencies.
+__global__ void tc_reduce_kernel(const TcRed* __restrict__ tasks, int ntasks, int64_t total,
+                                 const float* __restrict__ part, double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].e0 <= e) lo = mid; else hi = mid - 1;
     }
+    const TcRed R = tasks[lo];
+    const int loc = (int)(e - R.e0);
+    const int j = loc / R.m_valid, i = loc - j * R.m_valid;
+    const int64_t ss = (int64_t)128 * R.n_stride;
+    const float* p = part + R.slot0 + (int64_t)j * 128 + i;
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int s = 0;
+    for (; s + 8 <= R.nslot; s += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = p[(s + u) * ss];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += (double)v[u];
+    }
+    for (int u = 0; s < R.nslot; ++s, ++u) a[u] += (double)p[s * ss];
+    out[R.out + (int64_t)j * R.ld + R.m0 + i] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
 }
 
@@ -488,8 +489,9 @@ __global__ void tc_convert_psi_kernel(const double* __restrict__ psi, const TcPs
 void launch_tc_reduce(const TcRed* tasks, int ntasks, int64_t total, const float* part, double* out,
                       cudaStream_t s) {
   if (ntasks <= 0 || total <= 0) return;
-  const int b = ntasks < 152 * 8 ? ntasks : 152 * 8;
-  tc_reduce_kernel<<<b, 256, 0, s>>>(tasks, ntasks, part, out);
+  int64_t b = (total + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  tc_reduce_kernel<<<(int)b, 256, 0, s>>>(tasks, ntasks, total, part, out);
 }
 
 bool bounded_wait_probe(int arrive, int* err_dev, int* ok_dev, cudaStream_t s) {
