@@ -466,6 +466,66 @@ def precond_probe(n):
     print(json.dumps({"precond_probe": n, "finite": bool(np.all(np.isfinite(t)))}))
 
 
+def precond_ab(args):
+    """Learned against diagonal Davidson preconditioner at --workload
+    (default CAS(20,20) M=1024): the network is trained on the device on
+    residuals recorded from CAS(6,6) (4 sweeps), CAS(12,12) (2 sweeps) and
+    CAS(16,16) (1 sweep); the workload then runs --warmup mixed sweeps, and at
+    five bonds of a further left-to-right pass gbd_probe_step solves the same
+    two-site problem to ||r|| < 1e-8 with each preconditioner, in the FP64
+    tier and in the mixed tiers with FP64 refinement.  One JSON line with
+    Davidson iterations and times; no bench line."""
+    from paper_2609_09990_gb300 import gbdmrg as G
+    import torch
+    ctx = G.Context(0)
+    train = []
+    for name, nsw in (("cas6_m64", 4), ("cas12_m256", 2), ("cas16_m512", 1)):
+        w = WORKLOADS[name]
+        h, chol = make_integrals(w["n_orb"], w["n_chol"], w["seed"])
+        train.append((h, chol, w["n_elec"], 0, [w["M"]] * nsw, [1e-8] * nsw, {"seed": w["seed"]}))
+    t = time.perf_counter()
+    loss = ctx.train_precond(train, epochs=400, lr=3e-3)
+    train_s = time.perf_counter() - t
+    _, _, samples = ctx.davidson_counts()
+    wl = WORKLOADS[args.workload]
+    n, ne, nq, M, seed = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"]
+    h, chol = make_integrals(n, nq, seed)
+    nsw = max(args.warmup, 1)
+    ctx.setup(h, chol, ne, 0, [M] * nsw, [1e-6] * nsw, seed=seed, precision=PREC["bf16"], fp64_refine=0)
+    ctx.init_state()
+    for sweep in range(nsw):
+        ctx.run_sweep(sweep)
+    ks = [int(round(1 + i * (n - 4) / 4)) for i in range(5)]
+    rows = []
+    for k in range(max(ks) + 1):
+        if k in ks:
+            for tier, prec, refine in (("fp64", 0, 0), ("mixed+fp64_refine", PREC["bf16"], 200)):
+                for pc in (0, 1):
+                    ctx.set_preconditioner(pc)
+                    it0 = ctx.davidson_counts()[0]
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    _, e64, r64 = ctx.probe_step(k, prec, refine, 1e-8)
+                    dt = time.perf_counter() - t
+                    rows.append({"bond": k, "tier": tier, "preconditioner": "learned" if pc else "diagonal",
+                                 "iterations": ctx.davidson_counts()[0] - it0, "seconds": dt, "energy": e64,
+                                 "final_residual_fp64": r64})
+            ctx.set_preconditioner(0)
+        ctx.run_step(k, 0, M, 1e-6)
+    ctx.close()
+    summary = {}
+    for tier in ("fp64", "mixed+fp64_refine"):
+        for pc in ("diagonal", "learned"):
+            sel = [r for r in rows if r["tier"] == tier and r["preconditioner"] == pc]
+            summary[f"{tier}/{pc}"] = {"iterations": sum(r["iterations"] for r in sel),
+                                       "seconds": sum(r["seconds"] for r in sel)}
+    de = max(abs(a["energy"] - b["energy"]) for a in rows for b in rows
+             if a["bond"] == b["bond"] and a["tier"] == b["tier"] and a is not b)
+    print(json.dumps({"precond_ab": args.workload, "train_s": train_s, "train_loss": loss, "train_samples": samples,
+                      "warm_sweeps": nsw, "summary": summary, "max_energy_difference_same_problem_Ha": de,
+                      "probes": rows}))
+
+
 def states_run(args):
     """Excited states by penalty deflation on a workload (gbd_solve_states):
     the lowest `--states` roots of any spin (no <S^2> guard), each from its
@@ -599,12 +659,17 @@ def main():
     ap.add_argument("--penalty", type=float, default=2.0, help="deflation penalty (Ha) of --states")
     ap.add_argument("--probe-warm-sweeps", type=int, default=0, help="--sigma-probe on the state after this many "
                     "mixed-precision sweeps (profiler started before the timed builds)")
+    ap.add_argument("--precond-ab", action="store_true", help="learned against diagonal preconditioner on "
+                    "--workload after --warmup sweeps (probe solves to 1e-8; no bench line)")
     ap.add_argument("--precond-probe", type=int, default=0, help="profiling driver: one fused learned-"
                     "preconditioner application on this many elements (no bench line)")
     ap.add_argument("--probe-davidson", action="store_true", help="--sigma-probe: one mixed-precision Davidson "
                     "solve at the central bond instead of the sigma builds")
     ap.add_argument("--probe-orders", default="0", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2")
     args = ap.parse_args()
+    if args.precond_ab:
+        precond_ab(args)
+        return
     if args.precond_probe:
         precond_probe(args.precond_probe)
         return

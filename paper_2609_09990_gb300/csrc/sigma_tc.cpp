@@ -589,16 +589,29 @@ TcPlan* Engine::tc_plan(const EnlOp& lenl, const EnlOp& renl, int prec) {
 TcPlan* Engine::tc_plan_impl(const EnlOp& lenl, const EnlOp& renl, int prec) {
   if (tc_fixed_cap) return tc_build(lenl, renl, prec, TcTune{{tc_fixed_cap, tc_fixed_cap}});
   if (!autotune) return tc_build(lenl, renl, prec, TcTune());
+  // shape class: operand type, size of the two-site state, number of Renl
+  // sub-blocks, and how that size is spread over the sectors (the effective
+  // number of sectors (sum_Q w_Q)^2 / sum_Q w_Q^2, w_Q = E_L(Q) E_R(Q)): a
+  // state of the same size in a few large sectors tiles differently from one
+  // spread over many small ones
   auto lg = [](double x) { return (int64_t)std::lround(2.0 * std::log2(std::max(x, 1.0))); };
-  const int64_t ka = lg((double)psi_size), kb = lg((double)renl.subs.size());
-  const int64_t key = ((int64_t)prec << 40) | (ka << 20) | kb;
+  double w1 = 0, w2 = 0;
+  for (int q = 0; q < EL.n(); ++q) {
+    const double w = (double)EL.dim[q] * ER.dim[q];
+    w1 += w;
+    w2 += w * w;
+  }
+  const int64_t ka = lg((double)psi_size), kb = lg((double)renl.subs.size()), ks = lg(w2 > 0 ? w1 * w1 / w2 : 1.0);
+  const int64_t key = ((int64_t)prec << 48) | (ka << 32) | (kb << 16) | ks;
   auto it = tuned.find(key);
   if (it != tuned.end()) return tc_build(lenl, renl, prec, it->second);
-  // a class within two half-octave buckets of a tuned one takes its shape
-  // (sizes drift from sweep to sweep; tuning again would cost more than it gains)
+  // a class within two half-octave buckets of a tuned one in every feature
+  // takes its shape (sizes drift from sweep to sweep; tuning again would
+  // cost more than it gains)
   for (const auto& kv : tuned) {
-    const int64_t p2 = kv.first >> 40, a2 = (kv.first >> 20) & 0xFFFFF, b2 = kv.first & 0xFFFFF;
-    if (p2 == prec && std::llabs(a2 - ka) <= 2 && std::llabs(b2 - kb) <= 2) {
+    const int64_t p2 = kv.first >> 48, a2 = (kv.first >> 32) & 0xFFFF, b2 = (kv.first >> 16) & 0xFFFF,
+                  s2 = kv.first & 0xFFFF;
+    if (p2 == prec && std::llabs(a2 - ka) <= 2 && std::llabs(b2 - kb) <= 2 && std::llabs(s2 - ks) <= 2) {
       tuned[key] = kv.second;
       return tc_build(lenl, renl, prec, kv.second);
     }
