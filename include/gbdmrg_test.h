@@ -61,6 +61,8 @@ typedef struct {
   double sweep_max_residual;      /* largest final ||r|| of the current or last sweep */
   double enlarge_dev_ms;          /* device time of the block-axpy launches forming the enlarged operators */
   double enlarge_bytes;           /* their algorithmic bytes: 8 (terms + 1) per output element */
+  double rdm_ms;                  /* wall time of the last gbd_rdms (or RDMs of a solve) */
+  double rdm_env_bytes;           /* peak device bytes of its operator-string environments */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or
@@ -174,15 +176,24 @@ int gbd_apply_heff_prec(gbd_ctx *ctx, int32_t k, int32_t prec, const double *in,
 int gbd_run_step(gbd_ctx *ctx, int32_t k, int32_t dir, int32_t M, double tol, double *energy,
                  double *discarded, double *kept, int32_t cap, int32_t *nkept);
 /* One- and two-particle RDMs of the current MPS (conventions of
- * gbd_result); rdm1 [n^2], rdm2 [n^4] or NULL. */
+ * gbd_result); rdm1 [n^2], rdm2 [n^4] or NULL.  Contracted through the MPS
+ * (operator-string environments, cost polynomial in n and M; device FP64
+ * environments of at most a few GB at n = 20, M = 1024). */
 int gbd_rdms(gbd_ctx *ctx, double *rdm1, double *rdm2);
+/* The same RDMs from the determinant expansion of the MPS (an independent
+ * route for cross-checks); GBD_ERR_ARG above 4e8 determinants. */
+int gbd_rdms_ci(gbd_ctx *ctx, double *rdm1, double *rdm2);
 /* One- and two-orbital reduced density matrices of the current MPS (the
  * inputs of gbd_orbital_entropies): rho1 [n][4][4] in the local basis |0>,
  * |alpha>, |beta>, |alpha beta> = c+_alpha^x c+_beta^y |vac> (index x + 2y);
  * rho2 [n(n-1)/2][16][16] for the pairs (i < j) in lexicographic order, pair
  * index x_i + 4 x_j with the modes of i before those of j.  Either may be
- * NULL. */
+ * NULL.  Contracted through the MPS, like gbd_rdms: entries that connect
+ * different particle numbers are exactly zero and not computed. */
 int gbd_orbital_rdms(gbd_ctx *ctx, double *rho1, double *rho2);
+/* The same from the determinant expansion (GBD_ERR_ARG above 4e8
+ * determinants), for cross-checks. */
+int gbd_orbital_rdms_ci(gbd_ctx *ctx, double *rho1, double *rho2);
 /* MPO channel keys of one bond (kind<<40 | nops<<32 | code0<<16 | code1). */
 int gbd_mpo_labels(gbd_ctx *ctx, int32_t bond, uint64_t *keys, int32_t cap, int32_t *count);
 /* One environment block (side 0 = left, 1 = right) for (channel, sector index). */

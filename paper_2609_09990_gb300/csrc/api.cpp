@@ -632,6 +632,22 @@ int gbd_rdms(gbd_ctx* ctx, double* rdm1, double* rdm2) {
   });
 }
 
+int gbd_rdms_ci(gbd_ctx* ctx, double* rdm1, double* rdm2) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    ctx->eng->rdms_ci(rdm1, rdm2);
+    return GBD_OK;
+  });
+}
+
+int gbd_orbital_rdms_ci(gbd_ctx* ctx, double* rho1, double* rho2) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || !ctx->eng->prepared) return fail(ctx, GBD_ERR_STATE, "no state");
+    ctx->eng->orbital_rdms_ci(rho1, rho2);
+    return GBD_OK;
+  });
+}
+
 int gbd_rdm3(gbd_ctx* ctx, double* rdm3) {
   return guarded(ctx, [&]() {
     if (!rdm3) return fail(ctx, GBD_ERR_ARG, "rdm3 is NULL");
@@ -875,6 +891,8 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->sweep_max_residual = t.sweep_max_residual;
   s->enlarge_dev_ms = t.enl_dev_ms;
   s->enlarge_bytes = t.enl_bytes;
+  s->rdm_ms = t.rdm_ms;
+  s->rdm_env_bytes = t.rdm_env_bytes;
   for (int i = 0; i < 2; ++i) {
     s->tc_stage_alg_bytes[i] = t.tc_alg_st[i];
     s->tc_stage_box_bytes[2 * i] = t.tc_box_st[i][0];

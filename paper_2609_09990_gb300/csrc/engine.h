@@ -98,6 +98,7 @@ struct Stats {
   double env_wall_ms = 0;   // environment update: upload (plan checks) + kernels, wall
   double enl_dev_ms = 0, enl_bytes = 0;   // block-axpy launches of the enlarged operators: device time, bytes
   double tcb_ms[5] = {0, 0, 0, 0, 0};   // plan-build phases: layout/groups, panels, tiles, upload, maps
+  double rdm_ms = 0, rdm_env_bytes = 0;   // last rdms(): wall time, peak bytes of its environments
   void add(const Stats& o) {   // sum of the additive counters (batched solves)
     sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
     enl_ms += o.enl_ms; step_ms += o.step_ms; trunc_ms += o.trunc_ms; davidson_ms += o.davidson_ms;
@@ -123,6 +124,7 @@ struct Stats {
     tc_gemm_ms += o.tc_gemm_ms; tc_bytes += o.tc_bytes; tc_build_ms += o.tc_build_ms; enl_host_ms += o.enl_host_ms; diag_ms += o.diag_ms;
     trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms; env_wall_ms += o.env_wall_ms;
     enl_dev_ms += o.enl_dev_ms; enl_bytes += o.enl_bytes;
+    rdm_ms += o.rdm_ms; rdm_env_bytes = std::max(rdm_env_bytes, o.rdm_env_bytes);
     for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
     for (int i = 0; i < 4; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
     max_discarded = std::max(max_discarded, o.max_discarded);
@@ -152,6 +154,10 @@ struct GraphSeq {   // one captured launch sequence (see Engine::replay)
   int calls = 0;
 };
 
+namespace opstr {
+struct StringSet;
+}
+
 class Engine {
  public:
   explicit Engine(int device);
@@ -161,16 +167,25 @@ class Engine {
   void init_state();       // initial MPS and environments
   double sweep(int s);     // returns the Ritz value of the last step
   double final_energy();
+  // spin-summed 1-/2-RDMs of the current MPS, contracted through the MPS
+  // (operator-string environments; rdm_mps.cpp)
   void rdms(double* rdm1, double* rdm2);
+  // the same from the determinant expansion (at most 4e8 determinants)
+  void rdms_ci(double* rdm1, double* rdm2);
   // spin-summed 3-RDM [n^6] of the current MPS (determinant expansion;
   // needs 2 n^2 determinant-length vectors on the device)
   void rdm3(double* out);
   // one- and two-orbital reduced density matrices of the current MPS:
   // rho1 [n][4][4], rho2 [n(n-1)/2][16][16] for the pairs (i<j) in
   // lexicographic order (local basis of orbital i: |0>, |a>, |b>, |ab> =
-  // c+_a^x c+_b^y |vac>; pair basis index 4 x_i + x_j with the modes of i
-  // before those of j)
+  // c+_a^x c+_b^y |vac>, index x + 2y; pair basis index x_i + 4 x_j with the
+  // modes of i before those of j), contracted through the MPS (rdm_mps.cpp)
   void orbital_rdms(double* rho1, double* rho2);
+  // the same from the determinant expansion
+  void orbital_rdms_ci(double* rho1, double* rho2);
+  // values <psi|O|psi> / <psi|psi> of many Jordan-Wigner operator strings
+  // through operator-string environments (rdm_mps.cpp)
+  std::vector<double> eval_strings(opstr::StringSet& S);
   // excited states by penalty deflation: the converged lower states stay
   // resident (both site layouts) and enter every two-site step through
   // overlap environments; sigma gains w sum_j phi_j (phi_j . x) and the
@@ -308,6 +323,7 @@ class Engine {
     return (T*)p;
   }
   void check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, const char* what) const;
+  const double* site_block(int i, int qi, int s, int& ld) const;
   void check(const GemmPlan& p) const;
   void check(const AxpyPlan& p) const;
   void dfree(void* p);

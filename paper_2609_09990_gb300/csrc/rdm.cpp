@@ -89,6 +89,34 @@ std::vector<int> excitations(int n, int k) {
 
 }  // namespace
 
+// site block X_i(q, s): m_i(q) x m_{i+1}(q+s), row-major with leading
+// dimension ld, inside either site layout; nullptr if q + s is no sector
+const double* Engine::site_block(int i, int qi, int s, int& ld) const {
+  const Bond& bl = bonds[i];
+  const Bond& br = bonds[i + 1];
+  const Site& S = sites[i];
+  int r = br.find(bl.na[qi] + QA[s], bl.nb[qi] + QB[s]);
+  if (r < 0) return nullptr;
+  if (S.layout == 1) {
+    int coff = 0, cols = 0;
+    for (int t = 0; t < 4; ++t) {
+      int rr = br.find(bl.na[qi] + QA[t], bl.nb[qi] + QB[t]);
+      if (rr < 0) continue;
+      if (t < s) coff += br.dim[rr];
+      cols += br.dim[rr];
+    }
+    ld = cols;
+    return S.d + S.off[qi] + coff;
+  }
+  int roff = 0;
+  for (int t = 0; t < s; ++t) {
+    int jj = bl.find(br.na[r] - QA[t], br.nb[r] - QB[t]);
+    if (jj >= 0) roff += bl.dim[jj];
+  }
+  ld = br.dim[r];
+  return S.d + S.off[r] + (int64_t)roff * br.dim[r];
+}
+
 // The current MPS expanded into the determinant basis: C[Ia * Nb_str + Ib]
 // (device, caller frees), not normalised.
 double* Engine::expand_ci(int64_t& Na_str, int64_t& Nb_str) {
@@ -97,32 +125,8 @@ double* Engine::expand_ci(int64_t& Na_str, int64_t& Nb_str) {
   Nb_str = (int64_t)binom_i(n, Nb);
   const int64_t ndet = Na_str * Nb_str;
   if (ndet > (int64_t)400000000) throw Error(-1, "RDMs need the determinant expansion; too many determinants");
-  // site block X_i(q, s): m_i(q) x m_{i+1}(q+s) with its leading dimension
-  auto block = [&](int i, int qi, int s, int& ld) -> const double* {
-    const Bond& bl = bonds[i];
-    const Bond& br = bonds[i + 1];
-    const Site& S = sites[i];
-    int r = br.find(bl.na[qi] + QA[s], bl.nb[qi] + QB[s]);
-    if (r < 0) return nullptr;
-    if (S.layout == 1) {
-      int coff = 0, cols = 0;
-      for (int t = 0; t < 4; ++t) {
-        int rr = br.find(bl.na[qi] + QA[t], bl.nb[qi] + QB[t]);
-        if (rr < 0) continue;
-        if (t < s) coff += br.dim[rr];
-        cols += br.dim[rr];
-      }
-      ld = cols;
-      return S.d + S.off[qi] + coff;
-    }
-    int roff = 0;
-    for (int t = 0; t < s; ++t) {
-      int jj = bl.find(br.na[r] - QA[t], br.nb[r] - QB[t]);
-      if (jj >= 0) roff += bl.dim[jj];
-    }
-    ld = br.dim[r];
-    return S.d + S.off[r] + (int64_t)roff * br.dim[r];
-  };
+  auto block = [&](int i, int qi, int s, int& ld) { return site_block(i, qi, s, ld); };
+
   // ---- prefixes (sites < h), rows of P_i(q)
   struct Fix { std::vector<uint32_t> a, b; double* d = nullptr; };
   std::vector<Fix> pre(1);
@@ -279,7 +283,7 @@ double* Engine::expand_ci(int64_t& Na_str, int64_t& Nb_str) {
   return C;
 }
 
-void Engine::rdms(double* rdm1, double* rdm2) {
+void Engine::rdms_ci(double* rdm1, double* rdm2) {
   int64_t Na_str = 0, Nb_str = 0;
   double* C = expand_ci(Na_str, Nb_str);
   const int64_t ndet = Na_str * Nb_str;
@@ -474,7 +478,7 @@ void Engine::rdm3(double* out) {
 // "Cholesky decomposition for the wavefunction", ingredient (ii)): rho_ij
 // from the determinant expansion by pair_rdm_kernel (fermionic partial trace
 // with the pair's modes moved to the front), rho_i as its partial trace.
-void Engine::orbital_rdms(double* rho1, double* rho2) {
+void Engine::orbital_rdms_ci(double* rho1, double* rho2) {
   int64_t NaS = 0, NbS = 0;
   double* C = expand_ci(NaS, NbS);
   const int64_t ndet = NaS * NbS;

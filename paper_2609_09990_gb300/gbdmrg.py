@@ -60,7 +60,8 @@ class gbd_stats(C.Structure):
                 ("tc_stage_dense_bytes", C.c_double * 4), ("tc_gemm_ms_by_stage", C.c_double * 2),
                 ("davidson_iterations", C.c_int64), ("inner_matvecs", C.c_int64), ("n_solves", C.c_int64),
                 ("n_solves_above_tol", C.c_int64), ("sweep_max_residual", C.c_double),
-                ("enlarge_dev_ms", C.c_double), ("enlarge_bytes", C.c_double)]
+                ("enlarge_dev_ms", C.c_double), ("enlarge_bytes", C.c_double),
+                ("rdm_ms", C.c_double), ("rdm_env_bytes", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -123,6 +124,8 @@ def lib():
         "gbd_run_step": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, _dp, _dp, _dp,
                                    C.c_int32, _ip]),
         "gbd_rdms": (C.c_int, [vp, _dp, _dp]),
+        "gbd_rdms_ci": (C.c_int, [vp, _dp, _dp]),
+        "gbd_orbital_rdms_ci": (C.c_int, [vp, _dp, _dp]),
         "gbd_rdm3": (C.c_int, [vp, _dp]),
         "gbd_orbital_rdms": (C.c_int, [vp, _dp, _dp]),
         "gbd_orbital_entropies": (C.c_int, [vp, _dp, _dp]),
@@ -406,6 +409,13 @@ class Context:
         self._check(self.L.gbd_rdms(self.ptr, _d(r1), _d(r2)), "gbd_rdms")
         return r1, r2
 
+    def rdms_ci(self, n):
+        """gbd_rdms_ci: the same RDMs from the determinant expansion."""
+        r1 = np.zeros((n, n))
+        r2 = np.zeros((n, n, n, n))
+        self._check(self.L.gbd_rdms_ci(self.ptr, _d(r1), _d(r2)), "gbd_rdms_ci")
+        return r1, r2
+
     def rdm3(self, n):
         """gbd_rdm3: the spin-summed 3-RDM [n]*6 of the current state."""
         out = np.zeros((n,) * 6)
@@ -417,6 +427,13 @@ class Context:
         r1 = np.zeros((n, 4, 4))
         r2 = np.zeros((max(n * (n - 1) // 2, 1), 16, 16))
         self._check(self.L.gbd_orbital_rdms(self.ptr, _d(r1), _d(r2)), "gbd_orbital_rdms")
+        return r1, r2[:n * (n - 1) // 2]
+
+    def orbital_rdms_ci(self, n):
+        """gbd_orbital_rdms_ci: the same from the determinant expansion."""
+        r1 = np.zeros((n, 4, 4))
+        r2 = np.zeros((max(n * (n - 1) // 2, 1), 16, 16))
+        self._check(self.L.gbd_orbital_rdms_ci(self.ptr, _d(r1), _d(r2)), "gbd_orbital_rdms_ci")
         return r1, r2[:n * (n - 1) // 2]
 
     def orbital_entropies(self, n):
