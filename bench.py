@@ -241,18 +241,30 @@ def run_ours(args, rank, world):
     rdm_times = None
     if args.rdms:
         # RDMs of the current state, each timed on its own (device work
-        # synchronised by the call): 1-/2-RDM, orbital entropies and mutual
-        # information, and the 3-RDM where its 2 n^2 determinant-length
-        # vectors fit
+        # synchronised by the call): 1-/2-RDM and orbital entropies with
+        # mutual information, contracted through the MPS; where the
+        # determinant expansion fits, the same RDMs by that route (time and
+        # largest difference) and the 3-RDM where its 2 n^2
+        # determinant-length vectors fit
         from math import comb
         rdm_times = {}
+        e_final = ctx.final_energy()
         t = time.perf_counter()
         g1, g2 = ctx.rdms(n)
         rdm_times["rdm12_s"] = time.perf_counter() - t
+        rdm_times["rdm12_env_gb"] = ctx.stats()["rdm_env_bytes"] / 1e9
+        eri = np.einsum("Qpq,Qrs->pqrs", chol, chol)
+        e_rdm = float(np.einsum("pq,pq", h, g1) + 0.5 * np.einsum("pqrs,pqrs", eri, g2))
+        rdm_times["energy_from_rdms_minus_energy"] = e_rdm - e_final
         t = time.perf_counter()
         s1, mi = ctx.orbital_entropies(n)
         rdm_times["orbital_entropies_s"] = time.perf_counter() - t
         ndet = comb(n, ne // 2) ** 2
+        if ndet <= 4e8:
+            t = time.perf_counter()
+            c1, c2 = ctx.rdms_ci(n)
+            rdm_times["rdm12_determinant_route_s"] = time.perf_counter() - t
+            rdm_times["routes_max_abs_diff"] = float(max(np.abs(g1 - c1).max(), np.abs(g2 - c2).max()))
         if 2 * n * n * ndet * 8 <= 64e9:
             t = time.perf_counter()
             ctx.rdm3(n)
