@@ -57,7 +57,7 @@ METRIC = "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u2
 # of algorithmic bytes).  The launches of a sweep move the same kinds of
 # panels, so traffic is reported as this ratio times their algorithmic bytes
 # per launch.
-TC_DRAM_PER_ALG_BYTE = (1051.665152e6 + 928.384512e6 + 2761.424384e6 + 160.108032e6) / 2359843136.0
+TC_DRAM_PER_ALG_BYTE = (1051.977984e6 + 928.156672e6 + 1963.578112e6 + 149.253376e6) / 2359843136.0
 DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
 
 
@@ -384,7 +384,7 @@ def run_batched(args, rank, world):
                 load_imbalance=float(load.max() / load.mean()) if load.size else 1.0)
 
 
-def sigma_probe(prec, orders=(0,), warm_sweeps=0, davidson=False):
+def sigma_probe(prec, orders=(1,), warm_sweeps=0, davidson=False):
     """Profiling driver for the tensor-core sigma: CAS(16,16) M=512, initial
     state (or, with warm_sweeps > 0, the state after that many sweeps in the
     mixed tiers), steps up to the central bond (7,8), then three sigma builds
@@ -677,7 +677,8 @@ def main():
                     "preconditioner application on this many elements (no bench line)")
     ap.add_argument("--probe-davidson", action="store_true", help="--sigma-probe: one mixed-precision Davidson "
                     "solve at the central bond instead of the sigma builds")
-    ap.add_argument("--probe-orders", default="0", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2")
+    ap.add_argument("--probe-orders", default="1", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2 "
+                    "(1 is the library's default)")
     args = ap.parse_args()
     if args.precond_ab:
         precond_ab(args)
