@@ -117,6 +117,23 @@ int gbd_set_tier_stop(gbd_ctx *ctx, double floor_mult, int32_t hard_stag);
  * GBD_ERR_ARG for another prec. */
 int gbd_set_env_precision(gbd_ctx *ctx, int32_t prec);
 
+/* Environment updates compute one channel of each certified
+ * Hermitian-conjugate pair and fill the other with its transpose times the
+ * pair's sign (enable = 1, the default), or compute every channel
+ * (enable = 0).  Certification (at gbd_setup, from the MPO's W tensors):
+ * L[d] = sign L[c]^T holds for every MPS because W's column d equals the
+ * transposed, conjugate-relabelled column c times sign, inductively from
+ * bond 0 (right environments: W's rows, from bond n).  GBD_ERR_ARG for
+ * another enable. */
+int gbd_set_env_conjugates(gbd_ctx *ctx, int32_t enable);
+/* The certified pairs of one bond (side 0 = left environments, 1 = right):
+ * partner[c] = the conjugate channel (c for a self-conjugate or zero
+ * channel, -1 when none is certified), sign[c] its sign; count = channels
+ * of the bond (buffers of cap entries, either may be NULL).
+ * GBD_ERR_STATE before gbd_setup. */
+int gbd_env_conjugates(gbd_ctx *ctx, int32_t side, int32_t bond, int32_t *partner, int32_t *sign, int32_t cap,
+                       int32_t *count);
+
 /* Reduced-precision schedules solve steps whose two-site state has fewer
  * than n elements (chain ends) in FP64: there the tensor-core plan costs
  * more than it saves.  Default 4096; 0 = always the tensor-core tiers. */
@@ -316,6 +333,13 @@ int gbd_host_select(int32_t count, const double *lam, const int32_t *key, const 
  * |s_0 ... s_{n-1}> (site 0 most significant). */
 int gbd_host_mpo(int32_t n, const double *h, int32_t n_chol, const double *chol, int32_t k_switch,
                  int32_t *bond_dims, double *dense);
+/* The certified Hermitian-conjugate channel pairs of the MPO of (h, chol)
+ * at one bond, as gbd_env_conjugates reports them for a context (side 0 =
+ * left environments, 1 = right); host only.  GBD_ERR_ARG for bad sizes or a
+ * buffer smaller than the bond's channel count. */
+int gbd_host_mpo_conjugates(int32_t n, const double *h, int32_t n_chol, const double *chol, int32_t k_switch,
+                            int32_t side, int32_t bond, int32_t *partner, int32_t *sign, int32_t cap,
+                            int32_t *count);
 
 #ifdef __cplusplus
 }

@@ -422,6 +422,36 @@ int gbd_set_env_precision(gbd_ctx* ctx, int32_t prec) {
   });
 }
 
+int gbd_set_env_conjugates(gbd_ctx* ctx, int32_t enable) {
+  return guarded(ctx, [&]() {
+    if (enable != 0 && enable != 1) return fail(ctx, GBD_ERR_ARG, "enable must be 0 or 1");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->env_conj = enable != 0;
+    return GBD_OK;
+  });
+}
+
+int gbd_env_conjugates(gbd_ctx* ctx, int32_t side, int32_t bond, int32_t* partner, int32_t* sign, int32_t cap,
+                       int32_t* count) {
+  return guarded(ctx, [&]() {
+    if (!ctx->eng || ctx->eng->conj_l.empty()) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");
+    gbd::Engine& e = *ctx->eng;
+    if (side != 0 && side != 1) return fail(ctx, GBD_ERR_ARG, "side must be 0 (left) or 1 (right)");
+    if (bond < 0 || bond > e.n) return fail(ctx, GBD_ERR_ARG, "bond out of range");
+    const auto& c = side == 0 ? e.conj_l[bond] : e.conj_r[bond];
+    const auto& sg = side == 0 ? e.sign_l[bond] : e.sign_r[bond];
+    if (count) *count = (int)c.size();
+    if (partner || sign) {
+      if (cap < (int)c.size()) return fail(ctx, GBD_ERR_ARG, "buffer too small");
+      for (size_t i = 0; i < c.size(); ++i) {
+        if (partner) partner[i] = c[i];
+        if (sign) sign[i] = sg[i];
+      }
+    }
+    return GBD_OK;
+  });
+}
+
 int gbd_gemm_tc_selftest(gbd_ctx* ctx, int32_t M, int32_t N, int32_t K, int32_t nterms, int32_t flags, int32_t prec,
                          uint64_t seed, double* max_err, double* max_ref) {
   return guarded(ctx, [&]() {
@@ -1003,6 +1033,36 @@ int gbd_host_mpo(int32_t n, const double* h, int32_t n_chol, const double* chol,
         dim = nd;
       }
       for (size_t i = 0; i < (size_t)dim * dim; ++i) dense[i] = env[0].empty() ? 0.0 : env[0][i];
+    }
+    return GBD_OK;
+  } catch (...) {
+    return GBD_ERR_ARG;
+  }
+}
+
+int gbd_host_mpo_conjugates(int32_t n, const double* h, int32_t n_chol, const double* chol, int32_t k_switch,
+                            int32_t side, int32_t bond, int32_t* partner, int32_t* sign, int32_t cap, int32_t* count) {
+  if (n < 1 || n > 32 || !h || (n_chol > 0 && !chol) || (side != 0 && side != 1) || bond < 0 || bond > n)
+    return GBD_ERR_ARG;
+  try {
+    std::vector<double> eri((size_t)n * n * n * n, 0.0);
+    for (int Q = 0; Q < n_chol; ++Q)
+      for (int pq = 0; pq < n * n; ++pq)
+        for (int rs = 0; rs < n * n; ++rs)
+          eri[(size_t)pq * n * n + rs] += chol[(size_t)Q * n * n + pq] * chol[(size_t)Q * n * n + rs];
+    gbd::Mpo m;
+    gbd::build_mpo(n, h, eri.data(), k_switch, m);
+    std::vector<std::vector<int>> cl, sl, cr, sr;
+    gbd::mpo_conjugates(m, cl, sl, cr, sr);
+    const auto& c = side == 0 ? cl[bond] : cr[bond];
+    const auto& sg = side == 0 ? sl[bond] : sr[bond];
+    if (count) *count = (int)c.size();
+    if (partner || sign) {
+      if (cap < (int)c.size()) return GBD_ERR_ARG;
+      for (size_t i = 0; i < c.size(); ++i) {
+        if (partner) partner[i] = c[i];
+        if (sign) sign[i] = sg[i];
+      }
     }
     return GBD_OK;
   } catch (...) {

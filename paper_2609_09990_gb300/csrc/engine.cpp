@@ -934,6 +934,7 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
   for (int key = 0; key < groups.nkeys; ++key) {
     if (groups.start[key] == groups.start[key + 1]) continue;
     const int b = key / groups.nq, qin = key % groups.nq;
+    if (env_derived(bond, b, true)) continue;   // filled by the transpose of its partner
     int jin = bnew.find(el.qa[qin], el.qb[qin]);
     if (jin < 0) continue;
     int qout = lenl.subs[groups.idx[groups.start[key]]].qout;
@@ -964,9 +965,63 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
   }
   const double th0 = now_ms();
   timed_env_launch(p1, p2);
+  env_transposes(out, bond, true);
   stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
   dfree(T);
+}
+
+// a derived channel of an environment update: its certified Hermitian
+// partner has a lower index, so its blocks are that partner's transposed
+bool Engine::env_derived(int bond, int c, bool left) const {
+  if (!env_conj) return false;
+  const auto& cj = left ? conj_l : conj_r;
+  if (bond >= (int)cj.size() || c >= (int)cj[bond].size()) return false;
+  const int d = cj[bond][c];
+  return d >= 0 && d < c;
+}
+
+// out[d](q' <- q) = sign out[c](q <- q')^T for every derived channel d of
+// the bond (partner c, computed by the launch before), one tile list
+void Engine::env_transposes(Env& out, int bond, bool left) {
+  if (!env_conj) return;
+  const auto& cj = left ? conj_l : conj_r;
+  const auto& sg = left ? sign_l : sign_r;
+  const Bond& bd = bonds[bond];
+  std::vector<TransTask> tasks;
+  std::vector<TransTile> tiles;
+  for (int d = 0; d < out.nch; ++d) {
+    if (!env_derived(bond, d, left)) continue;
+    const int c = cj[bond][d];
+    for (int q = 0; q < out.nsec; ++q) {
+      const int64_t od = out.at(d, q);
+      if (od < 0) continue;
+      const int qo = bd.find(bd.na[q] + mpo.dA[bond][d], bd.nb[q] + mpo.dB[bond][d]);
+      const int64_t oc = qo >= 0 ? out.at(c, qo) : -1;
+      if (oc < 0) throw Error(-6, "conjugate channel block missing");
+      const int rows = bd.dim[q], cols = bd.dim[qo];   // the partner's block (q <- q')
+      const int t = (int)tasks.size();
+      tasks.push_back({out.d + oc, out.d + od, rows, cols, (double)sg[bond][d]});
+      for (int r0 = 0; r0 < rows; r0 += 32)
+        for (int c0 = 0; c0 < cols; c0 += 32) tiles.push_back({t, r0, c0, 0});
+    }
+  }
+  if (tiles.empty()) return;
+  for (const TransTask& t : tasks) {
+    check_range(t.src, t.rows, t.cols, t.cols, "transpose src");
+    check_range(t.dst, t.cols, t.rows, t.rows, "transpose dst");
+  }
+  TransTask* d_tasks = dalloc<TransTask>(tasks.size());
+  TransTile* d_tiles = dalloc<TransTile>(tiles.size());
+  h2d(d_tasks, tasks.data(), tasks.size() * sizeof(TransTask));
+  h2d(d_tiles, tiles.data(), tiles.size() * sizeof(TransTile));
+  EnvTimer tm = timer_begin(&stats.env_ms);
+  launch_block_transpose(d_tasks, d_tiles, (int)tiles.size(), stream);
+  stats.launches++;
+  CK(cudaGetLastError());
+  timer_end(tm);
+  dfree(d_tasks);
+  dfree(d_tiles);
 }
 
 // a pair of timing events around device work on the engine stream; the
@@ -1025,6 +1080,7 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
   for (int key = 0; key < groups.nkeys; ++key) {
     if (groups.start[key] == groups.start[key + 1]) continue;
     const int b = key / groups.nq, qin = key % groups.nq;
+    if (env_derived(bond, b, false)) continue;   // filled by the transpose of its partner
     int jin = bnew.find(er.qa[qin], er.qb[qin]);
     if (jin < 0) continue;
     int qout = renl.subs[groups.idx[groups.start[key]]].qout;
@@ -1055,6 +1111,7 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
   }
   const double th0 = now_ms();
   timed_env_launch(p1, p2);
+  env_transposes(out, bond, false);
   stats.env_wall_ms += now_ms() - th0;
   stats.env_flops += p1.flops + p2.flops;
   dfree(T);
@@ -2062,6 +2119,7 @@ void Engine::prepare(int n_, int n_elec, int two_sz, int n_chol, const double* h
     }
   }
   build_mpo(n, h.data(), eri.data(), n / 2, mpo);
+  mpo_conjugates(mpo, conj_l, sign_l, conj_r, sign_r);
   clear_states();   // deflated states and a saved MPS belong to the previous problem
   free_snapshot();
   stats = Stats();

@@ -245,6 +245,13 @@ class Engine {
   int env_prec = -1;
   bool env_tc_used = false;   // the right environments hold tensor-core updates
   bool force_fp64_env = false;
+  // certified Hermitian-conjugate channel pairs of the MPO (mpo_conjugates):
+  // an environment update computes one channel of each pair and transposes
+  // it into the other (env_conj = false: every channel computed)
+  std::vector<std::vector<int>> conj_l, sign_l, conj_r, sign_r;
+  bool env_conj = true;
+  bool env_derived(int bond, int c, bool left) const;
+  void env_transposes(Env& out, int bond, bool left);
   // stopping of the accurate tier: a plateau (no 30 % drop over 3
   // iterations) ends it below tier2_floor_mult * u2 * max(1, |theta|);
   // hard_stag_iters > 0: no 30 % drop over that many iterations ends it at

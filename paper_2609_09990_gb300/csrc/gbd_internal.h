@@ -78,6 +78,11 @@ struct Mpo {
 };
 
 void build_mpo(int n, const double* h, const double* eri, int k_switch, Mpo& out);
+// certified Hermitian-conjugate channel pairs per bond: cl/cr[bond][c] = the
+// partner d with L[d] = sl[c] L[c]^T (R[d] = sr[c] R[c]^T), c itself for a
+// self-conjugate or zero channel, -1 when none is certified
+void mpo_conjugates(const Mpo& m, std::vector<std::vector<int>>& cl, std::vector<std::vector<int>>& sl,
+                    std::vector<std::vector<int>>& cr, std::vector<std::vector<int>>& sr);
 
 // ---------------------------------------------------------------- grouped GEMM
 // C[out] = beta * C + sum_terms alpha * op(A) op(B), op = transpose if flag.
@@ -143,6 +148,11 @@ constexpr int kAxpyChunk = 1024;   // output elements per work chunk of the bloc
 void launch_gemm_f64(const GemmPlan& p, cudaStream_t s);
 void launch_axpy(const AxpyPlan& p, cudaStream_t s);
 void launch_set_identity(double* d, int m, cudaStream_t s);
+// dst = sign * src^T for blocks src (rows x cols, row-major, dense); one
+// 32 x 32 tile per item
+struct TransTask { const double* src; double* dst; int32_t rows, cols; double sign; };
+struct TransTile { int32_t task, r0, c0, pad; };
+void launch_block_transpose(const TransTask* tasks, const TransTile* tiles, int ntiles, cudaStream_t s);
 // Davidson vector ops (vectors V_j = V + j * stride)
 void launch_multi_dot(const double* V, int64_t stride, int k, const double* x, int64_t n, double* out_dev,
                       double* partial, int nblk, cudaStream_t s);

@@ -336,6 +336,30 @@ void launch_axpy(const AxpyPlan& p, cudaStream_t s) {
   axpy_kernel<<<(int)grid, kAxpyThreads, 0, s>>>(p.d_terms, p.d_outs, p.d_cstart, no, p.nchunks);
 }
 
+// dst = sign * src^T, one 32 x 32 tile of one task per CTA: coalesced reads
+// of src rows into shared memory, coalesced writes of dst rows
+__global__ void __launch_bounds__(256)
+block_transpose_kernel(const TransTask* __restrict__ tasks, const TransTile* __restrict__ tiles) {
+  __shared__ double t[32][33];
+  const TransTile tl = tiles[blockIdx.x];
+  const TransTask T = tasks[tl.task];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = tl.r0 + i, c = tl.c0 + tx;
+    if (r < T.rows && c < T.cols) t[i][tx] = T.src[(int64_t)r * T.cols + c];
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int c = tl.c0 + j, r = tl.r0 + tx;   // dst row c, column r
+    if (r < T.rows && c < T.cols) T.dst[(int64_t)c * T.rows + r] = T.sign * t[tx][j];
+  }
+}
+
+void launch_block_transpose(const TransTask* tasks, const TransTile* tiles, int ntiles, cudaStream_t s) {
+  if (ntiles <= 0) return;
+  block_transpose_kernel<<<ntiles, 256, 0, s>>>(tasks, tiles);
+}
+
 void launch_set_identity(double* d, int m, cudaStream_t s) {
   set_identity_kernel<<<grid_for((int64_t)m * m, 256), 256, 0, s>>>(d, m);
 }

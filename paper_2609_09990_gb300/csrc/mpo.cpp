@@ -19,6 +19,8 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -235,6 +237,90 @@ void build_mpo(int n, const double* h, const double* eri, int k_switch, Mpo& out
       return x.sin < y.sin;
     });
     out.W[i] = std::move(ent);
+  }
+}
+
+// Hermitian-conjugate channel pairs, certified from the W tensors.  For a
+// real MPS, L_b[c]^T = <L|O_c^T|L>: if every left environment at bond k
+// satisfies L_k[conj a] = sign_a L_k[a]^T (bond 0: only the identity is
+// nonzero), then L_{k+1}[d] = sign L_{k+1}[c]^T whenever W_k's column d
+// equals sign times column c with each entry (a, s', s, v) replaced by
+// (conj a, s, s', sign_a v).  Right environments follow the same rule on
+// W_k's rows from bond n (only the H channel nonzero) down.  Channels whose
+// column (row) has no such partner, or whose coefficients differ in the last
+// bit, stay unpaired (-1) and are computed; so do self-conjugate ones.
+void mpo_conjugates(const Mpo& m, std::vector<std::vector<int>>& cl, std::vector<std::vector<int>>& sl,
+                    std::vector<std::vector<int>>& cr, std::vector<std::vector<int>>& sr) {
+  const int n = m.n;
+  cl.assign(n + 1, {});
+  sl.assign(n + 1, {});
+  cr.assign(n + 1, {});
+  sr.assign(n + 1, {});
+  auto self = [&](int bond, std::vector<std::vector<int>>& c, std::vector<std::vector<int>>& sg) {
+    const int nc = (int)m.labels[bond].size();
+    c[bond].resize(nc);
+    sg[bond].assign(nc, 1);
+    for (int i = 0; i < nc; ++i) c[bond][i] = i;
+  };
+  self(0, cl, sl);
+  self(n, cr, sr);
+  using Ent = std::tuple<int, int, int, double>;   // (channel at the other bond, s_out, s_in, value)
+  // entries sorted, first value made positive; sg: the sign taken out
+  auto canon = [](std::vector<Ent> v, int& sg) {
+    std::sort(v.begin(), v.end());
+    sg = 1;
+    if (!v.empty() && std::get<3>(v[0]) < 0) {
+      sg = -1;
+      for (auto& e : v) std::get<3>(e) = -std::get<3>(e);
+    }
+    return v;
+  };
+  auto pair_up = [&](const std::vector<std::vector<Ent>>& lines, const std::vector<int>& cprev,
+                     const std::vector<int>& sprev, std::vector<int>& cout, std::vector<int>& sout) {
+    const int nc = (int)lines.size();
+    cout.assign(nc, -1);
+    sout.assign(nc, 1);
+    std::map<std::vector<Ent>, std::vector<int>> by;
+    std::vector<int> sg(nc, 1);
+    for (int c = 0; c < nc; ++c) by[canon(lines[c], sg[c])].push_back(c);
+    for (int c = 0; c < nc; ++c) {
+      if (cout[c] >= 0) continue;
+      if (lines[c].empty()) {   // a zero environment
+        cout[c] = c;
+        continue;
+      }
+      std::vector<Ent> t;
+      bool ok = true;
+      for (const Ent& e : lines[c]) {
+        const int a = std::get<0>(e);
+        if (cprev[a] < 0) {
+          ok = false;
+          break;
+        }
+        t.emplace_back(cprev[a], std::get<2>(e), std::get<1>(e), sprev[a] * std::get<3>(e));
+      }
+      if (!ok) continue;
+      int st = 1;
+      auto it = by.find(canon(t, st));
+      if (it == by.end()) continue;
+      for (int d : it->second) {
+        if (cout[d] >= 0) continue;
+        cout[c] = d;
+        cout[d] = c;
+        sout[c] = sout[d] = st * sg[d];   // lines[d] = sg[d] st t
+        break;
+      }
+    }
+  };
+  for (int k = 0; k < n; ++k) {   // left: columns of W_k (bond k -> bond k + 1)
+    std::vector<std::vector<Ent>> col(m.labels[k + 1].size());
+    for (const MpoEntry& e : m.W[k]) col[e.b].emplace_back(e.a, e.sout, e.sin, e.v);
+    pair_up(col, cl[k], sl[k], cl[k + 1], sl[k + 1]);
+  }
+  for (int k = n - 1; k >= 0; --k) {   // right: rows of W_k (bond k + 1 -> bond k)
+    std::vector<std::vector<Ent>> row(m.labels[k].size());
+    for (const MpoEntry& e : m.W[k]) row[e.a].emplace_back(e.b, e.sout, e.sin, e.v);
+    pair_up(row, cr[k + 1], sr[k + 1], cr[k], sr[k]);
   }
 }
 

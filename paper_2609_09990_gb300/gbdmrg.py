@@ -125,6 +125,10 @@ def lib():
                                    C.c_int32, _ip]),
         "gbd_rdms": (C.c_int, [vp, _dp, _dp]),
         "gbd_rdms_ci": (C.c_int, [vp, _dp, _dp]),
+        "gbd_set_env_conjugates": (C.c_int, [vp, C.c_int32]),
+        "gbd_host_mpo_conjugates": (C.c_int, [C.c_int32, _dp, C.c_int32, _dp, C.c_int32, C.c_int32, C.c_int32, _ip,
+                                              _ip, C.c_int32, _ip]),
+        "gbd_env_conjugates": (C.c_int, [vp, C.c_int32, C.c_int32, _ip, _ip, C.c_int32, _ip]),
         "gbd_orbital_rdms_ci": (C.c_int, [vp, _dp, _dp]),
         "gbd_rdm3": (C.c_int, [vp, _dp]),
         "gbd_orbital_rdms": (C.c_int, [vp, _dp, _dp]),
@@ -409,6 +413,20 @@ class Context:
         self._check(self.L.gbd_rdms(self.ptr, _d(r1), _d(r2)), "gbd_rdms")
         return r1, r2
 
+    def set_env_conjugates(self, enable):
+        self._check(self.L.gbd_set_env_conjugates(self.ptr, int(enable)), "gbd_set_env_conjugates")
+
+    def env_conjugates(self, side, bond):
+        """gbd_env_conjugates: (partner, sign) arrays of one bond."""
+        cnt = C.c_int32(0)
+        self._check(self.L.gbd_env_conjugates(self.ptr, side, bond, None, None, 0, C.byref(cnt)),
+                    "gbd_env_conjugates")
+        part = np.zeros(cnt.value, dtype=np.int32)
+        sg = np.zeros(cnt.value, dtype=np.int32)
+        self._check(self.L.gbd_env_conjugates(self.ptr, side, bond, _i(part), _i(sg), cnt.value, C.byref(cnt)),
+                    "gbd_env_conjugates")
+        return part, sg
+
     def rdms_ci(self, n):
         """gbd_rdms_ci: the same RDMs from the determinant expansion."""
         r1 = np.zeros((n, n))
@@ -645,6 +663,27 @@ def host_mpo(h, chol, k_switch=None, dense=False):
     if rc != GBD_OK:
         raise GbdError(f"gbd_host_mpo: {ERRORS.get(rc, rc)}")
     return (bd, out) if dense else bd
+
+
+def host_mpo_conjugates(h, chol, side, bond, k_switch=None):
+    """gbd_host_mpo_conjugates: (partner, sign) of the certified conjugate
+    channel pairs of one bond of the MPO of (h, chol)."""
+    L = lib()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    chol = np.ascontiguousarray(chol, dtype=np.float64)
+    n = h.shape[0]
+    ks = n // 2 if k_switch is None else k_switch
+    cnt = C.c_int32(0)
+    rc = L.gbd_host_mpo_conjugates(n, _d(h), chol.shape[0], _d(chol), ks, side, bond, None, None, 0, C.byref(cnt))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_mpo_conjugates: {ERRORS.get(rc, rc)}")
+    part = np.zeros(cnt.value, dtype=np.int32)
+    sg = np.zeros(cnt.value, dtype=np.int32)
+    rc = L.gbd_host_mpo_conjugates(n, _d(h), chol.shape[0], _d(chol), ks, side, bond, _i(part), _i(sg), cnt.value,
+                                   C.byref(cnt))
+    if rc != GBD_OK:
+        raise GbdError(f"gbd_host_mpo_conjugates: {ERRORS.get(rc, rc)}")
+    return part, sg
 
 
 def multi_dot_noalloc(device, V_ptr, stride, k, x_ptr, n, out_ptr, stream=None):
