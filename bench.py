@@ -460,6 +460,38 @@ def sigma_probe(prec, orders=(1,), warm_sweeps=0, davidson=False):
     ctx.close()
 
 
+def rdm_probe(workload, warm_sweeps):
+    """Profiling driver for the RDM pass: `workload` after warm_sweeps sweeps
+    in the mixed tiers; the CUDA profiler is started right before gbd_rdms
+    (1-/2-RDMs contracted through the MPS), so
+    `ncu --profile-from-start off` captures that pass alone.  Prints its
+    time (CUDA-synchronised by the call) and peak environment bytes."""
+    from paper_2609_09990_gb300 import gbdmrg as G
+    import torch
+    wl = WORKLOADS[workload]
+    n, ne, nq, M, seed = wl["n_orb"], wl["n_elec"], wl["n_chol"], wl["M"], wl["seed"]
+    h, chol = make_integrals(n, nq, seed)
+    ctx = G.Context(0)
+    ctx.setup(h, chol, ne, 0, [M] * warm_sweeps, [1e-6] * warm_sweeps, seed=seed, precision=PREC["bf16"],
+              fp64_refine=0)
+    ctx.init_state()
+    for s in range(warm_sweeps):
+        ctx.run_sweep(s)
+    ctx.final_energy()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    s0 = ctx.stats()
+    t = time.perf_counter()
+    g1, g2 = ctx.rdms(n)
+    dt = time.perf_counter() - t
+    torch.cuda.profiler.stop()
+    s1 = ctx.stats()
+    print(json.dumps({"rdm_probe": workload, "warm_sweeps": warm_sweeps, "seconds": dt,
+                      "env_gb": s1["rdm_env_bytes"] / 1e9, "launches": s1["kernel_launches"] - s0["kernel_launches"],
+                      "trace_gamma": float(np.trace(g1))}))
+    ctx.close()
+
+
 def precond_probe(n):
     """Profiling driver for the fused learned-preconditioner kernel: n
     elements of (r, diag) and a seeded random network, one application
@@ -673,6 +705,8 @@ def main():
                     "mixed-precision sweeps (profiler started before the timed builds)")
     ap.add_argument("--precond-ab", action="store_true", help="learned against diagonal preconditioner on "
                     "--workload after --warmup sweeps (probe solves to 1e-8; no bench line)")
+    ap.add_argument("--rdm-probe", action="store_true", help="profiling driver: the RDM pass of --workload after "
+                    "--probe-warm-sweeps (default 2) mixed sweeps (no bench line)")
     ap.add_argument("--precond-probe", type=int, default=0, help="profiling driver: one fused learned-"
                     "preconditioner application on this many elements (no bench line)")
     ap.add_argument("--probe-davidson", action="store_true", help="--sigma-probe: one mixed-precision Davidson "
@@ -685,6 +719,9 @@ def main():
         return
     if args.precond_probe:
         precond_probe(args.precond_probe)
+        return
+    if args.rdm_probe:
+        rdm_probe(args.workload, args.probe_warm_sweeps or 2)
         return
     if args.sigma_probe:
         sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")), args.probe_warm_sweeps,

@@ -316,22 +316,26 @@ std::vector<double> Engine::eval_strings(StringSet& S) {
       P.rrows[c].push_back(e.rc);
     }
   }
-  // split-K layout of the products
+  // split-K layout of the products: the output tiles of all classes of a
+  // bond share one launch; K is split until that launch has about four
+  // 32 x 32 tiles per SM, each split keeping at least 2048 of K
   int64_t gsize = 0;
   for (int b = 1; b <= n; ++b) {
     BondProd& P = prod[b];
     const Bond& bd = bonds[b];
+    std::vector<int64_t> ksum(P.shift.size(), 0), tiles(P.shift.size(), 0);
+    int64_t tiles_all = 0;
     for (size_t c = 0; c < P.shift.size(); ++c) {
-      int64_t ksum = 0;
       for (int q = 0; q < bd.nsec(); ++q) {
         const int qo = bd.find(bd.na[q] + P.shift[c].first, bd.nb[q] + P.shift[c].second);
-        if (qo >= 0) ksum += (int64_t)bd.dim[qo] * bd.dim[q];
+        if (qo >= 0) ksum[c] += (int64_t)bd.dim[qo] * bd.dim[q];
       }
-      // split K only as far as the output tiles of the class need it to fill
-      // the device (about 4 tiles per SM over the bond's classes)
-      const int64_t tiles = (int64_t)((P.lrows[c].size() + 31) / 32) * ((P.rrows[c].size() + 31) / 32);
-      const int64_t want = (4 * (int64_t)num_sms + tiles - 1) / tiles;
-      const int ns = (int)std::max<int64_t>(1, std::min<int64_t>({16, ksum / 16384, want}));
+      tiles[c] = (int64_t)((P.lrows[c].size() + 31) / 32) * ((P.rrows[c].size() + 31) / 32);
+      tiles_all += tiles[c];
+    }
+    const int64_t want = (4 * (int64_t)num_sms + std::max<int64_t>(tiles_all, 1) - 1) / std::max<int64_t>(tiles_all, 1);
+    for (size_t c = 0; c < P.shift.size(); ++c) {
+      const int ns = (int)std::max<int64_t>(1, std::min<int64_t>({64, ksum[c] / 2048, want}));
       P.gbase.push_back(gsize);
       P.nsplit.push_back(ns);
       gsize += (int64_t)ns * P.lrows[c].size() * P.rrows[c].size();
