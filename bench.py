@@ -135,6 +135,8 @@ def run_ours(args, rank, world):
     ctx.set_accurate_tier(3 if args.tier2 == "tf32x3" else 4)
     ctx.set_tier_stop(args.floor_mult, args.hard_stag)
     ctx.set_env_precision(ENV_PREC[args.env_prec])
+    if args.tc_sout_min is not None:
+        ctx.set_tc_sout_split(args.tc_sout_min)
     nsw = args.warmup + args.steps
     ctx.setup(h, chol, ne, 0, [M] * (nsw + 1), schedule(nsw + 1, args.tol), seed=seed, precision=prec,
               fp64_refine=args.refine)
@@ -384,7 +386,7 @@ def run_batched(args, rank, world):
                 load_imbalance=float(load.max() / load.mean()) if load.size else 1.0)
 
 
-def sigma_probe(prec, orders=(1,), warm_sweeps=0, davidson=False):
+def sigma_probe(prec, orders=(1,), warm_sweeps=0, davidson=False, order_a=0):
     """Profiling driver for the tensor-core sigma: CAS(16,16) M=512, initial
     state (or, with warm_sweeps > 0, the state after that many sweeps in the
     mixed tiers), steps up to the central bond (7,8), then three sigma builds
@@ -434,6 +436,7 @@ def sigma_probe(prec, orders=(1,), warm_sweeps=0, davidson=False):
         ctx.close()
         return
     ref = None
+    ctx.set_tc_order_a(order_a)
     for order in orders:
         ctx.set_tc_order(order)
         s0 = ctx.stats()
@@ -447,7 +450,8 @@ def sigma_probe(prec, orders=(1,), warm_sweeps=0, davidson=False):
         nb = s1["n_sigma_tc"] - s0["n_sigma_tc"]
         per = lambda key: (s1[key] - s0[key]) / nb
         perv = lambda key: [(a - b) / nb for a, b in zip(s1[key], s0[key])]
-        print(json.dumps({"sigma_probe": prec, "warm_sweeps": warm_sweeps, "stage_b_order": order, "bond": k,
+        print(json.dumps({"sigma_probe": prec, "warm_sweeps": warm_sweeps, "stage_a_order": order_a,
+                          "stage_b_order": order, "bond": k,
                           "psi_len": int(x.size),
                           "builds": nb, "identical_to_first_order": bool(np.array_equal(y, ref)),
                           "tc_gemm_ms_per_build": per("tc_gemm_ms"), "tc_gemm_ms_each": each,
@@ -711,6 +715,10 @@ def main():
                     "preconditioner application on this many elements (no bench line)")
     ap.add_argument("--probe-davidson", action="store_true", help="--sigma-probe: one mixed-precision Davidson "
                     "solve at the central bond instead of the sigma builds")
+    ap.add_argument("--tc-sout-min", type=int, default=None, help="stage-B s_out split threshold on E_L(q) rows "
+                    "(library default if omitted)")
+    ap.add_argument("--probe-order-a", type=int, default=0, help="stage-A tile order of --sigma-probe (0 the "
+                    "library's default, 1 Renl-stack blocks together)")
     ap.add_argument("--probe-orders", default="1", help="stage-B tile orders timed by --sigma-probe, e.g. 0,1,2 "
                     "(1 is the library's default)")
     args = ap.parse_args()
@@ -725,7 +733,7 @@ def main():
         return
     if args.sigma_probe:
         sigma_probe(args.sigma_probe, tuple(int(o) for o in args.probe_orders.split(",")), args.probe_warm_sweeps,
-                    args.probe_davidson)
+                    args.probe_davidson, args.probe_order_a)
         return
     if args.states:
         states_run(args)

@@ -91,6 +91,19 @@ int gbd_set_adaptive_bond_dim(gbd_ctx *ctx, double max_discarded, int32_t m_min)
  * computes the same products in the same order, so the result is
  * identical for all three. */
 int gbd_set_tc_order(gbd_ctx *ctx, int32_t order);
+/* Tile order of stage A (Y^T = Renl stack x psi^T): 0 (default) most
+ * expensive tile first; 1 the N tiles of each 128-row block of the Renl
+ * stack adjacent (blocks most expensive first), so that they share its A
+ * boxes through L2.  Results are identical for both. */
+int gbd_set_tc_order_a(gbd_ctx *ctx, int32_t order);
+/* Stage B of the tensor-core sigma per output sector q: with E_L(q) of at
+ * least min_rows rows (default 160), one product per s_out section of E_L(q)
+ * over the Y^T sections that section reads (its Lenl panel holds that
+ * section's rows only), else one product over all of E_L(q) (its panel has
+ * the zero rows of the sections a Y^T section does not reach).  0 splits
+ * every sector, a large value none.  The sums differ only in their split-K
+ * grouping. */
+int gbd_set_tc_sout_split(gbd_ctx *ctx, int32_t min_rows);
 
 /* Preconditioner of the following Davidson solves (GBD_PRECOND_DIAG or
  * GBD_PRECOND_LEARNED; the latter needs weights in the context). */

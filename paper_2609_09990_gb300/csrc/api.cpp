@@ -392,6 +392,24 @@ int gbd_set_tc_order(gbd_ctx* ctx, int32_t order) {
   });
 }
 
+int gbd_set_tc_sout_split(gbd_ctx* ctx, int32_t min_rows) {
+  return guarded(ctx, [&]() {
+    if (min_rows < 0) return fail(ctx, GBD_ERR_ARG, "min_rows < 0");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tc_sout_min = min_rows;
+    return GBD_OK;
+  });
+}
+
+int gbd_set_tc_order_a(gbd_ctx* ctx, int32_t order) {
+  return guarded(ctx, [&]() {
+    if (order < 0 || order > 1) return fail(ctx, GBD_ERR_ARG, "order not in {0,1}");
+    if (!ctx->eng) ctx->eng.reset(new gbd::Engine(ctx->device));
+    ctx->eng->tc_order_a = order;
+    return GBD_OK;
+  });
+}
+
 int gbd_set_preconditioner(gbd_ctx* ctx, int32_t preconditioner) {
   return guarded(ctx, [&]() {
     if (!ctx->eng) return fail(ctx, GBD_ERR_STATE, "gbd_setup first");

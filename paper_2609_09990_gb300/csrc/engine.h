@@ -237,6 +237,8 @@ class Engine {
   int pcg_steps = 4;          // inner PCG (preconditioner 3): at most this many matvecs per correction
   double pcg_rel_tol = 0.1;   // ... stopping when |residual| < pcg_rel_tol |r|
   int tc_order = 1;           // stage-B tile order: 0 (q,m0,chunk,n0), 1 (q,chunk,m0,n0), 2 (q,chunk,n0,m0)
+  int tc_order_a = 0;         // stage-A tile order: 0 most expensive first, 1 Renl-stack blocks together
+  int tc_sout_min = 160;      // stage B: output sectors with E_L(q) >= this many rows split by s_out section
   int tier2 = 2;              // operands of the accurate tier: 2 = TF32x3, 3 = BF16x3 (TcPrec)
   // environment updates of the sweep steps of reduced-precision schedules:
   // -1 = FP64 (default), else on the tensor cores with these operands

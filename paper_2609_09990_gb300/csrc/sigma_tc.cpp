@@ -134,7 +134,29 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   }
   std::vector<int32_t> koff((size_t)nb * nq * 4, -1);   // K offset of section (b, qin, sin) in K_qout
   std::vector<char> yuse((size_t)nb * nq, 0);            // (b, qin) has a section in use
-  std::vector<int64_t> Kq(nq, 0), yrow0(nq, 0), lrow0(nq, 0);
+  std::vector<int64_t> Kq(nq, 0), yrow0(nq, 0);
+  // K groups of output sector q: sections read by only the s_out section g
+  // of E_L(q) form group g (0..3), sections read by several form group 4;
+  // each group starts at a K-block boundary.  gk[q][g] = first K, gk[q][g+1]
+  // bounds it (aligned up).  Stage B multiplies Y^T(q) by one Lenl panel per
+  // s_out section over group s_out and group 4 only, so the panel holds the
+  // rows of that section alone (no zero rows of other sections).
+  std::vector<std::array<int64_t, 6>> gk(nq);
+  std::vector<std::array<int64_t, 5>> glen(nq);
+  std::vector<std::array<int64_t, 4>> lrow0s(nq), kqs(nq);   // Lenl panel of (q, s_out): first row, K length
+  std::vector<int64_t> lrow0(nq, -1);                        // unsplit sector: one panel over E_L(q)
+  std::vector<int> smask((size_t)nb * nq * 4, 0);          // s_out sections reading a section
+  // split sectors: E_L(q) of at least tc_sout_min rows (smaller ones keep one
+  // panel over all of E_L(q): their zero rows cost less than more, smaller
+  // tiles); an unsplit sector has all its sections in group 0
+  std::vector<char> spl(nq, 0);
+  for (int q = 0; q < nq; ++q) spl[q] = EL.dim[q] >= tc_sout_min;
+  auto group_of = [&](int32_t key) {
+    const int m = smask[key];
+    if (!spl[renl.subs[rfirst[key / 4]].qout]) return 0;
+    return (m & (m - 1)) ? 4 : __builtin_ctz(m);
+  };
+  auto upW = [&](int64_t x) { return (x + W - 1) / W * W; };
   int64_t yrows = 0, ls_rows = 0;
   {
     std::vector<std::vector<int32_t>> secs((size_t)nq);
@@ -142,31 +164,58 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       const size_t bq = (size_t)s.b * nq + s.qin, key = bq * 4 + s.sin;
       if (s.cols != EL.sdim[s.qin][s.sin] || s.rows != EL.sdim[s.qout][s.sout])
         throw Error(-3, "enlarged-operator sub-block does not match its sections");
-      if (rfirst[bq] < 0 || koff[key] != -1) continue;   // no Y block, or already listed
+      if (rfirst[bq] < 0) continue;   // no Y block
       if (renl.subs[rfirst[bq]].qout != s.qout) throw Error(-3, "Lenl and Renl channels disagree on the sector");
+      smask[key] |= 1 << s.sout;
+      if (koff[key] != -1) continue;   // already listed
       koff[key] = -2;
       secs[s.qout].push_back((int32_t)key);
     }
     for (int q = 0; q < nq; ++q) {
-      std::sort(secs[q].begin(), secs[q].end());   // (b, qin, sin) order
+      // (group, b, qin, sin) order
+      std::sort(secs[q].begin(), secs[q].end(), [&](int32_t x, int32_t y) {
+        const int gx = group_of(x), gy = group_of(y);
+        return gx != gy ? gx < gy : x < y;
+      });
       int64_t k = 0;
-      for (int32_t key : secs[q]) {
-        koff[key] = (int32_t)k;
-        yuse[key / 4] = 1;
-        const int qin = (key / 4) % nq, sin = key % 4;
-        k += up16(EL.sdim[qin][sin]);
-        // Y^T(q) section written by stage A and read by stage B
-        const double yb = (double)P->eb * nh * ER.dim[q] * EL.sdim[qin][sin];
-        P->bytes_alg += 2.0 * yb;
-        P->alg_st[0] += yb;
-        P->alg_st[1] += yb;
+      size_t i = 0;
+      for (int g = 0; g < 5; ++g) {
+        k = upW(k);
+        gk[q][g] = k;
+        for (; i < secs[q].size() && group_of(secs[q][i]) == g; ++i) {
+          const int32_t key = secs[q][i];
+          koff[key] = (int32_t)k;
+          yuse[key / 4] = 1;
+          const int qin = (key / 4) % nq, sin = key % 4;
+          k += up16(EL.sdim[qin][sin]);
+          // Y^T(q) section written by stage A and read by stage B
+          const double yb = (double)P->eb * nh * ER.dim[q] * EL.sdim[qin][sin];
+          P->bytes_alg += 2.0 * yb;
+          P->alg_st[0] += yb;
+          P->alg_st[1] += yb;
+        }
+        glen[q][g] = k - gk[q][g];
       }
+      gk[q][5] = upW(k);
       Kq[q] = k;
-      const int64_t nblk = (k + W - 1) / W;
+      const int64_t nblk = gk[q][5] / W;
       yrow0[q] = yrows;
       yrows += nblk * ER.dim[q];
-      lrow0[q] = ls_rows;
-      ls_rows += nblk * EL.dim[q];
+      for (int so = 0; so < 4; ++so) {
+        lrow0s[q][so] = -1;
+        kqs[q][so] = 0;
+      }
+      if (!spl[q]) {
+        lrow0[q] = ls_rows;
+        ls_rows += nblk * EL.dim[q];
+        continue;
+      }
+      for (int so = 0; so < 4; ++so) {
+        if (EL.soff[q][so] < 0 || (glen[q][so] == 0 && glen[q][4] == 0)) continue;
+        kqs[q][so] = upW(glen[q][so]) + upW(glen[q][4]);
+        lrow0s[q][so] = ls_rows;
+        ls_rows += kqs[q][so] / W * EL.sdim[q][so];
+      }
     }
   }
   P->yt_pitch = W;
@@ -313,11 +362,20 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     std::vector<int32_t> ks(lenl.subs.size(), 0);
     for (size_t i = 0; i < lenl.subs.size(); ++i) {
       const EnlSub& s = lenl.subs[i];
-      const int32_t k = koff[((size_t)s.b * nq + s.qin) * 4 + s.sin];
+      const int32_t key = (int32_t)(((size_t)s.b * nq + s.qin) * 4 + s.sin);
+      const int32_t k = koff[key];
       if (k < 0) continue;
-      r0[i] = lrow0[s.qout] + EL.soff[s.qout][s.sout];
-      c0[i] = k;
-      ks[i] = EL.dim[s.qout];
+      const int q = s.qout, g = group_of(key);
+      if (!spl[q]) {   // rows at the E_L(q) offset of sout in every K block of q
+        r0[i] = lrow0[q] + EL.soff[q][s.sout];
+        c0[i] = k;
+        ks[i] = EL.dim[q];
+        continue;
+      }
+      // panel (qout, sout): group sout first, then group 4
+      r0[i] = lrow0s[q][s.sout];
+      c0[i] = g == 4 ? upW(glen[q][s.sout]) + (k - gk[q][4]) : k - gk[q][s.sout];
+      ks[i] = EL.sdim[q][s.sout];
     }
     convert(lenl, r0, c0, &ks, P->ls, P->ls_pitch);
   }
@@ -387,7 +445,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         tiles.push_back(T);
       }
   }
-  // stage A: most expensive tiles first; stage B: by the keys, in the
+  // stage A: most expensive tiles first (tc_order_a 0) or the N tiles of each
+  // Renl-stack block together (1); stage B: by the keys, in the
   // priority tc_order names (tiles that read the same boxes adjacent, so
   // that they run at the same time on neighbouring SMs and share the boxes
   // through L2)
@@ -411,6 +470,18 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         for (int i = 0; i < 5; ++i)
           if (bkey[a][pm[i]] != bkey[b][pm[i]]) return bkey[a][pm[i]] < bkey[b][pm[i]];
         return false;
+      });
+    } else if (which == 0 && tc_order_a == 1) {
+      // the N tiles of one 128-row block of the Renl stack (same out row)
+      // adjacent, so they run together and read its A boxes from DRAM
+      // once; blocks by their summed cost, most expensive first
+      std::map<int64_t, double> bcost;
+      for (size_t i = 0; i < tiles.size(); ++i) bcost[tiles[i].out] += cost[i];
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double ca = bcost[tiles[a].out], cb = bcost[tiles[b].out];
+        if (ca != cb) return ca > cb;
+        if (tiles[a].out != tiles[b].out) return tiles[a].out < tiles[b].out;
+        return tiles[a].n0 < tiles[b].n0;
       });
     } else
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
@@ -464,40 +535,93 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
     kc = std::max<int64_t>(256, std::min<int64_t>(nh == 2 ? 512 : 2048, kc));
     P->kc = kc;
   }
+  // sections of sigma that no product reaches are written as zeros by the
+  // reduction (tasks without slots)
+  std::vector<TcRed> zero_red;
   for (int q = 0; q < nq; ++q) {
     if (EL.dim[q] <= 0 || ER.dim[q] <= 0) continue;
-    const int N = EL.dim[q];
-    // one term list per output sector, shared by its tiles
-    const int ot0 = (int)terms.size();
-    for (int64_t k0 = 0; k0 < Kq[q]; k0 += kc) {
-      const int64_t blk = k0 / W, k = std::min<int64_t>(kc, Kq[q] - k0);
-      term_k.push_back((int32_t)k);
-      terms.push_back({0, (int32_t)(yrow0[q] + blk * ER.dim[q]), (int32_t)(lrow0[q] + blk * EL.dim[q]), (int32_t)k, 0,
-                       0, ER.dim[q], EL.dim[q]});
-    }
-    const int ot1 = (int)terms.size();
-    for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
-      for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
-        TcTile T{};
-        T.t0 = ot0;
-        T.t1 = ot1;
-        T.n0 = n0;
-        T.m0 = m0;
-        T.m_valid = std::min(128, ER.dim[q] - m0);
-        const int nv = std::min(tune.ncap[1], N - n0);
-        T.n_mma = (int)up16(nv);
-        T.n_valid = nv;
-        T.bsel = bsel_for(T.n_mma);
-        T.mode = kTcSigma;
-        T.beta = 0;
-        T.ld = ER.dim[q];
-        T.out = psi_off[q] + (int64_t)n0 * ER.dim[q];
-        P->flops_exec += 2.0 * 128 * T.n_mma * (double)Kq[q];
-        tiles.push_back(T);
-        // key (q, m0, chunk, -, n0): by default the n tiles of one
-        // (q, m0, chunk) read the same Y^T boxes and run together
-        bkey.push_back({q, m0, 0, 0, n0});   // chunk index filled by the split
+    if (!spl[q]) {
+      // one product over all of E_L(q) and K_q
+      const int N = EL.dim[q];
+      const int ot0 = (int)terms.size();
+      for (int64_t k0 = 0; k0 < Kq[q]; k0 += kc) {
+        const int64_t blk = k0 / W, k = std::min<int64_t>(kc, Kq[q] - k0);
+        term_k.push_back((int32_t)k);
+        terms.push_back({0, (int32_t)(yrow0[q] + blk * ER.dim[q]), (int32_t)(lrow0[q] + blk * EL.dim[q]), (int32_t)k,
+                         0, 0, ER.dim[q], EL.dim[q]});
       }
+      const int ot1 = (int)terms.size();
+      for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
+        for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
+          TcTile T{};
+          T.t0 = ot0;
+          T.t1 = ot1;
+          T.n0 = n0;
+          T.m0 = m0;
+          T.m_valid = std::min(128, ER.dim[q] - m0);
+          const int nv = std::min(tune.ncap[1], N - n0);
+          T.n_mma = (int)up16(nv);
+          T.n_valid = nv;
+          T.bsel = bsel_for(T.n_mma);
+          T.mode = kTcSigma;
+          T.beta = 0;
+          T.ld = ER.dim[q];
+          T.out = psi_off[q] + (int64_t)n0 * ER.dim[q];
+          P->flops_exec += 2.0 * 128 * T.n_mma * (double)Kq[q];
+          tiles.push_back(T);
+          bkey.push_back({q * 4, m0, 0, 0, n0});   // chunk index filled by the split
+        }
+      continue;
+    }
+    for (int so = 0; so < 4; ++so) {
+      if (EL.soff[q][so] < 0) continue;
+      const int N = EL.sdim[q][so];
+      const int64_t out0 = psi_off[q] + (int64_t)EL.soff[q][so] * ER.dim[q];
+      if (lrow0s[q][so] < 0) {
+        for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
+          zero_red.push_back({out0, 0, 0, ER.dim[q], m0, std::min(128, ER.dim[q] - m0), N, 0, 0});
+        continue;
+      }
+      // one term list per (q, s_out): group s_out, then group 4, in chunks
+      // of at most kc starting on K-block boundaries
+      const int ot0 = (int)terms.size();
+      auto add_range = [&](int64_t kabs, int64_t len, int64_t kpanel) {
+        for (int64_t k0 = 0; k0 < len; k0 += kc) {
+          const int64_t k = std::min<int64_t>(kc, len - k0);
+          const int64_t yblk = (kabs + k0) / W, pblk = (kpanel + k0) / W;
+          term_k.push_back((int32_t)k);
+          terms.push_back({0, (int32_t)(yrow0[q] + yblk * ER.dim[q]), (int32_t)(lrow0s[q][so] + pblk * N),
+                           (int32_t)k, 0, 0, ER.dim[q], N});
+        }
+      };
+      add_range(gk[q][so], glen[q][so], 0);
+      add_range(gk[q][4], glen[q][4], upW(glen[q][so]));
+      const int ot1 = (int)terms.size();
+      double ksum = 0;
+      for (int t = ot0; t < ot1; ++t) ksum += terms[t].k;
+      for (int m0 = 0; m0 < ER.dim[q]; m0 += 128)
+        for (int n0 = 0; n0 < N; n0 += tune.ncap[1]) {
+          TcTile T{};
+          T.t0 = ot0;
+          T.t1 = ot1;
+          T.n0 = n0;
+          T.m0 = m0;
+          T.m_valid = std::min(128, ER.dim[q] - m0);
+          const int nv = std::min(tune.ncap[1], N - n0);
+          T.n_mma = (int)up16(nv);
+          T.n_valid = nv;
+          T.bsel = bsel_for(T.n_mma);
+          T.mode = kTcSigma;
+          T.beta = 0;
+          T.ld = ER.dim[q];
+          T.out = out0 + (int64_t)n0 * ER.dim[q];
+          P->flops_exec += 2.0 * 128 * T.n_mma * ksum;
+          tiles.push_back(T);
+          // key (q s_out, m0, chunk, -, n0): by default the n tiles of one
+          // (q, s_out, m0, chunk) read the same Y^T boxes and run together
+          bkey.push_back({q * 4 + so, m0, 0, 0, n0});   // chunk index filled by the split
+        }
+    }
   }
   // ---- split K: a stage-B tile with more than one chunk becomes one tile
   //      per chunk writing an FP32 partial slot, summed in FP64 by
@@ -538,6 +662,11 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
         split.push_back(Cc);
       }
       red.push_back(R);
+    }
+    for (TcRed z : zero_red) {
+      z.e0 = red_total;
+      red_total += (int64_t)z.m_valid * z.n_valid;
+      red.push_back(z);
     }
     tiles.swap(split);
     bkey.swap(skey);

@@ -126,6 +126,8 @@ def lib():
         "gbd_rdms": (C.c_int, [vp, _dp, _dp]),
         "gbd_rdms_ci": (C.c_int, [vp, _dp, _dp]),
         "gbd_set_env_conjugates": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_tc_order_a": (C.c_int, [vp, C.c_int32]),
+        "gbd_set_tc_sout_split": (C.c_int, [vp, C.c_int32]),
         "gbd_host_mpo_conjugates": (C.c_int, [C.c_int32, _dp, C.c_int32, _dp, C.c_int32, C.c_int32, C.c_int32, _ip,
                                               _ip, C.c_int32, _ip]),
         "gbd_env_conjugates": (C.c_int, [vp, C.c_int32, C.c_int32, _ip, _ip, C.c_int32, _ip]),
@@ -365,6 +367,12 @@ class Context:
 
     def set_tc_order(self, order):
         self._check(self.L.gbd_set_tc_order(self.ptr, order), "gbd_set_tc_order")
+
+    def set_tc_sout_split(self, min_rows):
+        self._check(self.L.gbd_set_tc_sout_split(self.ptr, min_rows), "gbd_set_tc_sout_split")
+
+    def set_tc_order_a(self, order):
+        self._check(self.L.gbd_set_tc_order_a(self.ptr, order), "gbd_set_tc_order_a")
 
     def set_preconditioner(self, preconditioner):
         self._check(self.L.gbd_set_preconditioner(self.ptr, preconditioner), "gbd_set_preconditioner")
