@@ -57,7 +57,7 @@ METRIC = "sigma-build TFLOP/s; sweep time at CAS(16,16) M=512 vs FP64 GPU at \u2
 # of algorithmic bytes).  The launches of a sweep move the same kinds of
 # panels, so traffic is reported as this ratio times their algorithmic bytes
 # per launch.
-TC_DRAM_PER_ALG_BYTE = (1051.977984e6 + 928.156672e6 + 1963.578112e6 + 149.253376e6) / 2359843136.0
+TC_DRAM_PER_ALG_BYTE = (1052.990976e6 + 930.154752e6 + 1648.479232e6 + 86.380032e6) / 2359843136.0
 DTYPE = {"fp64": "f64", "tf32": "tf32/f32-acc", "bf16": "bf16/f32-acc"}
 
 
