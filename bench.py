@@ -163,7 +163,8 @@ def run_ours(args, rank, world):
     dt = t1 - t0
     keys = ["sigma_ms", "tc_ms", "tc_gemm_ms", "tc_build_ms", "env_ms", "enlarge_ms", "enlarge_host_ms",
             "enlarge_dev_ms", "diag_ms",
-            "davidson_ms", "truncate_ms", "truncate_rho_ms", "truncate_eig_ms", "env_wall_ms", "step_ms"]
+            "davidson_ms", "truncate_ms", "truncate_rho_ms", "truncate_eig_ms", "env_wall_ms", "step_ms",
+            "h2d_wait_ms"]
     breakdown = {k: (st1[k] - st0[k]) / args.steps for k in keys}
     breakdown["sigma_builds"] = (st1["n_sigma"] - st0["n_sigma"]) / args.steps
     breakdown["tc_sigma_builds"] = (st1["n_sigma_tc"] - st0["n_sigma_tc"]) / args.steps

@@ -63,6 +63,7 @@ typedef struct {
   double enlarge_bytes;           /* their algorithmic bytes: 8 (terms + 1) per output element */
   double rdm_ms;                  /* wall time of the last gbd_rdms (or RDMs of a solve) */
   double rdm_env_bytes;           /* peak device bytes of its operator-string environments */
+  double h2d_wait_ms;             /* host time waiting for a region of the pinned staging ring */
 } gbd_stats;
 
 /* Sigma launch sequences replayed as CUDA graphs (1, the default) or

@@ -941,6 +941,7 @@ static void copy_stats(const gbd::Stats& t, gbd_stats* s) {
   s->enlarge_bytes = t.enl_bytes;
   s->rdm_ms = t.rdm_ms;
   s->rdm_env_bytes = t.rdm_env_bytes;
+  s->h2d_wait_ms = t.h2d_wait_ms;
   for (int i = 0; i < 2; ++i) {
     s->tc_stage_alg_bytes[i] = t.tc_alg_st[i];
     s->tc_stage_box_bytes[2 * i] = t.tc_box_st[i][0];

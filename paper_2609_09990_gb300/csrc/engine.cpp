@@ -459,7 +459,11 @@ void Engine::h2d(void* dst, const void* src, size_t bytes) {
   // the ring bytes of [start, start + n) last held positions
   // [start - cap, start + n - cap): wait for the copies that read them
   while (!pin_inflight.empty() && pin_inflight.front().start + pin_cap < start + n) {
-    CK(cudaEventSynchronize(pin_inflight.front().ev));
+    if (cudaEventQuery(pin_inflight.front().ev) == cudaErrorNotReady) {
+      const double tw = now_ms();
+      CK(cudaEventSynchronize(pin_inflight.front().ev));
+      stats.h2d_wait_ms += now_ms() - tw;
+    }
     ev_pool.push_back(pin_inflight.front().ev);
     pin_inflight.pop_front();
   }

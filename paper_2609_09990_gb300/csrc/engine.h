@@ -99,6 +99,7 @@ struct Stats {
   double enl_dev_ms = 0, enl_bytes = 0;   // block-axpy launches of the enlarged operators: device time, bytes
   double tcb_ms[5] = {0, 0, 0, 0, 0};   // plan-build phases: layout/groups, panels, tiles, upload, maps
   double rdm_ms = 0, rdm_env_bytes = 0;   // last rdms(): wall time, peak bytes of its environments
+  double h2d_wait_ms = 0;   // host time waiting for a staging-ring region (its earlier copy still queued)
   void add(const Stats& o) {   // sum of the additive counters (batched solves)
     sigma_flops += o.sigma_flops; sigma_ms += o.sigma_ms; env_flops += o.env_flops; env_ms += o.env_ms;
     enl_ms += o.enl_ms; step_ms += o.step_ms; trunc_ms += o.trunc_ms; davidson_ms += o.davidson_ms;
@@ -125,6 +126,7 @@ struct Stats {
     trunc_rho_ms += o.trunc_rho_ms; trunc_eig_ms += o.trunc_eig_ms; env_wall_ms += o.env_wall_ms;
     enl_dev_ms += o.enl_dev_ms; enl_bytes += o.enl_bytes;
     rdm_ms += o.rdm_ms; rdm_env_bytes = std::max(rdm_env_bytes, o.rdm_env_bytes);
+    h2d_wait_ms += o.h2d_wait_ms;
     for (int i = 0; i < 5; ++i) tcb_ms[i] += o.tcb_ms[i];
     for (int i = 0; i < 4; ++i) { tc_flops_p[i] += o.tc_flops_p[i]; tc_gemm_ms_p[i] += o.tc_gemm_ms_p[i]; }
     max_discarded = std::max(max_discarded, o.max_discarded);

@@ -61,7 +61,7 @@ class gbd_stats(C.Structure):
                 ("davidson_iterations", C.c_int64), ("inner_matvecs", C.c_int64), ("n_solves", C.c_int64),
                 ("n_solves_above_tol", C.c_int64), ("sweep_max_residual", C.c_double),
                 ("enlarge_dev_ms", C.c_double), ("enlarge_bytes", C.c_double),
-                ("rdm_ms", C.c_double), ("rdm_env_bytes", C.c_double)]
+                ("rdm_ms", C.c_double), ("rdm_env_bytes", C.c_double), ("h2d_wait_ms", C.c_double)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
