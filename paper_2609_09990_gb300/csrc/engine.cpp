@@ -376,6 +376,21 @@ void Engine::check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, 
   chk_size = it->second;
 }
 
+bool Engine::in_allocation(const void* p, int64_t rows, int64_t cols, int64_t ld, AllocCache& c) const {
+  if (rows <= 0 || cols <= 0) return true;
+  if (rows > 1 && ld < cols) return false;
+  const uintptr_t a = (uintptr_t)p;
+  const uintptr_t end = a + (uintptr_t)(((rows - 1) * ld + cols) * (int64_t)sizeof(double));
+  if (c.size && a >= c.base && end <= c.base + c.size) return true;
+  auto it = allocs.upper_bound(a);
+  if (it == allocs.begin()) return false;
+  --it;
+  if (a < it->first || end > it->first + it->second) return false;
+  c.base = it->first;
+  c.size = it->second;
+  return true;
+}
+
 void Engine::check(const GemmPlan& p) const {
   for (const auto& o : p.outs) {
     check_range(o.C, o.M, o.N, o.ldc, "C");

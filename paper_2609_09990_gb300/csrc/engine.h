@@ -334,6 +334,11 @@ class Engine {
     return (T*)p;
   }
   void check_range(const void* p, int64_t rows, int64_t cols, int64_t ld, const char* what) const;
+  // the same test without the shared cache (safe on several host threads
+  // while nothing is allocated or freed): false if the block leaves every
+  // live allocation
+  struct AllocCache { uintptr_t base = 0; size_t size = 0; };
+  bool in_allocation(const void* p, int64_t rows, int64_t cols, int64_t ld, AllocCache& c) const;
   const double* site_block(int i, int qi, int s, int& ld) const;
   void check(const GemmPlan& p) const;
   void check(const AxpyPlan& p) const;

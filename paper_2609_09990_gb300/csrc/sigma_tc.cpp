@@ -9,6 +9,7 @@
 // (TMEM) and stores it as FP64.  The enlarged operators and environments
 // stay FP64; only the matvec inside Davidson changes precision.
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <climits>
 #include <cmath>
@@ -17,6 +18,7 @@
 #include <tuple>
 
 #include "engine.h"
+#include "linalg_host.h"
 #include "tc_gemm.h"
 
 namespace gbd {
@@ -151,11 +153,8 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   // tiles); an unsplit sector has all its sections in group 0
   std::vector<char> spl(nq, 0);
   for (int q = 0; q < nq; ++q) spl[q] = EL.dim[q] >= tc_sout_min;
-  auto group_of = [&](int32_t key) {
-    const int m = smask[key];
-    if (!spl[renl.subs[rfirst[key / 4]].qout]) return 0;
-    return (m & (m - 1)) ? 4 : __builtin_ctz(m);
-  };
+  std::vector<int8_t> kgroup;   // group of every listed section (filled once its s_out mask is complete)
+  auto group_of = [&](int32_t key) { return (int)kgroup[key]; };
   auto upW = [&](int64_t x) { return (x + W - 1) / W * W; };
   int64_t yrows = 0, ls_rows = 0;
   {
@@ -171,6 +170,13 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       koff[key] = -2;
       secs[s.qout].push_back((int32_t)key);
     }
+    kgroup.assign(smask.size(), 0);
+    for (int q = 0; q < nq; ++q)
+      if (spl[q])
+        for (int32_t key : secs[q]) {
+          const int m = smask[key];
+          kgroup[key] = (int8_t)((m & (m - 1)) ? 4 : __builtin_ctz(m));
+        }
     for (int q = 0; q < nq; ++q) {
       // (group, b, qin, sin) order
       std::sort(secs[q].begin(), secs[q].end(), [&](int32_t x, int32_t y) {
@@ -327,14 +333,36 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
   // ---- convert the sub-blocks (once per step)
   auto convert = [&](const EnlOp& op, const std::vector<int64_t>& rowof, const std::vector<int64_t>& colof,
                      const std::vector<int32_t>* kstride, void** panel, int64_t pitch) {
-    std::vector<TcConv> tasks;
-    for (size_t i = 0; i < op.subs.size(); ++i) {
-      const EnlSub& s = op.subs[i];
-      if (rowof[i] < 0) continue;   // not used by any product
-      check_range(s.ptr, s.rows, s.cols, s.cols, "tc convert source");
-      tasks.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], (int32_t)colof[i],
+    // task lists of contiguous blocks of sub-blocks on the host pool,
+    // concatenated in block order (the same list as a serial pass)
+    const size_t nsub = op.subs.size();
+    const int nblk = (int)std::min<size_t>(16, (nsub + 2047) / 2048);
+    std::vector<std::vector<TcConv>> part((size_t)std::max(nblk, 1));
+    std::atomic<int> bad(0);
+    auto work = [&](int bb) {
+      const size_t i0 = nsub * bb / nblk, i1 = nsub * (bb + 1) / nblk;
+      std::vector<TcConv>& out = part[bb];
+      out.reserve(i1 - i0);
+      AllocCache cache;
+      for (size_t i = i0; i < i1; ++i) {
+        const EnlSub& s = op.subs[i];
+        if (rowof[i] < 0) continue;   // not used by any product
+        if (!in_allocation(s.ptr, s.rows, s.cols, s.cols, cache)) {
+          bad = 1;
+          return;
+        }
+        out.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], (int32_t)colof[i],
                        kstride ? (*kstride)[i] : 0});
-    }
+      }
+    };
+    if (nblk > 1) host_parallel_for(nblk, work);
+    else if (nblk == 1) work(0);
+    if (bad) throw Error(-6, "plan check: tc convert source outside its allocation");
+    std::vector<TcConv> tasks;
+    size_t ntask = 0;
+    for (const auto& v : part) ntask += v.size();
+    tasks.reserve(ntask);
+    for (const auto& v : part) tasks.insert(tasks.end(), v.begin(), v.end());
     if (tasks.empty()) return;
     TcConv* d = dalloc<TcConv>(tasks.size());
     h2d(d, tasks.data(), tasks.size() * sizeof(TcConv));
