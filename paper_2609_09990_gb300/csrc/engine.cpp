@@ -791,6 +791,7 @@ void Engine::build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPl
     EnlPart& P = parts[u];
     const size_t e0 = runs[u].first, e1 = runs[u].second;
     const int b = W[e0].b;
+    if (env_derived(k + 1, b, true)) return;   // the transpose of its partner (append_conjugates)
     Buckets B;
     for (size_t e = e0; e < e1; ++e) B.lst[W[e].sout * 4 + W[e].sin].push_back({W[e].a, W[e].v});
     B.classify();
@@ -833,6 +834,7 @@ void Engine::build_lenl(int k, const Env& Lk, const Space& el, EnlOp& op, AxpyPl
     }
   });
   merge_parts(parts, op, ax);
+  append_conjugates(op, k + 1, true);
 }
 
 // Renl[b] over E_R(Q) (Q in er), from R_{i+1} and W_i (i = site).  Sub-block
@@ -854,6 +856,7 @@ void Engine::build_renl(int i, const Env& R, const Space& er, EnlOp& op, AxpyPla
   parallel_for((int)units.size(), [&](int u) {
     EnlPart& P = parts[u];
     const int b = units[u];
+    if (env_derived(i, b, false)) return;   // the transpose of its partner (append_conjugates)
     Buckets B;
     for (const MpoEntry* e : bya[b]) B.lst[e->sout * 4 + e->sin].push_back({e->b, e->v});
     B.classify();
@@ -896,6 +899,39 @@ void Engine::build_renl(int i, const Env& R, const Space& er, EnlOp& op, AxpyPla
     }
   });
   merge_parts(parts, op, ax);
+  append_conjugates(op, i, false);
+}
+
+// A derived channel d of certified partner c (sign s): Enl[d] = s Enl[c]^T
+// (Enl[b] = sum_a W[a,b] (x) Env[a] and the certification of W), so each
+// sub-block (c; qin, sin -> qout, sout) gives (d; qout, sout -> qin, sin)
+// reading the same memory transposed.  No combination is formed twice.
+void Engine::append_conjugates(EnlOp& op, int bond, bool left) const {
+  if (!env_conj) return;
+  const auto& cj = left ? conj_l : conj_r;
+  const auto& sg = left ? sign_l : sign_r;
+  if (bond >= (int)cj.size()) return;
+  const int nch = (int)cj[bond].size();
+  std::vector<std::vector<size_t>> by((size_t)nch);
+  const size_t n0 = op.subs.size();
+  for (size_t i = 0; i < n0; ++i) by[op.subs[i].b].push_back(i);
+  for (int d = 0; d < nch; ++d) {
+    if (!env_derived(bond, d, left)) continue;
+    for (size_t i : by[cj[bond][d]]) {
+      const EnlSub s = op.subs[i];
+      EnlSub t = s;
+      t.b = d;
+      t.qin = s.qout;
+      t.sin = s.sout;
+      t.qout = s.qin;
+      t.sout = s.sin;
+      t.rows = s.cols;
+      t.cols = s.rows;
+      t.sign = s.sign * sg[bond][d];
+      t.trans = s.trans ^ 1;
+      op.subs.push_back(t);
+    }
+  }
 }
 
 void Engine::finish_enl(EnlOp& op, AxpyPlan& ax) {
@@ -973,6 +1009,7 @@ void Engine::env_update_left(const EnlOp& lenl, const Space& el, const Site& A, 
       for (int gi = groups.start[tb.key]; gi < groups.start[tb.key + 1]; ++gi) {
         const EnlSub* s = &lenl.subs[groups.idx[gi]];
         if (s->sout != so) continue;
+        if (s->trans) throw Error(-6, "environment update of a derived channel");
         p1.add_term(s->ptr, s->cols, U_in + (int64_t)el.soff[tb.qin][s->sin] * nin, nin, s->cols, 0, s->sign);
       }
     }
@@ -1119,6 +1156,7 @@ void Engine::env_update_right(const EnlOp& renl, const Space& er, const Site& B,
       for (int gi = groups.start[tb.key]; gi < groups.start[tb.key + 1]; ++gi) {
         const EnlSub* s = &renl.subs[groups.idx[gi]];
         if (s->sout != so) continue;
+        if (s->trans) throw Error(-6, "environment update of a derived channel");
         p1.add_term(s->ptr, s->cols, B_in + er.soff[tb.qin][s->sin], er.dim[tb.qin], s->cols, 2, s->sign);
       }
     }
@@ -1267,7 +1305,10 @@ void Engine::plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg) {
       A.add_out(Yb + ER.soff[qout][so], ldy, EL.dim[qin], ER.sdim[qout][so], 0);
       for (const EnlSub* s : subs) {
         if (s->sout != so) continue;
-        A.add_term(sg.in + psi_off[qin] + ER.soff[qin][s->sin], ER.dim[qin], s->ptr, s->cols, s->cols, 2, s->sign);
+        if (s->trans)   // Rsub^T = sign * (the block at ptr), cols x rows
+          A.add_term(sg.in + psi_off[qin] + ER.soff[qin][s->sin], ER.dim[qin], s->ptr, s->rows, s->cols, 0, s->sign);
+        else
+          A.add_term(sg.in + psi_off[qin] + ER.soff[qin][s->sin], ER.dim[qin], s->ptr, s->cols, s->cols, 2, s->sign);
       }
     }
   }
@@ -1284,8 +1325,8 @@ void Engine::plan_sigma(const EnlOp& lenl, const EnlOp& renl, Sigma& sg) {
       for (const EnlSub* s : it->second) {
         auto yo = yoff.find({s->b, s->qin});
         if (yo == yoff.end()) continue;
-        B.add_term(s->ptr, s->cols, sg.Y + yo->second + (int64_t)EL.soff[s->qin][s->sin] * ld, ld, s->cols, 0,
-                   s->sign);
+        B.add_term(s->ptr, s->trans ? s->rows : s->cols, sg.Y + yo->second + (int64_t)EL.soff[s->qin][s->sin] * ld, ld,
+                   s->cols, s->trans ? 1 : 0, s->sign);
       }
     }
   upload(A);

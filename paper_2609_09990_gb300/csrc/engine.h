@@ -55,6 +55,7 @@ struct EnlSub {       // one sub-block of an enlarged operator
   const double* ptr;
   int64_t own_off;    // >= 0: offset into the owned buffer (resolved later)
   double sign;
+  int trans = 0;      // 1: the block is sign * (the cols x rows block at ptr)^T (a conjugate channel's)
 };
 struct EnlOp {
   std::vector<EnlSub> subs;
@@ -255,6 +256,9 @@ class Engine {
   std::vector<std::vector<int>> conj_l, sign_l, conj_r, sign_r;
   bool env_conj = true;
   bool env_derived(int bond, int c, bool left) const;
+  // sub-blocks of the derived channels of an enlarged operator: the
+  // transposes of their partners' (bond: the channels' bond)
+  void append_conjugates(EnlOp& op, int bond, bool left) const;
   void env_transposes(Env& out, int bond, bool left);
   // stopping of the accurate tier: a plateau (no 30 % drop over 3
   // iterations) ends it below tier2_floor_mult * u2 * max(1, |theta|);

@@ -347,12 +347,14 @@ TcPlan* Engine::tc_build(const EnlOp& lenl, const EnlOp& renl, int prec, TcTune 
       for (size_t i = i0; i < i1; ++i) {
         const EnlSub& s = op.subs[i];
         if (rowof[i] < 0) continue;   // not used by any product
-        if (!in_allocation(s.ptr, s.rows, s.cols, s.cols, cache)) {
+        const bool ok = s.trans ? in_allocation(s.ptr, s.cols, s.rows, s.rows, cache)
+                                : in_allocation(s.ptr, s.rows, s.cols, s.cols, cache);
+        if (!ok) {
           bad = 1;
           return;
         }
-        out.push_back({s.ptr, s.sign, s.rows, s.cols, s.cols, (int32_t)rowof[i], (int32_t)colof[i],
-                       kstride ? (*kstride)[i] : 0});
+        out.push_back({s.ptr, s.sign, s.rows, s.cols, s.trans ? s.rows : s.cols, (int32_t)rowof[i],
+                       (int32_t)colof[i], kstride ? (*kstride)[i] : 0, s.trans});
       }
     };
     if (nblk > 1) host_parallel_for(nblk, work);
